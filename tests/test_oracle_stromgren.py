@@ -1,0 +1,112 @@
+"""Physics pins of the whole oracle sweep: Test 1 of Sect. 5.1.
+
+* The analytic Stromgren radius and recombination time reproduce the values
+  printed in the paper (r_S = 5.4 kpc, t_rec = 3.86e15 s = 122.4 Myr).
+* The equilibrium-profile solver (Eq. inner_stromgren_region) balances the
+  local rate equation and, globally, emitted photons against recombinations.
+* The oracle's I-front (ionised-volume radius) follows the equilibrium
+  solution at late times; 42 and 84 bins agree (Sect. 5.1.2); the photon
+  budget closes to 1e-10 relative at every checkpoint.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0912_4273_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def paper():
+    return json.load(open(os.path.join(GOLDEN, "paper_test1.json")))
+
+
+def test_analytic_constants_match_paper(paper):
+    rs = O.stromgren_radius(paper["Ndot"], paper["n_H"], paper["alpha_B"])
+    tr = O.recombination_time(paper["n_H"], paper["alpha_B"])
+    assert rs / I.KPC_CM == pytest.approx(paper["r_S_kpc"], rel=0.01)
+    assert tr == pytest.approx(paper["t_rec_s"], rel=0.001)
+    assert tr / I.MYR_S == pytest.approx(paper["t_rec_Myr"], rel=0.001)
+    # front history: r_I(t_rec) = r_S (1 - 1/e)^(1/3); velocity is the derivative
+    t = np.linspace(0.1, 4, 50) * tr
+    r = O.ifront_radius(t, paper["Ndot"], paper["n_H"], paper["alpha_B"])
+    v = O.ifront_velocity(t, paper["Ndot"], paper["n_H"], paper["alpha_B"])
+    dr = np.gradient(r, t)
+    assert np.allclose(v[5:-5], dr[5:-5], rtol=0.02)
+
+
+def test_equilibrium_profile_balances(paper):
+    nH, Nd, a, s = paper["n_H"], paper["Ndot"], paper["alpha_B"], I.SIGMA_H
+    r, y, tau = O.equilibrium_profile(9 * I.KPC_CM, Nd, nH, a, s)
+    x = 1 - y
+    # local balance n_HI Ndot e^-tau sigma / (4 pi r^2) = x^2 n_H^2 alpha_B
+    lhs = y * nH * Nd * np.exp(-tau) * s / (4 * math.pi * r * r)
+    rhs = x * x * nH * nH * a
+    mid = (r > 0.5 * I.KPC_CM) & (r < 5.5 * I.KPC_CM)
+    assert np.allclose(lhs[mid], rhs[mid], rtol=1e-6)
+    # global balance: all photons recombine inside (e^-tau(inf) ~ 0)
+    rec = np.trapezoid(4 * math.pi * r * r * rhs, r)
+    assert tau[-1] > 50
+    assert rec == pytest.approx(Nd, rel=2e-3)
+
+
+def _run(nbins, steps=200, n=8192, seed=0):
+    prob = I.stromgren_problem(n, seed=seed)
+    sim = O.OracleSim(prob, O.Params(nbins=nbins, seed=seed), I.fibonacci_bins(nbins))
+    dt = 500 * I.MYR_S / steps
+    out = []
+    for k in range(5):
+        sim.step(dt, steps // 5)
+        b = sim.budget
+        out.append(((k + 1) * (steps // 5) * dt, O.ionised_radius_sphere(sim.y, prob.volume, prob.interior), b))
+    return prob, sim, out
+
+
+@pytest.fixture(scope="module")
+def run42():
+    return _run(42)
+
+
+def test_budget_closes(run42):
+    for t, r, b in run42[2]:
+        res = b["emitted"] - b["absorbed"] - b["escaped"] - b["in_flight"]
+        assert abs(res) < 1e-10 * b["emitted"]
+        assert b["absorbed"] > 0.5 * b["emitted"]
+
+
+def test_ifront_follows_equilibrium_solution(run42, paper):
+    nH, Nd, a = paper["n_H"], paper["Ndot"], paper["alpha_B"]
+    r, y, _ = O.equilibrium_profile(9 * I.KPC_CM, Nd, nH, a, I.SIGMA_H)
+    r_eq = (3 * np.trapezoid((1 - y) * r * r, r)) ** (1 / 3)  # ionised-volume radius
+    rs = O.stromgren_radius(Nd, nH, a)
+    tr = O.recombination_time(nH, a)
+    for t, ri, _ in run42[2]:
+        if t < 2.4 * tr:
+            continue
+        expect = r_eq * (1 - math.exp(-t / tr)) ** (1 / 3)
+        assert abs(ri / expect - 1) < 0.03, (t / I.MYR_S, ri / expect)
+    assert abs(run42[2][-1][1] / (r_eq * (1 - math.exp(-500 * I.MYR_S / tr)) ** (1 / 3)) - 1) < 0.02
+    assert 1.0 < r_eq / rs < 1.1
+
+
+def test_interior_profile_close_to_equilibrium(run42, paper):
+    prob, sim, _ = run42
+    r, ye, _ = O.equilibrium_profile(9 * I.KPC_CM, paper["Ndot"], paper["n_H"], paper["alpha_B"],
+                                     I.SIGMA_H)
+    y = sim.y
+    c = prob.pos[prob.src_vertex[0]]
+    rv = np.linalg.norm(prob.pos - c, axis=1)
+    for lo in (1.0, 2.0, 3.0, 4.0):
+        s = prob.interior & (rv >= lo * I.KPC_CM) & (rv < (lo + 1) * I.KPC_CM)
+        ratio = np.median(y[s]) / np.interp((lo + 0.5) * I.KPC_CM, r, ye)
+        assert 0.25 < ratio < 4.0, (lo, ratio)
+
+
+def test_bin_count_converged(run42):
+    _, _, out84 = _run(84)
+    assert abs(out84[-1][1] / run42[2][-1][1] - 1) < 0.03
