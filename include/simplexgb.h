@@ -1,0 +1,162 @@
+/*
+ * simplexgb.h -- C ABI of the GB300 (sm_103a) SimpleX2 direction-conserving
+ * photon transport library.
+ *
+ * The library runs the data-parallel hot path of SimpleX2 (Paardekooper,
+ * Kruip & Icke 2010): repeated radiative-transfer steps on a Delaunay graph in
+ * which photons held in n global direction bins move one edge per step along
+ * the most straightforward neighbours of the edge associated with their bin
+ * (Sect. 2.2.3), are absorbed with optical depth n_HI sigma dL (Sect. 4.4,
+ * Eq. optical_depth) and ionise hydrogen through the subcycled rate equation
+ * (Sect. 4.5, Eqs. rate_eq_subcycle, phot_ion_rate_subcycle).
+ *
+ * Conventions shared by every call
+ *   - Return value: SX_OK (0) or a negative SX_E* code; sx_last_error() gives
+ *     a one-line reason.  A failed call leaves the context usable unless it
+ *     returns SX_ECUDA (a CUDA error; the CUDA context may be lost).
+ *   - Host pointers are read during the call (or, for sx_step, not at all);
+ *     the library keeps no reference to them.  Device memory is the caller's:
+ *     the per-grid state lives in one device workspace the caller allocates
+ *     (size from sx_workspace_bytes) and keeps alive until sx_destroy.
+ *   - Vertex ids are the caller's order 0..n-1.  The CSR is symmetric, each
+ *     row sorted strictly ascending, no self loops (a Delaunay graph).
+ *   - Work is queued on the stream given in sx_config (NULL = the legacy
+ *     default stream).  sx_step returns once its work is queued; the read
+ *     calls synchronise the stream before returning.
+ *   - A context is not thread-safe; distinct contexts on distinct streams may
+ *     be driven from distinct threads.
+ */
+#ifndef SIMPLEXGB_H
+#define SIMPLEXGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SX_OK = 0,
+    SX_EINVAL = -1,   /* bad argument or malformed grid */
+    SX_ENOMEM = -2,   /* workspace too small */
+    SX_ECUDA = -3,    /* CUDA runtime error */
+    SX_ESTATE = -4,   /* call out of order (e.g. step before load) */
+    SX_ETIMEOUT = -5  /* a bounded device wait gave up */
+};
+
+enum {
+    SX_FP64 = 0,           /* photons, transport and chemistry in FP64 */
+    SX_FP32_TRANSPORT = 1  /* photons and transport in FP32 (Kahan-compensated
+                              gathers); chemistry, neutral fraction and the
+                              photon budget in FP64 */
+};
+
+#define SX_MAX_BINS 128
+#define SX_MAX_DEGREE 64      /* per non-sink vertex */
+#define SX_MAX_SOURCES 4096
+#define SX_FLAG_SINK 1u
+
+typedef struct sx_ctx sx_ctx;
+
+typedef struct {
+    int32_t nbins;          /* direction bins n, 1..SX_MAX_BINS (paper: 42 or 84) */
+    int32_t precision;      /* SX_FP64 or SX_FP32_TRANSPORT */
+    uint64_t seed;          /* random rotations: Philox4x32-10 key */
+    double sigma;           /* photoionisation cross-section, cm^2 (6.3e-18 at 13.6 eV) */
+    double alpha_B;         /* case-B recombination coefficient, cm^3/s (2.59e-13 at 1e4 K) */
+    double kappa;           /* global path-length correction; <= 0: computed at load */
+    double chem_frac;       /* subcycle length = chem_frac / (Gamma + R), 0 < f <= 1 */
+    double chem_tol;        /* equilibrium when |dy| <= chem_tol * y after a subcycle */
+    int32_t chem_max_sub;   /* subcycle cap per step (>= 1) */
+    int32_t device;         /* CUDA device ordinal */
+    void *stream;           /* cudaStream_t, or NULL */
+} sx_config;
+
+typedef struct {
+    double emitted;     /* photons injected by the sources */
+    double absorbed;    /* photons used by photoionisation */
+    double escaped;     /* photons that reached a sink (or had no outgoing edge) */
+    double in_flight;   /* photons travelling along edges after the last step */
+} sx_budget;
+
+typedef struct {
+    int64_t n, nnz;          /* vertices, directed edges */
+    int64_t step;            /* steps taken so far */
+    int64_t workspace_bytes; /* bytes the grid uses */
+    double kappa;            /* path-length correction in use */
+    int64_t subcycles;       /* chemistry subcycles summed over vertices and steps */
+    int64_t capped;          /* vertex-steps that hit chem_max_sub */
+    int32_t max_degree;      /* largest non-sink degree */
+    int32_t nsources;
+} sx_info;
+
+/* Fill cfg with the Test-1 defaults of Sect. 5.1 (42 bins, FP32 transport,
+   sigma 6.3e-18, alpha_B 2.59e-13, chem_frac 0.5, chem_tol 1e-5,
+   chem_max_sub 1000, seed 0, device 0, NULL stream). */
+void sx_config_default(sx_config *cfg);
+
+/* Create a context.  bin_dirs: nbins x 3 unit vectors (row-major, FP64) --
+   the global direction bins of Sect. 2.2.3 before rotation.  They are copied.
+   Errors: SX_EINVAL (nbins out of range, zero vector, bad precision or
+   chemistry parameters), SX_ECUDA. */
+int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out);
+
+/* Device workspace needed for a grid of n vertices and nnz directed edges. */
+int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes);
+
+/* Load a grid (Sect. 2.1): copy it to the device and build the per-edge
+   tables -- reverse edge, int8-quantised edge direction, the <= 3 most
+   straightforward neighbours of every edge (Sect. 2.2.2, within 90 degrees)
+   -- the global path correction kappa (Sect. 2.2.3) and the per-vertex
+   constants A = n_H V, tau_max = n_H sigma kappa <L>, alpha_B n_H.
+     pos     n x 3 FP64 positions (cm)
+     row_ptr n + 1 int64 CSR offsets; col nnz int32 neighbour ids
+     nH      n FP64 hydrogen densities (cm^-3); volume n FP64 cell volumes (cm^3)
+     flags   n bytes, bit 0 = sink (absorbs everything into "escaped")
+     y0      n FP64 initial neutral fractions, or NULL for 1 (neutral)
+     d_workspace, workspace_bytes: caller-owned device memory, >= sx_workspace_bytes,
+             256-byte aligned.
+   Resets the step counter, the sources and the budget.  Errors: SX_EINVAL
+   (asymmetric/unsorted CSR, id out of range, self loop, non-sink degree >
+   SX_MAX_DEGREE, nnz >= 2^31), SX_ENOMEM (workspace too small), SX_ECUDA. */
+int sx_load_grid(sx_ctx *ctx, int64_t n, const double *pos, const int64_t *row_ptr,
+                 const int32_t *col, const double *nH, const double *volume,
+                 const uint8_t *flags, const double *y0, void *d_workspace,
+                 int64_t workspace_bytes);
+
+/* Make vertex a source of photons_per_s ionising photons (Sect. 4.3); the
+   photons of a step, photons_per_s * dt, enter the vertex in equal shares per
+   bin.  Adding a source to a vertex twice adds the rates.  Errors: SX_EINVAL
+   (vertex out of range, negative rate, too many sources), SX_ESTATE. */
+int sx_add_source(sx_ctx *ctx, int32_t vertex, double photons_per_s);
+
+/* Queue nsteps radiative-transfer steps of dt_s seconds each (Sect. 4.6):
+   per step, rotate the bins at random (Philox4x32-10, counter = step), move
+   packets in flight to the closest bin of the new orientation, inject the
+   sources, update ionisation and absorb (FP64), route the transmitted photons
+   one edge further.  Errors: SX_EINVAL (dt <= 0, nsteps < 0), SX_ESTATE. */
+int sx_step(sx_ctx *ctx, double dt_s, int32_t nsteps);
+
+/* Wait for the context's queued work. */
+int sx_sync(sx_ctx *ctx);
+
+/* Neutral fraction y = 1 - x per vertex (caller order), n doubles. */
+int sx_read_neutral_fraction(sx_ctx *ctx, double *y_out);
+
+/* Photon budget (FP64) and, if per_vertex != NULL, the photons in flight
+   towards every vertex (n doubles). */
+int sx_read_photons(sx_ctx *ctx, double *per_vertex, sx_budget *budget);
+
+int sx_get_info(const sx_ctx *ctx, sx_info *info);
+
+/* Release the context (not the caller's workspace). */
+void sx_destroy(sx_ctx *ctx);
+
+/* Reason for the last failure of a call on ctx (or of sx_create if ctx is NULL). */
+const char *sx_last_error(const sx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIMPLEXGB_H */

@@ -1,0 +1,311 @@
+// sx_api.cu -- the extern "C" boundary declared in include/simplexgb.h.
+// Host code only marshals arguments, copies inputs and queues kernels; every
+// step of the transport path runs in the kernels of sx_setup.cu / sx_step.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/simplexgb.h"
+#include "sx_internal.cuh"
+
+struct sx_ctx {
+  sx_config cfg;
+  cudaStream_t stream = nullptr;
+  std::vector<double> bins;
+  sx::DevGrid g{};
+  sx::Layout L{};
+  double *bins_dev = nullptr;  // inside the workspace
+  bool loaded = false;
+  int64_t step = 0;
+  double emitted = 0.0;
+  std::vector<int32_t> src_vertex;
+  std::vector<double> src_rate;
+  std::unordered_map<int32_t, int> src_slot;
+  int32_t max_degree = 0;
+  bool punit_set = false;  // FP32 photons are stored in units of g.punit photons
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(sx_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg; else g_create_err = msg;
+  return code;
+}
+
+static int cuda_fail(sx_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, SX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SX_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+extern "C" {
+
+void sx_config_default(sx_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->nbins = 42;
+  cfg->precision = SX_FP32_TRANSPORT;
+  cfg->seed = 0;
+  cfg->sigma = 6.3e-18;
+  cfg->alpha_B = 2.59e-13;
+  cfg->kappa = 0.0;
+  cfg->chem_frac = 0.5;
+  cfg->chem_tol = 1e-5;
+  cfg->chem_max_sub = 1000;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+}
+
+int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
+  if (!out) return fail(nullptr, SX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg || !bin_dirs) return fail(nullptr, SX_EINVAL, "cfg or bin_dirs is NULL");
+  if (cfg->nbins < 1 || cfg->nbins > SX_MAX_BINS)
+    return fail(nullptr, SX_EINVAL, "nbins must be in 1..128");
+  if (cfg->precision != SX_FP64 && cfg->precision != SX_FP32_TRANSPORT)
+    return fail(nullptr, SX_EINVAL, "precision must be SX_FP64 or SX_FP32_TRANSPORT");
+  if (!(cfg->chem_frac > 0.0 && cfg->chem_frac <= 1.0))
+    return fail(nullptr, SX_EINVAL, "chem_frac must be in (0, 1]");
+  if (!(cfg->chem_tol >= 0.0) || cfg->chem_max_sub < 1)
+    return fail(nullptr, SX_EINVAL, "chem_tol must be >= 0 and chem_max_sub >= 1");
+  if (!(cfg->sigma >= 0.0) || !(cfg->alpha_B >= 0.0))
+    return fail(nullptr, SX_EINVAL, "sigma and alpha_B must be >= 0");
+  for (int b = 0; b < cfg->nbins; ++b) {
+    const double *d = bin_dirs + 3 * b;
+    const double l2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    if (!(std::fabs(l2 - 1.0) < 1e-6)) return fail(nullptr, SX_EINVAL, "bin directions must be unit vectors");
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return fail(nullptr, SX_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (cfg->device < 0 || cfg->device >= ndev) return fail(nullptr, SX_EINVAL, "device ordinal out of range");
+  sx_ctx *c = new sx_ctx();
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  c->bins.assign(bin_dirs, bin_dirs + 3 * cfg->nbins);
+  *out = c;
+  return SX_OK;
+}
+
+int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes) {
+  if (!ctx || !bytes || n < 1 || nnz < 0) return fail(const_cast<sx_ctx *>(ctx), SX_EINVAL, "bad arguments");
+  const sx::Layout L = sx::make_layout(n, nnz, ctx->cfg.nbins, ctx->cfg.precision);
+  *bytes = (int64_t)(L.total + sizeof(double) * 3 * sx::kMaxBins + 256);
+  return SX_OK;
+}
+
+int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr,
+                 const int32_t *col, const double *nH, const double *volume, const uint8_t *flags,
+                 const double *y0, void *d_workspace, int64_t workspace_bytes) {
+  if (!c) return SX_EINVAL;
+  c->loaded = false;
+  if (n < 1 || !pos || !row_ptr || !nH || !volume || !flags || !d_workspace)
+    return fail(c, SX_EINVAL, "n < 1 or a required pointer is NULL");
+  const int64_t nnz = row_ptr[n];
+  if (row_ptr[0] != 0 || nnz < 0) return fail(c, SX_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (nnz > 0 && !col) return fail(c, SX_EINVAL, "col is NULL");
+  if (nnz >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "nnz must be < 2^31");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+    return fail(c, SX_EINVAL, "workspace must be 256-byte aligned");
+  int64_t need = 0;
+  sx_workspace_bytes(c, n, nnz, &need);
+  if (workspace_bytes < need)
+    return fail(c, SX_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  const cudaStream_t st = c->stream;
+  c->L = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision);
+  sx::DevGrid &g = c->g;
+  g = sx::DevGrid{};
+  sx::bind_layout(g, d_workspace, c->L);
+  g.n = n;
+  g.nnz = nnz;
+  g.nbins = c->cfg.nbins;
+  g.nbp = (g.nbins + 3) / 4 * 4;
+  g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
+  g.precision = c->cfg.precision;
+  g.punit = 1.0;
+  c->punit_set = c->cfg.precision == SX_FP64;
+  c->bins_dev = reinterpret_cast<double *>(static_cast<char *>(d_workspace) + c->L.total);
+  char *base = static_cast<char *>(d_workspace);
+  // zero the state that must start at zero
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_P0, 0, c->L.off_M0 - c->L.off_P0, st));
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_M0, 0, c->L.off_partials - c->L.off_M0, st));
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_partials, 0, c->L.off_tabs - c->L.off_partials, st));
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_src, 0, sizeof(double) * sx::kMaxSources, st));
+  // inputs
+  SX_CUDA(c, cudaMemcpyAsync(g.pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  if (nnz) SX_CUDA(c, cudaMemcpyAsync(g.s_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_nH, nH, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_vol, volume, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_flags, flags, n, cudaMemcpyHostToDevice, st));
+  if (y0) SX_CUDA(c, cudaMemcpyAsync(g.s_y0, y0, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(c->bins_dev, c->bins.data(), sizeof(double) * c->bins.size(),
+                             cudaMemcpyHostToDevice, st));
+  // tables
+  SX_CUDA(c, sx::launch_setup(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
+  SX_CUDA(c, sx::launch_rotation(g, c->bins_dev, c->cfg.seed, 0, 1, st));
+  SX_CUDA(c, sx::launch_kappa_and_consts(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
+                                          y0 ? g.s_y0 : nullptr, st));
+  unsigned long long diag[sx::kDiagCount];
+  SX_CUDA(c, cudaMemcpyAsync(diag, g.diag, sizeof(diag), cudaMemcpyDeviceToHost, st));
+  SX_CUDA(c, cudaStreamSynchronize(st));
+  const unsigned long long errb = diag[sx::kDiagError];
+  c->max_degree = (int32_t)diag[sx::kDiagMaxDeg];
+  if (errb) {
+    std::string m = "malformed grid:";
+    if (errb & sx::kErrColRange) m += " neighbour id out of range;";
+    if (errb & sx::kErrSelfLoop) m += " self loop;";
+    if (errb & sx::kErrUnsorted) m += " row not sorted strictly ascending;";
+    if (errb & sx::kErrAsym) m += " CSR not symmetric;";
+    if (errb & sx::kErrRowPtr) m += " row_ptr not monotone;";
+    if (errb & sx::kErrDegree) m += " non-sink degree > " + std::to_string(SX_MAX_DEGREE) + ";";
+    return fail(c, SX_EINVAL, m);
+  }
+  SX_CUDA(c, cudaMemsetAsync(g.diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
+  c->step = 0;
+  c->emitted = 0.0;
+  c->src_vertex.clear();
+  c->src_rate.clear();
+  c->src_slot.clear();
+  c->loaded = true;
+  return SX_OK;
+}
+
+int sx_add_source(sx_ctx *c, int32_t vertex, double rate) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (vertex < 0 || vertex >= c->g.n) return fail(c, SX_EINVAL, "source vertex out of range");
+  if (!(rate >= 0.0) || !std::isfinite(rate)) return fail(c, SX_EINVAL, "rate must be finite and >= 0");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  auto it = c->src_slot.find(vertex);
+  int slot;
+  if (it != c->src_slot.end()) {
+    slot = it->second;
+    c->src_rate[slot] += rate;
+  } else {
+    if ((int)c->src_vertex.size() >= sx::kMaxSources) return fail(c, SX_EINVAL, "too many sources");
+    slot = (int)c->src_vertex.size();
+    c->src_vertex.push_back(vertex);
+    c->src_rate.push_back(rate);
+    c->src_slot[vertex] = slot;
+    const int32_t s32 = slot;
+    SX_CUDA(c, cudaMemcpyAsync(reinterpret_cast<char *>(c->g.vc + vertex) + offsetof(sx::VConst, src),
+                               &s32, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+  }
+  SX_CUDA(c, cudaMemcpyAsync(c->g.src_rate + slot, &c->src_rate[slot], sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SX_OK;
+}
+
+int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  if (!c->punit_set) {
+    // FP32 storage: fix the photon unit at the power of two just above the
+    // photons the sources emit in one step, so that packets stay near 1 and
+    // the scaling itself is exact
+    double tot = 0.0;
+    for (double r : c->src_rate) tot += r * dt;
+    if (tot > 0.0) {
+      int ex = 0;
+      std::frexp(tot, &ex);
+      c->g.punit = std::ldexp(1.0, ex);
+      c->punit_set = true;
+    }
+  }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, c->step, 0, c->stream));
+    SX_CUDA(c, sx::launch_step(c->g, c->step, dt, c->cfg.chem_frac, c->cfg.chem_tol,
+                               c->cfg.chem_max_sub, c->stream));
+    for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
+    c->step++;
+  }
+  return SX_OK;
+}
+
+int sx_sync(sx_ctx *c) {
+  if (!c) return SX_EINVAL;
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SX_OK;
+}
+
+int sx_read_neutral_fraction(sx_ctx *c, double *y_out) {
+  if (!c || !y_out) return fail(c, SX_EINVAL, "NULL argument");
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  SX_CUDA(c, cudaMemcpyAsync(y_out, c->g.y, sizeof(double) * c->g.n, cudaMemcpyDeviceToHost, c->stream));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  return SX_OK;
+}
+
+int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  if (b) {
+    double tmp[4] = {0, 0, 0, 0};
+    SX_CUDA(c, sx::launch_budget(c->g, c->stream));
+    SX_CUDA(c, cudaMemcpyAsync(tmp, c->g.budget_dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    SX_CUDA(c, cudaStreamSynchronize(c->stream));
+    b->emitted = c->emitted;
+    b->absorbed = tmp[0] * c->g.punit;
+    b->escaped = tmp[1] * c->g.punit;
+    b->in_flight = c->step > 0 ? tmp[2] * c->g.punit : 0.0;
+  }
+  if (per_vertex) {
+    if (c->step == 0) {
+      std::memset(per_vertex, 0, sizeof(double) * c->g.n);
+    } else {
+      SX_CUDA(c, sx::launch_inflight(c->g, c->step, c->stream));
+      SX_CUDA(c, cudaMemcpyAsync(per_vertex, c->g.s_out, sizeof(double) * c->g.n, cudaMemcpyDeviceToHost, c->stream));
+      SX_CUDA(c, cudaStreamSynchronize(c->stream));
+      for (int64_t i = 0; i < c->g.n; ++i) per_vertex[i] *= c->g.punit;
+    }
+  }
+  return SX_OK;
+}
+
+int sx_get_info(const sx_ctx *c, sx_info *info) {
+  if (!c || !info) return SX_EINVAL;
+  std::memset(info, 0, sizeof(*info));
+  if (!c->loaded) return SX_OK;
+  unsigned long long diag[sx::kDiagCount];
+  double kappa = 0.0;
+  if (cudaSetDevice(c->cfg.device) != cudaSuccess) return SX_ECUDA;
+  if (cudaMemcpyAsync(diag, c->g.diag, sizeof(diag), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&kappa, c->g.kappa_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return SX_ECUDA;
+  info->n = c->g.n;
+  info->nnz = c->g.nnz;
+  info->step = c->step;
+  int64_t wb = 0;
+  sx_workspace_bytes(c, c->g.n, c->g.nnz, &wb);
+  info->workspace_bytes = wb;
+  info->kappa = kappa;
+  info->subcycles = (int64_t)diag[sx::kDiagSubcycles];
+  info->capped = (int64_t)diag[sx::kDiagCapped];
+  info->max_degree = c->max_degree;
+  info->nsources = (int32_t)c->src_vertex.size();
+  return SX_OK;
+}
+
+void sx_destroy(sx_ctx *c) { delete c; }
+
+const char *sx_last_error(const sx_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

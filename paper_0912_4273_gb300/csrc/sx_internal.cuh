@@ -1,0 +1,174 @@
+// sx_internal.cuh -- device data layout and shared device helpers of the
+// SimpleX2 DCT library (sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sx {
+
+constexpr int kQ = 127;            // quantisation of unit vectors (int8)
+constexpr int kMaxBins = 128;
+constexpr int kMaxDeg = 64;        // largest non-sink degree the step kernel stages
+constexpr int kTile = 32;          // vertices per CTA in the step kernel (one chemistry warp)
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+constexpr int kMaxSources = 4096;
+constexpr uint32_t kRotTag = 0x53583252u;  // Philox counter word 3 of the rotation draws
+constexpr int kRotMaxAttempts = 64;
+
+// One directed Delaunay edge i -> col, stored in i's CSR row (16 bytes).
+struct __align__(16) Edge {
+  int32_t col;   // target vertex
+  int32_t twin;  // index of the reverse edge col -> i in col's row
+  char4 q;       // rint(127 * unit vector); w = 0
+  uchar4 st;     // most-straightforward slots of this edge (x, y, z), count in w
+};
+
+// Per-vertex constants (32 bytes).
+struct __align__(16) VConst {
+  double A;        // hydrogen atoms n_H V
+  double tau_max;  // optical depth of the neutral cell, n_H sigma kappa <L>
+  double R0;       // alpha_B n_H
+  int32_t flags;   // bit 0 sink
+  int32_t src;     // source slot or -1
+};
+
+// Written once per step by the rotation kernel, read by every CTA.
+struct StepTables {
+  float4 qb[kMaxBins];            // quantised rotated bins (x, y, z), as exact floats
+  int32_t inv_off[kMaxBins + 1];  // packets of old bins inv_idx[inv_off[b]..inv_off[b+1])
+  int32_t inv_idx[kMaxBins];      //   move to new bin b (ascending old index)
+  int32_t attempts;
+  int32_t remap;                  // 0: step 0, no previous orientation
+};
+
+enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagCount = 8 };
+
+// Error bits reported by the load kernels.
+enum : unsigned long long {
+  kErrColRange = 1ull, kErrSelfLoop = 2ull, kErrUnsorted = 4ull, kErrAsym = 8ull,
+  kErrRowPtr = 16ull, kErrDegree = 32ull
+};
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al. 2011)
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// rint(127 u) clamped to [-127, 127]; u is the IEEE result of the caller's ops.
+__device__ __forceinline__ int quantise(double u) {
+  double r = rint(__dmul_rn(127.0, u));
+  r = fmin(fmax(r, -127.0), 127.0);
+  return (int)r;
+}
+
+// ----------------------------------------------------------------------------
+// Float-float accumulation: hi + lo carries ~48 bits with FP32 arithmetic only
+// (Knuth two-sum).  Used for per-vertex and per-block photon sums in FP32 mode.
+// ----------------------------------------------------------------------------
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+  const float s = __fadd_rn(a.hi, b);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return FF{s, __fadd_rn(a.lo, err)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF r = ff_add(a, b.hi);
+  r.lo = __fadd_rn(r.lo, b.lo);
+  return r;
+}
+__device__ __forceinline__ FF ff_shfl_down(FF a, int d) {
+  return FF{__shfl_down_sync(0xffffffffu, a.hi, d), __shfl_down_sync(0xffffffffu, a.lo, d)};
+}
+__device__ __forceinline__ FF ff_warp_sum(FF a) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) a = ff_add(a, ff_shfl_down(a, d));
+  return a;  // lane 0
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+  return v;  // lane 0
+}
+
+// ----------------------------------------------------------------------------
+// Host-side launch wrappers (defined in the .cu files)
+// ----------------------------------------------------------------------------
+struct DevGrid {
+  int64_t n, nnz;
+  int nbins, nbp, mw;   // bins, bins padded to 4, mask words per edge (1, 2 or 4)
+  int precision;        // 0 FP64, 1 FP32 transport
+  double punit;         // photons per stored unit (power of two; stored = photons / punit)
+  double *pos;          // n*3
+  int32_t *row_ptr;     // n+1
+  Edge *edges;          // nnz
+  VConst *vc;           // n
+  double *mean_len;     // n
+  double *y;            // n
+  void *P[2];           // n*nbp photons (T), ping-pong
+  uint32_t *M[2];       // nnz*mw masks, ping-pong
+  double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
+  int64_t nblocks;
+  StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
+  double *src_rate;     // kMaxSources
+  unsigned long long *diag;  // kDiagCount
+  double *kappa_part;   // nblocks_kappa*2
+  int64_t nblocks_kappa;
+  double *kappa_dev;    // 1
+  double *budget_dev;   // 4
+  // load-time scratch
+  int64_t *s_row_ptr;
+  int32_t *s_col;
+  double *s_nH, *s_vol, *s_y0;
+  uint8_t *s_flags;
+  float4 *s_ev;         // nnz: edge vector (x, y, z) and length (w), FP32
+  double *s_out;        // n doubles for readouts
+};
+
+struct Layout {
+  size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
+      off_M1, off_partials, off_tabs, off_src, off_diag, off_kpart, off_kappa, off_budget,
+      off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
+      total;
+  int64_t nblocks, nblocks_kappa;
+};
+
+Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision);
+void bind_layout(DevGrid &g, void *base, const Layout &L);
+
+cudaError_t launch_setup(DevGrid &g, const double *bins_dev, double sigma, double alpha_B,
+                         double kappa_cfg, cudaStream_t st);
+cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double sigma,
+                                    double alpha_B, double kappa_cfg, const double *y0_dev,
+                                    cudaStream_t st);
+cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
+                            int unrotated, cudaStream_t st);
+cudaError_t launch_step(DevGrid &g, int64_t step, double dt, double chem_frac, double chem_tol,
+                        int chem_max_sub, cudaStream_t st);
+cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
+cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
+
+}  // namespace sx

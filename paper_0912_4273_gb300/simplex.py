@@ -1,0 +1,287 @@
+"""Python binding of libsimplexgb.so (the C ABI of include/simplexgb.h).
+
+Argument marshalling only: every step of the transport path runs in the CUDA
+library.  The functions named ``sx_*`` mirror the C entry points one to one
+and raise :class:`SimplexError` on a non-zero return.  :class:`Solver` bundles
+them with a device workspace taken from PyTorch's allocator.
+
+There is no CPU fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SX_OK, SX_EINVAL, SX_ENOMEM, SX_ECUDA, SX_ESTATE, SX_ETIMEOUT = 0, -1, -2, -3, -4, -5
+SX_FP64, SX_FP32_TRANSPORT = 0, 1
+SX_MAX_BINS = 128
+SX_MAX_DEGREE = 64
+SX_FLAG_SINK = 1
+
+
+class SimplexError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"simplexgb error {code}: {msg}")
+        self.code = code
+
+
+class sx_config(C.Structure):
+    _fields_ = [("nbins", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
+                ("sigma", C.c_double), ("alpha_B", C.c_double), ("kappa", C.c_double),
+                ("chem_frac", C.c_double), ("chem_tol", C.c_double),
+                ("chem_max_sub", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class sx_budget(C.Structure):
+    _fields_ = [("emitted", C.c_double), ("absorbed", C.c_double), ("escaped", C.c_double),
+                ("in_flight", C.c_double)]
+
+    def as_dict(self):
+        return dict(emitted=self.emitted, absorbed=self.absorbed, escaped=self.escaped,
+                    in_flight=self.in_flight)
+
+
+class sx_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("step", C.c_int64),
+                ("workspace_bytes", C.c_int64), ("kappa", C.c_double),
+                ("subcycles", C.c_int64), ("capped", C.c_int64), ("max_degree", C.c_int32),
+                ("nsources", C.c_int32)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+# (name, restype, argtypes) of every entry point of include/simplexgb.h
+_P = C.POINTER
+_SIGS = [
+    ("sx_config_default", None, [_P(sx_config)]),
+    ("sx_create", C.c_int, [_P(sx_config), _P(C.c_double), _P(C.c_void_p)]),
+    ("sx_workspace_bytes", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _P(C.c_int64)]),
+    ("sx_load_grid", C.c_int, [C.c_void_p, C.c_int64, _P(C.c_double), _P(C.c_int64),
+                               _P(C.c_int32), _P(C.c_double), _P(C.c_double), _P(C.c_uint8),
+                               _P(C.c_double), C.c_void_p, C.c_int64]),
+    ("sx_add_source", C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
+    ("sx_step", C.c_int, [C.c_void_p, C.c_double, C.c_int32]),
+    ("sx_sync", C.c_int, [C.c_void_p]),
+    ("sx_read_neutral_fraction", C.c_int, [C.c_void_p, _P(C.c_double)]),
+    ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
+    ("sx_get_info", C.c_int, [C.c_void_p, _P(sx_info)]),
+    ("sx_destroy", None, [C.c_void_p]),
+    ("sx_last_error", C.c_char_p, [C.c_void_p]),
+]
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def lib():
+    """Load libsimplexgb.so (built in-tree by ``build()``); raise if it is missing."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is not built; run __graft_entry__.build() first")
+            L = C.CDLL(path)
+            for name, res, args in _SIGS:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def _check(ctx, rc: int):
+    if rc != SX_OK:
+        msg = lib().sx_last_error(ctx)
+        raise SimplexError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# One-to-one wrappers of the C entry points
+# ---------------------------------------------------------------------------
+def sx_config_default() -> sx_config:
+    cfg = sx_config()
+    lib().sx_config_default(C.byref(cfg))
+    return cfg
+
+
+def sx_create(cfg: sx_config, bin_dirs: np.ndarray):
+    b = np.ascontiguousarray(bin_dirs, dtype=np.float64)
+    if b.shape != (cfg.nbins, 3):
+        raise ValueError("bin_dirs must be nbins x 3")
+    ctx = C.c_void_p()
+    _check(None, lib().sx_create(C.byref(cfg), _ptr(b, C.c_double), C.byref(ctx)))
+    return ctx
+
+
+def sx_workspace_bytes(ctx, n: int, nnz: int) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().sx_workspace_bytes(ctx, n, nnz, C.byref(out)))
+    return out.value
+
+
+def sx_load_grid(ctx, n, pos, row_ptr, col, nH, volume, flags, y0, d_workspace: int,
+                 workspace_bytes: int):
+    y0p = None if y0 is None else _ptr(y0, C.c_double)
+    _check(ctx, lib().sx_load_grid(ctx, n, _ptr(pos, C.c_double), _ptr(row_ptr, C.c_int64),
+                                   _ptr(col, C.c_int32), _ptr(nH, C.c_double),
+                                   _ptr(volume, C.c_double), _ptr(flags, C.c_uint8), y0p,
+                                   C.c_void_p(d_workspace), workspace_bytes))
+
+
+def sx_add_source(ctx, vertex: int, photons_per_s: float):
+    _check(ctx, lib().sx_add_source(ctx, int(vertex), float(photons_per_s)))
+
+
+def sx_step(ctx, dt_s: float, nsteps: int):
+    _check(ctx, lib().sx_step(ctx, float(dt_s), int(nsteps)))
+
+
+def sx_sync(ctx):
+    _check(ctx, lib().sx_sync(ctx))
+
+
+def sx_read_neutral_fraction(ctx, out: np.ndarray):
+    _check(ctx, lib().sx_read_neutral_fraction(ctx, _ptr(out, C.c_double)))
+
+
+def sx_read_photons(ctx, per_vertex=None) -> sx_budget:
+    b = sx_budget()
+    pv = None if per_vertex is None else _ptr(per_vertex, C.c_double)
+    _check(ctx, lib().sx_read_photons(ctx, pv, C.byref(b)))
+    return b
+
+
+def sx_get_info(ctx) -> sx_info:
+    info = sx_info()
+    _check(ctx, lib().sx_get_info(ctx, C.byref(info)))
+    return info
+
+
+def sx_destroy(ctx):
+    lib().sx_destroy(ctx)
+
+
+def sx_last_error(ctx=None) -> str:
+    m = lib().sx_last_error(ctx)
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# Convenience: one grid with a torch-allocated device workspace
+# ---------------------------------------------------------------------------
+class Solver:
+    """A SimpleX2 DCT solve of one grid on one GPU.
+
+    The workspace (per-grid device state) is a torch uint8 tensor on the
+    context's device, so that memory comes from PyTorch's caching allocator;
+    ``stream`` is a ``torch.cuda.Stream`` (default: the current stream).
+    """
+
+    def __init__(self, bins: np.ndarray, precision: int = SX_FP32_TRANSPORT, seed: int = 0,
+                 device: int = 0, stream=None, sigma: float = 6.3e-18, alpha_B: float = 2.59e-13,
+                 kappa: float = 0.0, chem_frac: float = 0.5, chem_tol: float = 1e-5,
+                 chem_max_sub: int = 1000):
+        import torch
+
+        self._torch = torch
+        cfg = sx_config_default()
+        cfg.nbins = len(bins)
+        cfg.precision = precision
+        cfg.seed = seed
+        cfg.sigma = sigma
+        cfg.alpha_B = alpha_B
+        cfg.kappa = kappa
+        cfg.chem_frac = chem_frac
+        cfg.chem_tol = chem_tol
+        cfg.chem_max_sub = chem_max_sub
+        cfg.device = device
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        cfg.stream = C.c_void_p(self.stream.cuda_stream)
+        self.cfg = cfg
+        self.nbins = len(bins)
+        self.ctx = sx_create(cfg, bins)
+        self.workspace = None
+        self.n = 0
+
+    def workspace_bytes(self, n: int, nnz: int) -> int:
+        return sx_workspace_bytes(self.ctx, n, nnz)
+
+    def load(self, problem=None, *, pos=None, row_ptr=None, col=None, nH=None, volume=None,
+             flags=None, y0=None, workspace=None):
+        if problem is not None:
+            pos, row_ptr, col = problem.pos, problem.row_ptr, problem.col
+            nH, volume, flags = problem.nH, problem.volume, problem.flags
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        nH = np.ascontiguousarray(nH, dtype=np.float64)
+        volume = np.ascontiguousarray(volume, dtype=np.float64)
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        y0 = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64)
+        n = len(pos)
+        nbytes = self.workspace_bytes(n, int(row_ptr[-1]))
+        if workspace is None:
+            workspace = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        self.workspace = workspace
+        sx_load_grid(self.ctx, n, pos, row_ptr, col, nH, volume, flags, y0,
+                     workspace.data_ptr(), workspace.numel())
+        self.n = n
+        if problem is not None:
+            for v, r in zip(problem.src_vertex, problem.src_rate):
+                self.add_source(int(v), float(r))
+        return self
+
+    def add_source(self, vertex: int, photons_per_s: float):
+        sx_add_source(self.ctx, vertex, photons_per_s)
+
+    def step(self, dt: float, nsteps: int = 1):
+        sx_step(self.ctx, dt, nsteps)
+
+    def sync(self):
+        sx_sync(self.ctx)
+
+    @property
+    def y(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float64)
+        sx_read_neutral_fraction(self.ctx, out)
+        return out
+
+    @property
+    def budget(self) -> dict:
+        return sx_read_photons(self.ctx).as_dict()
+
+    def photons(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float64)
+        sx_read_photons(self.ctx, out)
+        return out
+
+    @property
+    def info(self) -> dict:
+        i = sx_get_info(self.ctx)
+        return {k: getattr(i, k) for k, _ in sx_info._fields_}
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sx_destroy(self.ctx)
+            self.ctx = None
+        self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

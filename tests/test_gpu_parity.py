@@ -1,0 +1,180 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (element by element):
+  * SX_FP64: every arithmetic step of the path is the same IEEE FP64 sequence
+    as the oracle's except exp/expm1 (1-2 ulp between libraries) and the
+    order of the budget sums -> |dy| <= 1e-9, budget 1e-9 relative.
+  * SX_FP32_TRANSPORT: photons are rounded to FP32 at every hop (2^-24
+    relative) -> |dy| <= 1e-4 per vertex and 1e-5 of the emitted photons for
+    each budget term.
+Routing decisions (association, straight table, bin remap) are integer on
+both sides and therefore identical.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0912_4273_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_0912_4273_gb300 import simplex as S  # noqa: E402
+
+DT = 2.5 * I.MYR_S
+
+
+def budget_err(b, rb):
+    return max(abs(b[k] - rb[k]) for k in rb) / max(rb["emitted"], 1e-300)
+
+
+@pytest.fixture(scope="module")
+def c0():
+    prob = I.stromgren_problem(8192, seed=0)
+    bins = I.fibonacci_bins(42)
+    ref = O.OracleSim(prob, O.Params(nbins=42, seed=0), bins)
+    snaps = []
+    for k in range(4):
+        ref.step(DT, 50)
+        snaps.append((ref.y.copy(), ref.budget, ref.I.sum(axis=1)))
+    return prob, bins, ref, snaps
+
+
+@pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
+                                                 (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
+def test_c0_parity(c0, precision, ytol, btol):
+    prob, bins, ref, snaps = c0
+    s = S.Solver(bins, precision=precision, seed=0, kappa=ref.kappa).load(prob)
+    for k in range(4):
+        s.step(DT, 50)
+        y_ref, b_ref, ph_ref = snaps[k]
+        y = s.y
+        assert np.abs(y - y_ref).max() <= ytol, (k, np.abs(y - y_ref).max())
+        assert budget_err(s.budget, b_ref) <= btol
+        ph = s.photons()
+        assert np.abs(ph - ph_ref).max() <= btol * b_ref["emitted"]
+    info = s.info
+    assert info["step"] == 200
+    assert info["capped"] == 0
+    s.close()
+
+
+def test_kappa_computed_on_device_matches_oracle(c0):
+    prob, bins, ref, _ = c0
+    s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT).load(prob)
+    assert s.info["kappa"] == pytest.approx(ref.kappa, rel=1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("nbins", [6, 21, 32, 33, 63, 64, 65, 84, 128])
+def test_bin_counts(nbins):
+    prob = I.stromgren_problem(3000, seed=2)
+    bins = I.fibonacci_bins(nbins)
+    ref = O.OracleSim(prob, O.Params(nbins=nbins, seed=5), bins)
+    ref.step(DT, 25)
+    for precision, tol in ((S.SX_FP64, 1e-9), (S.SX_FP32_TRANSPORT, 1e-4)):
+        s = S.Solver(bins, precision=precision, seed=5, kappa=ref.kappa).load(prob)
+        s.step(DT, 25)
+        assert np.abs(s.y - ref.y).max() <= tol
+        assert budget_err(s.budget, ref.budget) <= (1e-9 if precision == S.SX_FP64 else 1e-5)
+        s.close()
+
+
+def test_deterministic_and_chunk_invariant(c0):
+    prob, bins, ref, _ = c0
+    out = []
+    for chunks in ((60,), (20, 40), (1,) * 60):
+        s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0).load(prob)
+        for c in chunks:
+            s.step(DT, c)
+        out.append((s.y, s.budget))
+        s.close()
+    for y, b in out[1:]:
+        assert np.array_equal(y, out[0][0])
+        assert b == out[0][1]
+
+
+def test_transparent_medium_conserves_photons():
+    p = np.random.default_rng(4).random((6000, 3))
+    sink = np.any((p < 0.05) | (p > 0.95), axis=1)
+    src = int(np.argmin(np.linalg.norm(p - 0.5, axis=1)))
+    prob = I.point_process_problem(p, 1e-3, sink_mask=sink, sources=[(src, 1e50)])
+    bins = I.fibonacci_bins(42)
+    ref = O.OracleSim(prob, O.Params(nbins=42, sigma=0.0), bins)
+    ref.step(1e13, 30)
+    s = S.Solver(bins, sigma=0.0, kappa=ref.kappa).load(prob)
+    s.step(1e13, 30)
+    b = s.budget
+    assert b["absorbed"] == 0.0
+    assert b["emitted"] == pytest.approx(b["escaped"] + b["in_flight"], rel=1e-6)
+    assert budget_err(b, ref.budget) <= 1e-5
+    s.close()
+
+
+def test_tiny_grid_and_no_sources():
+    p = np.random.default_rng(0).random((9, 3))
+    prob = I.point_process_problem(p, 1e-3, sources=[(0, 1e50)])
+    bins = I.fibonacci_bins(21)
+    ref = O.OracleSim(prob, O.Params(nbins=21), bins)
+    ref.step(1e13, 7)
+    s = S.Solver(bins, precision=S.SX_FP64, kappa=ref.kappa).load(prob)
+    s.step(1e13, 7)
+    assert np.abs(s.y - ref.y).max() <= 1e-9
+    assert budget_err(s.budget, ref.budget) <= 1e-9
+    s.close()
+    # no sources: nothing changes from a neutral start
+    prob.src_vertex = prob.src_vertex[:0]
+    prob.src_rate = prob.src_rate[:0]
+    s = S.Solver(bins).load(prob)
+    s.step(1e13, 5)
+    assert np.all(s.y == 1.0)
+    assert all(v == 0.0 for v in s.budget.values())
+    s.close()
+
+
+def test_initial_ionisation_recombines_like_oracle():
+    prob = I.stromgren_problem(2000, seed=3)
+    bins = I.fibonacci_bins(42)
+    y0 = np.random.default_rng(1).random(prob.n)
+    ref = O.OracleSim(prob, O.Params(nbins=42, seed=3), bins, y0=y0)
+    ref.step(DT, 10)
+    s = S.Solver(bins, precision=S.SX_FP64, seed=3, kappa=ref.kappa).load(prob, y0=y0)
+    s.step(DT, 10)
+    assert np.abs(s.y - ref.y).max() <= 1e-9
+    s.close()
+
+
+def test_invalid_grids_are_rejected():
+    prob = I.stromgren_problem(500, seed=0)
+    bins = I.fibonacci_bins(42)
+    s = S.Solver(bins)
+    with pytest.raises(S.SimplexError) as e:
+        s.step(DT, 1)
+    assert e.value.code == S.SX_ESTATE
+    # asymmetric: drop the first edge of vertex 0's row from the CSR
+    rp = prob.row_ptr.copy()
+    col = np.delete(prob.col, 0)
+    rp[1:] -= 1
+    with pytest.raises(S.SimplexError) as e:
+        s.load(pos=prob.pos, row_ptr=rp, col=col, nH=prob.nH, volume=prob.volume, flags=prob.flags)
+    assert e.value.code == S.SX_EINVAL and "symmetric" in str(e.value)
+    # a non-sink star centre with more than SX_MAX_DEGREE neighbours
+    n = 80
+    pos = np.random.default_rng(0).normal(size=(n, 3))
+    rows = [list(range(1, n))] + [[0] for _ in range(1, n)]
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    col = np.concatenate(rows).astype(np.int32)
+    with pytest.raises(S.SimplexError) as e:
+        s.load(pos=pos, row_ptr=row_ptr, col=col, nH=np.ones(n), volume=np.ones(n),
+               flags=np.zeros(n, np.uint8))
+    assert e.value.code == S.SX_EINVAL and "degree" in str(e.value)
+    # workspace too small
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(S.SimplexError) as e:
+        s.load(prob, workspace=small)
+    assert e.value.code == S.SX_ENOMEM
+    s.close()
