@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark of the SimpleX2 DCT sweep on GB300.
+
+Metric: DCT vertex-direction updates per second (interior vertices x bins x
+steps / time) on the Test-1 Stromgren workload at 2^20 interior vertices and
+84 bins, FP32 transport with FP64 chemistry (the configuration the headline
+metric is quoted on).  One step is one pass of the whole hot path: rotation
+and bin remap, gather, sources, chemistry, association and routing, budget.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica (its own grid and
+seed): the path has no data exchange between GPUs, so scaling is weak and
+the only collectives are a barrier and a max over the ranks' timings.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DCT vertex-direction updates/s"
+UNIT = "updates/s"
+
+WORKLOADS = {
+    # 2^20 interior vertices of the Test-1 grid (Sect. 5.1), 84 bins, 1000 steps over 500 Myr
+    "c1": dict(n=1 << 20, nbins=84, precision="fp32", dt_myr=0.5, seed=0,
+               name="Test-1 Stromgren grid, 2^20 interior Poisson-Delaunay vertices + sink shell, "
+                    "84 direction bins, FP32 transport / FP64 chemistry, dt = 0.5 Myr"),
+    # the small FP64 case
+    "c0": dict(n=8192, nbins=42, precision="fp64", dt_myr=2.5, seed=0,
+               name="Test-1 Stromgren grid, 8192 interior vertices + sink shell, 42 bins, FP64, "
+                    "dt = 2.5 Myr"),
+}
+
+# DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {"sx_step.cu_sha256": None, "bytes_per_launch": None, "workload": None}
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (NCCL on GPUs; the CPU tests drive them with gloo)
+# ---------------------------------------------------------------------------
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def dist_init(world: int, backend: str):
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    return units_per_rank * world / (max_ms * 1e-3)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+_CLK_FIELDS = ["timestamp", "index", "clocks.sm", "clocks.max.sm", "power.draw",
+               "clocks_event_reasons.active", "clocks_event_reasons.hw_slowdown",
+               "clocks_event_reasons.hw_thermal_slowdown",
+               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.samples = []
+        self.proc = None
+        self.gpu_index = gpu_index
+        self.period_ms = period_ms
+        self.t0 = self.t1 = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={','.join(_CLK_FIELDS)}", "--format=csv,noheader,nounits",
+               f"-lms", str(self.period_ms), "-i", str(self.gpu_index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._th = threading.Thread(target=self._read, daemon=True)
+        self._th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, which: str):
+        if which == "start":
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(self.period_ms / 1000.0 * 1.5)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [r for t, r in self.samples if self.t0 is not None and self.t0 <= t <= self.t1 + 0.05]
+        if not rows:  # timed region shorter than one period: nearest sample
+            rows = [min(self.samples, key=lambda s: abs(s[0] - (self.t0 or 0)))[1]] if self.samples else []
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[2]))
+                smax = float(r[3])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[6:10]):
+                if v.strip().lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def algorithmic_bytes_per_vertex(nbins: int, fp64: bool, mean_degree: float) -> float:
+    """Bytes one vertex-step must move: its bin row read once and written once,
+    y read and written (FP64), its adjacency (one 4-byte id per edge) and its
+    constants (16 bytes)."""
+    w = 8 if fp64 else 4
+    return 2 * nbins * w + 16 + 4 * mean_degree + 16
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_0912_4273_gb300", "csrc", "sx_step.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def make_problem(wl: dict, seed: int):
+    from paper_0912_4273_gb300 import inputs as I
+
+    return I.cached(I.stromgren_problem, wl["n"], seed=seed)
+
+
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    dist_init(world, "nccl")
+    seed = wl["seed"] + rank
+    prob = make_problem(wl, seed)
+    bins = I.fibonacci_bins(wl["nbins"])
+    dt = wl["dt_myr"] * I.MYR_S
+    fp64 = wl["precision"] == "fp64"
+    prec = S.SX_FP64 if fp64 else S.SX_FP32_TRANSPORT
+    stream = torch.cuda.Stream(device)
+    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream).load(prob)
+    n_int = int(prob.interior.sum())
+    solver.step(dt, args.warmup)
+    solver.sync()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    solver.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark("start")
+    e0.record(stream)
+    solver.step(dt, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks.mark("stop")
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    ms = e0.elapsed_time(e1)
+    info = solver.info
+    solver.profile(False)
+    clk = clocks.stop()
+    max_ms = reduce_max(ms, world, device)
+    value = aggregate(n_int * wl["nbins"] * args.steps, world, max_ms)
+    kernel_ms = info["step_kernel_ms"] / max(info["step_kernel_launches"], 1)
+    mean_deg = prob.nnz / prob.n
+    bytes_launch = algorithmic_bytes_per_vertex(wl["nbins"], fp64, mean_deg) * prob.n
+    achieved = bytes_launch / (kernel_ms * 1e-3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    traffic = None
+    if NCU_TRAFFIC["sx_step.cu_sha256"] == kernel_source_sha() and NCU_TRAFFIC["workload"] == args.config:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    budget = solver.budget
+    solver.close()
+
+    e2e = run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream) if not args.no_e2e else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = run_cpu_baseline(wl, prob, bins, dt, seed)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
+        "data": "synthetic (seeded Poisson-Delaunay Test-1 grid)",
+        "config": {"workload": wl["name"], "n_interior": n_int, "n_vertices": prob.n,
+                   "nnz": prob.nnz, "nbins": wl["nbins"],
+                   "chemistry": "f64", "transport": "f64" if fp64 else "f32",
+                   "l2": f"no flush: per-grid state {info['workspace_bytes'] / 1e9:.2f} GB > 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_step", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+        "clocks": clk,
+        "gpu_launches": 2 * args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "budget_residual": (budget["emitted"] - budget["absorbed"] - budget["escaped"]
+                            - budget["in_flight"]) / max(budget["emitted"], 1e-300),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream):
+    """The whole solve through the C ABI from pinned host buffers: load the grid
+    (host->device), every step read the photon budget back, at the end read the
+    neutral fraction."""
+    import torch
+
+    from paper_0912_4273_gb300 import simplex as S
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t.numpy()
+
+    host = dict(pos=pinned(prob.pos), row_ptr=pinned(prob.row_ptr), col=pinned(prob.col),
+                nH=pinned(prob.nH), volume=pinned(prob.volume), flags=pinned(prob.flags))
+    y_out = pinned(np.zeros(prob.n))
+    h2d = sum(a.nbytes for a in host.values())
+    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream)
+    nbytes = solver.workspace_bytes(prob.n, prob.nnz)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", local_rank))
+    K = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver.load(workspace=ws, **host)
+    for v, r in zip(prob.src_vertex, prob.src_rate):
+        solver.add_source(int(v), float(r))
+    for _ in range(K):
+        solver.step(dt, 1)
+        S.sx_read_photons(solver.ctx)
+    S.sx_read_neutral_fraction(solver.ctx, y_out)
+    t1 = time.perf_counter()
+    solver.close()
+    n_int = int(prob.interior.sum())
+    return {"value": n_int * wl["nbins"] * K / (t1 - t0), "unit": UNIT,
+            "h2d_bytes_per_step": (h2d + 12 * len(prob.src_rate)) / K,
+            "d2h_bytes_per_step": (y_out.nbytes + 24 * K) / K,
+            "seconds": t1 - t0}
+
+
+def run_cpu_baseline(wl, prob, bins, dt, seed, budget_s: float = 12.0, max_steps: int = 4):
+    import oracle as O
+
+    sim = O.OracleSim(prob, O.Params(nbins=wl["nbins"], seed=seed), bins)
+    n_int = int(prob.interior.sum())
+    done = 0
+    t0 = time.perf_counter()
+    while done < max_steps and (time.perf_counter() - t0) < budget_s:
+        sim.step(dt, 1)
+        done += 1
+    el = time.perf_counter() - t0
+    return {"value": n_int * wl["nbins"] * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} oracle steps (single thread, FP64) of the same grid"}
+
+
+def run_reference(args, wl, rank, world):
+    """The oracle as the reference arm: each step is one FP64 oracle step of a
+    2^14-vertex grid built with the same recipe (a bounded sample)."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_0912_4273_gb300 import inputs as I
+
+    n_sample = 1 << 14
+    prob = I.stromgren_problem(n_sample, seed=wl["seed"])
+    bins = I.fibonacci_bins(wl["nbins"])
+    dt = wl["dt_myr"] * I.MYR_S
+    sim = O.OracleSim(prob, O.Params(nbins=wl["nbins"], seed=wl["seed"]), bins)
+    sim.step(dt, args.warmup)
+    t0 = time.perf_counter()
+    sim.step(dt, args.steps)
+    el = time.perf_counter() - t0
+    n_int = int(prob.interior.sum())
+    value = n_int * wl["nbins"] * args.steps / el
+    sample = (f"each step one FP64 oracle step of a {n_sample}-vertex grid of the same recipe "
+              f"({wl['nbins']} bins), single thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Poisson-Delaunay Test-1 grid)",
+        "config": {"workload": wl["name"], "nbins": wl["nbins"], "sample_vertices": n_sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(WORKLOADS), default="c1")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    wl = WORKLOADS[args.config]
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    run_ours(args, wl, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -89,6 +89,8 @@ typedef struct {
     int64_t capped;          /* vertex-steps that hit chem_max_sub */
     int32_t max_degree;      /* largest non-sink degree */
     int32_t nsources;
+    double step_kernel_ms;   /* summed duration of the timed step-kernel launches */
+    int64_t step_kernel_launches;
 } sx_info;
 
 /* Fill cfg with the Test-1 defaults of Sect. 5.1 (42 bins, FP32 transport,
@@ -148,7 +150,13 @@ int sx_read_neutral_fraction(sx_ctx *ctx, double *y_out);
    towards every vertex (n doubles). */
 int sx_read_photons(sx_ctx *ctx, double *per_vertex, sx_budget *budget);
 
-int sx_get_info(const sx_ctx *ctx, sx_info *info);
+/* Counters of the grid; synchronises the stream if kernel timing is on. */
+int sx_get_info(sx_ctx *ctx, sx_info *info);
+
+/* enable = 1: bracket every step-kernel launch with a CUDA event pair on the
+   context's stream and accumulate the durations (reported by sx_get_info);
+   enabling resets the sums.  enable = 0: stop timing. */
+int sx_profile(sx_ctx *ctx, int enable);
 
 /* Release the context (not the caller's workspace). */
 void sx_destroy(sx_ctx *ctx);

@@ -274,6 +274,11 @@ double ox_kappa(int64_t n, const double *pos, const int64_t *row_ptr, const int3
 double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, double R0,
                double fc, double tol, int max_sub, int *nsub_out, int *capped_out) {
     double y = *y_io;
+    if (!(A > 0.0)) {              /* no atoms (n_H = 0): tau = 0, the cell is transparent */
+        if (nsub_out) *nsub_out = 0;
+        if (capped_out) *capped_out = 0;
+        return 1.0;
+    }
     double F = N_in / dt;          /* photons per second, constant over the step */
     double t_left = dt;
     double trans_int = 0.0;        /* integral of e^{-tau} dt */

@@ -26,7 +26,18 @@ struct sx_ctx {
   std::unordered_map<int32_t, int> src_slot;
   int32_t max_degree = 0;
   bool punit_set = false;  // FP32 photons are stored in units of g.punit photons
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  size_t events_used = 0;
+  double kernel_ms = 0.0;
+  int64_t kernel_launches = 0;
   std::string err;
+  ~sx_ctx() {
+    for (auto &e : events) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+  }
 };
 
 static thread_local std::string g_create_err;
@@ -153,7 +164,7 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
                              cudaMemcpyHostToDevice, st));
   // tables
   SX_CUDA(c, sx::launch_setup(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
-  SX_CUDA(c, sx::launch_rotation(g, c->bins_dev, c->cfg.seed, 0, 1, st));
+  SX_CUDA(c, sx::launch_rotation(g, c->bins_dev, c->cfg.seed, 0, 1, 1.0, st));
   SX_CUDA(c, sx::launch_kappa_and_consts(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
                                           y0 ? g.s_y0 : nullptr, st));
   unsigned long long diag[sx::kDiagCount];
@@ -177,6 +188,7 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
   c->src_vertex.clear();
   c->src_rate.clear();
   c->src_slot.clear();
+  g.nsrc = 0;
   c->loaded = true;
   return SX_OK;
 }
@@ -198,6 +210,7 @@ int sx_add_source(sx_ctx *c, int32_t vertex, double rate) {
     c->src_vertex.push_back(vertex);
     c->src_rate.push_back(rate);
     c->src_slot[vertex] = slot;
+    c->g.nsrc = (int)c->src_vertex.size();
     const int32_t s32 = slot;
     SX_CUDA(c, cudaMemcpyAsync(reinterpret_cast<char *>(c->g.vc + vertex) + offsetof(sx::VConst, src),
                                &s32, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
@@ -227,9 +240,19 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
     }
   }
   for (int32_t k = 0; k < nsteps; ++k) {
-    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, c->step, 0, c->stream));
+    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, c->step, 0, dt, c->stream));
+    if (c->profiling) {
+      if (c->events_used == c->events.size()) {
+        cudaEvent_t a, b;
+        SX_CUDA(c, cudaEventCreate(&a));
+        SX_CUDA(c, cudaEventCreate(&b));
+        c->events.emplace_back(a, b);
+      }
+      SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
+    }
     SX_CUDA(c, sx::launch_step(c->g, c->step, dt, c->cfg.chem_frac, c->cfg.chem_tol,
                                c->cfg.chem_max_sub, c->stream));
+    if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
     for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
     c->step++;
   }
@@ -279,10 +302,40 @@ int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
   return SX_OK;
 }
 
-int sx_get_info(const sx_ctx *c, sx_info *info) {
+static int drain_events(sx_ctx *c) {
+  if (!c->events_used) return SX_OK;
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t k = 0; k < c->events_used; ++k) {
+    float ms = 0.f;
+    SX_CUDA(c, cudaEventElapsedTime(&ms, c->events[k].first, c->events[k].second));
+    c->kernel_ms += ms;
+  }
+  c->kernel_launches += (int64_t)c->events_used;
+  c->events_used = 0;
+  return SX_OK;
+}
+
+int sx_profile(sx_ctx *c, int enable) {
+  if (!c) return SX_EINVAL;
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  int rc = drain_events(c);
+  if (rc) return rc;
+  c->profiling = enable != 0;
+  if (c->profiling) {
+    c->kernel_ms = 0.0;
+    c->kernel_launches = 0;
+  }
+  return SX_OK;
+}
+
+int sx_get_info(sx_ctx *c, sx_info *info) {
   if (!c || !info) return SX_EINVAL;
   std::memset(info, 0, sizeof(*info));
   if (!c->loaded) return SX_OK;
+  int rc = drain_events(c);
+  if (rc) return rc;
+  info->step_kernel_ms = c->kernel_ms;
+  info->step_kernel_launches = c->kernel_launches;
   unsigned long long diag[sx::kDiagCount];
   double kappa = 0.0;
   if (cudaSetDevice(c->cfg.device) != cudaSuccess) return SX_ECUDA;

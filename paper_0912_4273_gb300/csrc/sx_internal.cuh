@@ -27,7 +27,7 @@ struct __align__(16) Edge {
 
 // Per-vertex constants (32 bytes).
 struct __align__(16) VConst {
-  double A;        // hydrogen atoms n_H V
+  double invA;     // 1 / (hydrogen atoms n_H V); 0 for an empty cell
   double tau_max;  // optical depth of the neutral cell, n_H sigma kappa <L>
   double R0;       // alpha_B n_H
   int32_t flags;   // bit 0 sink
@@ -134,6 +134,8 @@ struct DevGrid {
   int64_t nblocks;
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
   double *src_rate;     // kMaxSources
+  double *src_share;    // kMaxSources: photons per bin per step of each source, stored units
+  int nsrc;
   unsigned long long *diag;  // kDiagCount
   double *kappa_part;   // nblocks_kappa*2
   int64_t nblocks_kappa;
@@ -150,7 +152,7 @@ struct DevGrid {
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
-      off_M1, off_partials, off_tabs, off_src, off_diag, off_kpart, off_kappa, off_budget,
+      off_M1, off_partials, off_tabs, off_src, off_share, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       total;
   int64_t nblocks, nblocks_kappa;
@@ -165,7 +167,7 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
                                     double alpha_B, double kappa_cfg, const double *y0_dev,
                                     cudaStream_t st);
 cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
-                            int unrotated, cudaStream_t st);
+                            int unrotated, double dt, cudaStream_t st);
 cudaError_t launch_step(DevGrid &g, int64_t step, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);

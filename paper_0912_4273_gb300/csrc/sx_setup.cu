@@ -36,6 +36,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
   L.off_partials = take(sizeof(double) * 4 * L.nblocks);
   L.off_tabs = take(sizeof(StepTables) * 2);
   L.off_src = take(sizeof(double) * kMaxSources);
+  L.off_share = take(sizeof(double) * kMaxSources);
   L.off_diag = take(sizeof(unsigned long long) * kDiagCount);
   L.off_kpart = take(sizeof(double) * 2 * L.nblocks_kappa);
   L.off_kappa = take(sizeof(double));
@@ -68,6 +69,7 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.nblocks = L.nblocks;
   g.tabs = reinterpret_cast<StepTables *>(b + L.off_tabs);
   g.src_rate = reinterpret_cast<double *>(b + L.off_src);
+  g.src_share = reinterpret_cast<double *>(b + L.off_share);
   g.diag = reinterpret_cast<unsigned long long *>(b + L.off_diag);
   g.kappa_part = reinterpret_cast<double *>(b + L.off_kpart);
   g.nblocks_kappa = L.nblocks_kappa;
@@ -296,7 +298,8 @@ __global__ void k_vconst(int64_t n, const double *__restrict__ nH, const double 
   if (i >= n) return;
   VConst c;
   const double nh = nH[i];
-  c.A = __dmul_rn(nh, vol[i]);
+  const double A = __dmul_rn(nh, vol[i]);
+  c.invA = A > 0.0 ? __ddiv_rn(1.0, A) : 0.0;
   c.tau_max = __dmul_rn(__dmul_rn(nh, sigma), __dmul_rn(*kappa, mean_len[i]));
   c.R0 = __dmul_rn(alpha_B, nh);
   c.flags = flags[i];

@@ -70,7 +70,13 @@ __device__ void rotate_quantise(const double R[9], const double *d, int q[3]) {
 
 __global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__restrict__ bins,
                                                   uint64_t seed, int64_t step, int unrotated,
-                                                  StepTables *__restrict__ out) {
+                                                  StepTables *__restrict__ out, int nsrc,
+                                                  const double *__restrict__ src_rate, double dt,
+                                                  double inv_punit, double *__restrict__ share) {
+  // photons each source puts in every bin this step, in stored units:
+  // ((rate dt) / n) / unit, the unit being a power of two
+  for (int s = threadIdx.x; s < nsrc; s += blockDim.x)
+    share[s] = __dmul_rn(__ddiv_rn(__dmul_rn(src_rate[s], dt), (double)nbins), inv_punit);
   __shared__ double sR[9], sRp[9];
   __shared__ int s_att;
   __shared__ int s_qn[kMaxBins][3], s_qo[kMaxBins][3];
@@ -125,38 +131,55 @@ __global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__res
 }
 
 cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
-                            int unrotated, cudaStream_t st) {
+                            int unrotated, double dt, cudaStream_t st) {
   k_rotation<<<1, 128, 0, st>>>(g.nbins, bins_dev, seed, step, unrotated,
-                                g.tabs + (unrotated ? 1 : 0));
+                                g.tabs + (unrotated ? 1 : 0), unrotated ? 0 : g.nsrc, g.src_rate, dt,
+                                1.0 / g.punit, g.src_share);
   return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------
-// Chemistry of one cell over one step; IEEE FP64 operations in the order of
-// the rate-equation update (no contraction).  Returns the transmitted fraction.
+// Chemistry of one cell over one step (Sect. 4.5): explicit subcycles at
+// constant flux F = N_in / dt; each subcycle absorbs F h (1 - e^-tau) photons
+// (one ionisation each) and transmits F h e^-tau; its length is
+// h = min(t_left, f_c / (Gamma + R)) with Gamma + R = ion / y + alpha_B n_e;
+// equilibrium (|dy| <= tol y) keeps the last subcycle's rates for the rest of
+// the step.  FP64.  One expm1 and one division per subcycle: e^-tau is
+// 1 + expm1(-tau) (its absolute error, 1e-16 of N_in, is what matters for the
+// transmitted photons), and f_c / (Gamma + R) = f_c y / (ion + R0 x y).
+// Returns the transmitted fraction f = (1/dt) sum e^-tau_k h_k.
 // ----------------------------------------------------------------------------
-__device__ double chem_cell(double &y_io, double N_in, double dt, double A, double tau_max,
-                            double R0, double fc, double tol, int max_sub, int &nsub,
-                            int &capped) {
+__device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt, double invA,
+                            double tau_max, double R0, double fc, double tol, int max_sub,
+                            int &nsub, int &capped) {
   double y = y_io;
-  const double F = __ddiv_rn(N_in, dt);
-  double t_left = dt;
-  double trans_int = 0.0;
   nsub = 0;
   capped = 0;
+  if (invA == 0.0) return 1.0;  // no atoms: transparent, nothing to ionise
+  const double F = __dmul_rn(N_in, inv_dt);
+  double t_left = dt;
+  double trans_int = 0.0;
   while (t_left > 0.0) {
-    const double tau = __dmul_rn(tau_max, y);
-    const double tr = exp(-tau);
-    const double ab = -expm1(-tau);
-    const double ion = __ddiv_rn(__dmul_rn(F, ab), A);
+    const double em = expm1(-__dmul_rn(tau_max, y));
+    const double ab = -em;                   // absorbed fraction
+    const double tr = __dadd_rn(1.0, em);    // transmitted fraction
+    const double ion = __dmul_rn(__dmul_rn(F, ab), invA);  // photoionisations per atom per s
     const double x = __dsub_rn(1.0, y);
-    const double rec = __dmul_rn(__dmul_rn(R0, x), x);
-    const double gam = (y > 0.0) ? __ddiv_rn(ion, y) : __ddiv_rn(__dmul_rn(F, tau_max), A);
-    const double rate = __dadd_rn(gam, __dmul_rn(R0, x));
+    const double r0x = __dmul_rn(R0, x);
+    const double rec = __dmul_rn(r0x, x);    // recombinations per atom per s
     double h = t_left;
-    if (rate > 0.0) {
-      const double hc = __ddiv_rn(fc, rate);
-      if (hc < h) h = hc;
+    if (y > 0.0) {
+      const double den = __dadd_rn(ion, __dmul_rn(r0x, y));
+      if (den > 0.0) {
+        const double hc = __ddiv_rn(__dmul_rn(fc, y), den);
+        if (hc < h) h = hc;
+      }
+    } else {
+      const double rate = __dadd_rn(__dmul_rn(__dmul_rn(F, tau_max), invA), r0x);
+      if (rate > 0.0) {
+        const double hc = __ddiv_rn(fc, rate);
+        if (hc < h) h = hc;
+      }
     }
     const double y_new = __dadd_rn(y, __dmul_rn(__dsub_rn(rec, ion), h));
     trans_int = __dadd_rn(trans_int, __dmul_rn(tr, h));
@@ -171,7 +194,7 @@ __device__ double chem_cell(double &y_io, double N_in, double dt, double A, doub
     }
   }
   y_io = y;
-  return __ddiv_rn(trans_int, dt);
+  return __dmul_rn(trans_int, inv_dt);
 }
 
 // ----------------------------------------------------------------------------
@@ -218,9 +241,8 @@ __device__ __forceinline__ void acc_add<float>(float &acc, float &c, float x) {
 struct StepArgs {
   int64_t n;
   int nbins, nbp;
-  double dt;
+  double dt, inv_dt;
   double punit;      // photons per stored unit (a power of two; 1 in FP64 mode)
-  double inv_punit;
   double fc, tol;
   int max_sub;
   const int32_t *__restrict__ row_ptr;
@@ -232,28 +254,51 @@ struct StepArgs {
   const uint32_t *__restrict__ M_prev;
   uint32_t *__restrict__ M_next;
   const StepTables *__restrict__ tab;
-  const double *__restrict__ src_rate;
+  const double *__restrict__ src_share;
   double *__restrict__ partials;
   unsigned long long *__restrict__ diag;
 };
 
+// Row stride (elements) of the shared photon tile: odd, so that a lane per
+// vertex walking its own row touches 32 distinct banks.
+__host__ __device__ __forceinline__ int tile_stride(int nbins) { return nbins | 1; }
+
+template <typename T>
+struct Acc;  // per-lane budget accumulator: FP64 sum, or float-float in FP32 mode
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ void add(double x) { v = __dadd_rn(v, x); }
+  __device__ double warp_total() { return warp_sum_d(v); }
+};
+template <>
+struct Acc<float> {
+  FF v{0.f, 0.f};
+  __device__ void add(float x) { v = ff_add(v, x); }
+  __device__ double warp_total() { return ff_to_double(ff_warp_sum(v)); }
+};
+
+#ifndef SX_STEP_MIN_BLOCKS
+#define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
+#endif
 template <typename T, int MW>
-__global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][nbp]
+  T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][tile_stride(nbins)]
   __shared__ float4 s_qb[kMaxBins];
   __shared__ int32_t s_inv_off[kMaxBins + 1];
   __shared__ int32_t s_inv_idx[kMaxBins];
-  __shared__ double s_Nin[kTile];
   __shared__ double s_f[kTile];
   __shared__ float4 s_eq[kWarps][kMaxDeg];
   __shared__ uint32_t s_am[kWarps][kMaxDeg][MW];
+  __shared__ T s_P[kWarps][kMaxBins];
+  __shared__ unsigned char s_act[kWarps][kMaxBins];
   __shared__ double s_bud[kWarps][3];
-  __shared__ double s_sink_esc;
   __shared__ int s_remap;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nbins = a.nbins, nbp = a.nbp;
+  const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
+  const int nwords = (nbins + 31) >> 5;
   for (int b = tid; b < nbins; b += kThreads) {
     s_qb[b] = a.tab->qb[b];
     s_inv_idx[b] = a.tab->inv_idx[b];
@@ -266,20 +311,17 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   const T *__restrict__ Pp = static_cast<const T *>(a.P_prev);
   T *__restrict__ Pn = static_cast<T *>(a.P_next);
 
-  // ---------------- phase 1: gather, remap, sources, N_in ----------------
+  // ---------------- phase 1: gather, remap, sources ----------------
   for (int vl = warp; vl < kTile; vl += kWarps) {
     const int64_t v = v0 + vl;
-    T *row = s_I + (size_t)vl * nbp;
-    if (v >= a.n) {
-      if (lane == 0) s_Nin[vl] = 0.0;
-      continue;
-    }
+    if (v >= a.n) break;
+    T *row = s_I + (size_t)vl * nbs;
     T acc[MW], cmp[MW];
 #pragma unroll
     for (int w = 0; w < MW; ++w) acc[w] = cmp[w] = T(0);
     const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
     for (int32_t e0 = r0; e0 < r1; e0 += 32) {
-      // lane k fetches the reverse edge and source of in-edge e0 + k
+      // lane k fetches in-edge e0 + k: its source and the sender's bin mask
       int32_t my_src = 0;
       uint32_t my_m[MW];
 #pragma unroll
@@ -289,30 +331,35 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         my_src = E.col;
         load_mask<MW>(a.M_prev, E.twin, my_m);
       }
-      const int cnt = min(32, r1 - e0);
-      for (int k = 0; k < cnt; ++k) {
+      uint32_t any = 0u;
+#pragma unroll
+      for (int w = 0; w < MW; ++w) any |= my_m[w];
+      // in-edges that carry photons, in the fixed (ascending source) order
+      uint32_t live = __ballot_sync(0xffffffffu, any != 0u);
+      while (live) {
+        const int k = __ffs(live) - 1;
+        live &= live - 1u;
         const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
         const T *__restrict__ Ps = Pp + (size_t)src * nbp;
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
-          const uint32_t mw = __shfl_sync(0xffffffffu, my_m[w], k);
-          const int b = lane + 32 * w;
-          if ((mw >> lane) & 1u) acc_add<T>(acc[w], cmp[w], Ps[b]);
+          if (w < nwords) {
+            const uint32_t mw = __shfl_sync(0xffffffffu, my_m[w], k);
+            if (mw != 0u && ((mw >> lane) & 1u)) acc_add<T>(acc[w], cmp[w], Ps[lane + 32 * w]);
+          }
         }
       }
     }
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
       const int b = lane + 32 * w;
-      if (b < nbp) row[b] = (b < nbins) ? acc[w] : T(0);
+      if (b < nbins) row[b] = acc[w];
     }
     __syncwarp();
     // move packets to the closest bin of this step's orientation, add sources
     T nv[MW];
     const int src = a.vc[v].src;
-    const double share =
-        src >= 0 ? __dmul_rn(__ddiv_rn(__dmul_rn(a.src_rate[src], a.dt), (double)nbins), a.inv_punit)
-                 : 0.0;
+    const T share = src >= 0 ? (T)a.src_share[src] : T(0);
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
       const int b = lane + 32 * w;
@@ -323,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         } else {
           s = row[b];
         }
-        if (src >= 0) s = s + (T)share;
+        if (src >= 0) s = s + share;
       }
       nv[w] = s;
     }
@@ -333,42 +380,44 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       const int b = lane + 32 * w;
       if (b < nbins) row[b] = nv[w];
     }
-    __syncwarp();
-    if constexpr (sizeof(T) == 8) {
-      // FP64: sequential sum over bins, the order of the plain definition
-      if (lane == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nbins; ++b) s = __dadd_rn(s, (double)row[b]);
-        s_Nin[vl] = s;
-      }
-    } else {
-      FF s{0.f, 0.f};
-#pragma unroll
-      for (int w = 0; w < MW; ++w) s = ff_add(s, (float)nv[w]);
-      s = ff_warp_sum(s);
-      if (lane == 0) s_Nin[vl] = ff_to_double(s);
-    }
   }
   __syncthreads();
 
-  // ---------------- phase 2: chemistry, lane per vertex ----------------
-  if (warp == 0) {
-    const int64_t v = v0 + lane;
-    double f = 0.0, sink_esc = 0.0;
+  // ---------------- phase 2: N_in and chemistry, lane per vertex ----------------
+  double bud_abs = 0.0, bud_sink = 0.0;
+  if (warp < kTile / 32) {
+    const int vl = warp * 32 + lane;
+    const int64_t v = v0 + vl;
+    double f = 0.0;
     int nsub = 0, capped = 0;
     if (v < a.n) {
+      const T *row = s_I + (size_t)vl * nbs;
+      double nin;  // stored photon units
+      if constexpr (sizeof(T) == 8) {
+        double s = 0.0;  // ascending bins: the order of the plain definition
+        for (int b = 0; b < nbins; ++b) s = __dadd_rn(s, (double)row[b]);
+        nin = s;
+      } else {
+        FF s{0.f, 0.f};
+        for (int b = 0; b < nbins; ++b) s = ff_add(s, (float)row[b]);
+        nin = ff_to_double(s);
+      }
       const VConst c = a.vc[v];
-      const double Nin = __dmul_rn(s_Nin[lane], a.punit);  // photons
       if (c.flags & 1) {
-        sink_esc = s_Nin[lane];  // stored units, like every budget partial
+        bud_sink = nin;  // a sink passes nothing on
       } else {
         double yv = a.y[v];
-        f = chem_cell(yv, Nin, a.dt, c.A, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub, capped);
-        a.y[v] = yv;
+        if (nin == 0.0 && yv == 1.0) {
+          f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
+        } else {
+          f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0, a.fc,
+                        a.tol, a.max_sub, nsub, capped);
+          a.y[v] = yv;
+        }
+        bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
       }
     }
-    s_f[lane] = f;
-    sink_esc = warp_sum_d(sink_esc);
+    s_f[vl] = f;
     unsigned ns = (unsigned)nsub, nc = (unsigned)capped;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -376,7 +425,6 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
       nc += __shfl_down_sync(0xffffffffu, nc, d);
     }
     if (lane == 0) {
-      s_sink_esc = sink_esc;
       if (ns) atomicAdd(&a.diag[kDiagSubcycles], (unsigned long long)ns);
       if (nc) atomicAdd(&a.diag[kDiagCapped], (unsigned long long)nc);
     }
@@ -384,28 +432,20 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
   __syncthreads();
 
   // ---------------- phase 3: transmit, associate, route ----------------
-  double w_abs = 0.0, w_esc = 0.0, w_fly = 0.0;  // lane 0 of each warp
+  Acc<T> fly, esc;
   for (int vl = warp; vl < kTile; vl += kWarps) {
     const int64_t v = v0 + vl;
-    if (v >= a.n) continue;
-    const T *row = s_I + (size_t)vl * nbp;
+    if (v >= a.n) break;
+    const T *row = s_I + (size_t)vl * nbs;
     T *__restrict__ Pv = Pn + (size_t)v * nbp;
     const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
     const int deg = r1 - r0;
     const int flags = a.vc[v].flags;
-    const double Nin = s_Nin[vl];
+    const T f = (T)s_f[vl];
     if ((flags & 1) || deg == 0 || deg > kMaxDeg) {
       // sinks pass nothing on; a vertex without edges loses what it transmits
-      double esc = 0.0;
-      if (!(flags & 1)) {
-        const T f = (T)s_f[vl];
-        double o = 0.0;
-        for (int b = lane; b < nbins; b += 32) o += (double)(row[b] * f);
-        o = warp_sum_d(o);
-        esc = o;
-        if (lane == 0) w_abs += Nin - o;
-      }
-      if (lane == 0) w_esc += esc;
+      if (!(flags & 1))
+        for (int b = lane; b < nbins; b += 32) esc.add(row[b] * f);
       for (int b = lane; b < nbp; b += 32) Pv[b] = T(0);
       for (int k = lane; k < deg; k += 32) {
         uint32_t z[MW];
@@ -425,20 +465,34 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
 #pragma unroll
       for (int w = 0; w < MW; ++w) s_am[warp][k][w] = 0u;
     }
-    __syncwarp();
-    const T f = (T)s_f[vl];
-    double o_sum = 0.0, o_fly = 0.0, o_esc = 0.0;
-    FF fo{0.f, 0.f}, ffly{0.f, 0.f}, fesc{0.f, 0.f};
+    // transmitted photons per bin; list the bins that carry any
+    int nact = 0;
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
-      const int b = lane + 32 * w;
-      if (b < nbins) {
-        const T O = row[b] * f;
+      if (w < nwords) {
+        const int b = lane + 32 * w;
+        T O = T(0);
+        if (b < nbins) O = row[b] * f;
+        const bool on = O != T(0);
+        const uint32_t bal = __ballot_sync(0xffffffffu, on);
+        if (on) s_act[warp][nact + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)b;
+        if (b < nbins) s_P[warp][b] = O;
+        nact += __popc(bal);
+      }
+    }
+    __syncwarp();
+    // association and routing of the bins that carry photons (an empty bin
+    // routes nothing: its mask bits stay clear and its stored value is zero)
+    for (int j0 = 0; j0 < nact; j0 += 32) {
+      const int j = j0 + lane;
+      if (j < nact) {
+        const int b = s_act[warp][j];
+        const T O = s_P[warp][b];
         const float4 qb = s_qb[b];
         float best = -FLT_MAX;
         for (int k = 0; k < deg; ++k) {
           const float4 qe = s_eq[warp][k];
-          // (q_e . q_b) * 256 + (255 - k): exact integer in FP32; the max
+          // (q_e . q_b) * 256 + (255 - k): an exact integer in FP32; the max
           // picks the largest dot and, among equal dots, the lowest slot
           const float d = fmaf(qe.x, qb.x, fmaf(qe.y, qb.y, fmaf(qe.z, qb.z, (float)(255 - k))));
           best = fmaxf(best, d);
@@ -448,52 +502,43 @@ __global__ void __launch_bounds__(kThreads) k_step(const StepArgs a) {
         const int cnt = (int)(stw >> 24);
         T P = T(0);
         if (cnt == 0) {
-          if constexpr (sizeof(T) == 8) o_esc += (double)O; else fesc = ff_add(fesc, (float)O);
+          esc.add(O);
         } else {
-          P = O / (T)cnt;
-          if constexpr (sizeof(T) == 8) o_fly += (double)O; else ffly = ff_add(ffly, (float)O);
-          for (int j = 0; j < cnt; ++j) {
-            const int s = (int)((stw >> (8 * j)) & 0xFFu);
-            atomicOr(&s_am[warp][s][w], 1u << lane);
+          if constexpr (sizeof(T) == 8) {
+            P = O / (T)cnt;
+          } else {
+            P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
           }
+          fly.add(O);
+          const uint32_t bit = 1u << (b & 31);
+          for (int m = 0; m < cnt; ++m) atomicOr(&s_am[warp][(stw >> (8 * m)) & 0xFFu][b >> 5], bit);
         }
-        if constexpr (sizeof(T) == 8) o_sum += (double)O; else fo = ff_add(fo, (float)O);
-        Pv[b] = P;
-      } else if (b < nbp) {
-        Pv[b] = T(0);
+        s_P[warp][b] = P;
       }
     }
     __syncwarp();
+    for (int b = lane; b < nbp; b += 32) Pv[b] = (b < nbins) ? s_P[warp][b] : T(0);
     for (int k = lane; k < deg; k += 32) {
       uint32_t m[MW];
 #pragma unroll
       for (int w = 0; w < MW; ++w) m[w] = s_am[warp][k][w];
       store_mask<MW>(a.M_next, (int64_t)r0 + k, m);
     }
-    if constexpr (sizeof(T) == 8) {
-      o_sum = warp_sum_d(o_sum);
-      o_fly = warp_sum_d(o_fly);
-      o_esc = warp_sum_d(o_esc);
-    } else {
-      o_sum = ff_to_double(ff_warp_sum(fo));
-      o_fly = ff_to_double(ff_warp_sum(ffly));
-      o_esc = ff_to_double(ff_warp_sum(fesc));
-    }
-    if (lane == 0) {
-      w_abs += Nin - o_sum;
-      w_fly += o_fly;
-      w_esc += o_esc;
-    }
     __syncwarp();
   }
+  // ---------------- budget partials of the tile ----------------
+  const double t_abs = warp_sum_d(bud_abs);
+  const double t_sink = warp_sum_d(bud_sink);
+  const double t_fly = fly.warp_total();
+  const double t_esc = esc.warp_total();
   if (lane == 0) {
-    s_bud[warp][0] = w_abs;
-    s_bud[warp][1] = w_esc;
-    s_bud[warp][2] = w_fly;
+    s_bud[warp][0] = t_abs;
+    s_bud[warp][1] = __dadd_rn(t_sink, t_esc);
+    s_bud[warp][2] = t_fly;
   }
   __syncthreads();
   if (tid == 0) {
-    double ab = 0.0, es = s_sink_esc, fl = 0.0;
+    double ab = 0.0, es = 0.0, fl = 0.0;
     for (int w = 0; w < kWarps; ++w) {
       ab += s_bud[w][0];
       es += s_bud[w][1];
@@ -514,8 +559,8 @@ static cudaError_t launch_step_t(DevGrid &g, int64_t step, double dt, double fc,
   a.nbins = g.nbins;
   a.nbp = g.nbp;
   a.dt = dt;
+  a.inv_dt = 1.0 / dt;
   a.punit = g.punit;
-  a.inv_punit = 1.0 / g.punit;
   a.fc = fc;
   a.tol = tol;
   a.max_sub = max_sub;
@@ -529,10 +574,10 @@ static cudaError_t launch_step_t(DevGrid &g, int64_t step, double dt, double fc,
   a.M_prev = g.M[prev];
   a.M_next = g.M[cur];
   a.tab = g.tabs;
-  a.src_rate = g.src_rate;
+  a.src_share = g.src_share;
   a.partials = g.partials;
   a.diag = g.diag;
-  const size_t smem = sizeof(T) * (size_t)kTile * g.nbp;
+  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_step<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);

@@ -214,6 +214,35 @@ def stromgren_problem(n_interior: int = 8192, box_kpc: float = 13.2, nH: float =
                              rate=rate, seed=seed, corner_source=corner_source))
 
 
+def cached(recipe, *args, cache_dir: str | None = None, **kw) -> Problem:
+    """``recipe(*args, **kw)``, memoised as an .npz in ``cache_dir`` (or in the
+    directory named by $SX_GRID_CACHE; no caching if neither is set)."""
+    import hashlib
+    import json
+    import os
+
+    cache_dir = cache_dir or os.environ.get("SX_GRID_CACHE")
+    if not cache_dir:
+        return recipe(*args, **kw)
+    key = hashlib.sha1(json.dumps([recipe.__name__, args, kw], sort_keys=True, default=str)
+                       .encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir, f"grid_{key}.npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return Problem(pos=z["pos"], row_ptr=z["row_ptr"], col=z["col"], nH=z["nH"],
+                       volume=z["volume"], flags=z["flags"], src_vertex=z["src_vertex"],
+                       src_rate=z["src_rate"], box=float(z["box"]),
+                       meta=json.loads(str(z["meta"])))
+    p = recipe(*args, **kw)
+    os.makedirs(cache_dir, exist_ok=True)
+    tmp = path + f".tmp{os.getpid()}.npz"
+    np.savez(tmp, pos=p.pos, row_ptr=p.row_ptr, col=p.col, nH=p.nH, volume=p.volume,
+             flags=p.flags, src_vertex=p.src_vertex, src_rate=p.src_rate, box=p.box,
+             meta=json.dumps(p.meta))
+    os.replace(tmp, path)
+    return p
+
+
 def point_process_problem(points: np.ndarray, nH, sink_mask=None, sources=()) -> Problem:
     """Wrap an explicit point set (tests): Delaunay graph + uniform volumes."""
     pts = np.ascontiguousarray(points, dtype=np.float64)

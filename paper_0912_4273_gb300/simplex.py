@@ -51,7 +51,8 @@ class sx_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("step", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("kappa", C.c_double),
                 ("subcycles", C.c_int64), ("capped", C.c_int64), ("max_degree", C.c_int32),
-                ("nsources", C.c_int32)]
+                ("nsources", C.c_int32), ("step_kernel_ms", C.c_double),
+                ("step_kernel_launches", C.c_int64)]
 
 
 _LIB = None
@@ -72,13 +73,15 @@ _SIGS = [
     ("sx_read_neutral_fraction", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
     ("sx_get_info", C.c_int, [C.c_void_p, _P(sx_info)]),
+    ("sx_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("sx_destroy", None, [C.c_void_p]),
     ("sx_last_error", C.c_char_p, [C.c_void_p]),
 ]
 
 
 def library_path() -> str:
-    return _build.lib_path()
+    """The in-tree build, unless $SIMPLEXGB_LIBRARY names another build of it."""
+    return os.environ.get("SIMPLEXGB_LIBRARY") or _build.lib_path()
 
 
 def lib():
@@ -168,6 +171,10 @@ def sx_get_info(ctx) -> sx_info:
     info = sx_info()
     _check(ctx, lib().sx_get_info(ctx, C.byref(info)))
     return info
+
+
+def sx_profile(ctx, enable: bool):
+    _check(ctx, lib().sx_profile(ctx, 1 if enable else 0))
 
 
 def sx_destroy(ctx):
@@ -268,6 +275,9 @@ class Solver:
         out = np.empty(self.n, dtype=np.float64)
         sx_read_photons(self.ctx, out)
         return out
+
+    def profile(self, enable: bool = True):
+        sx_profile(self.ctx, enable)
 
     @property
     def info(self) -> dict:

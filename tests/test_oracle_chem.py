@@ -95,3 +95,9 @@ def test_random_inputs_stay_physical():
 def test_no_photons_no_ions_is_a_fixed_point():
     y1, f, nsub, _ = O.chem(1.0, 0.0, 1e13, 1e58, 3.0, R0)
     assert y1 == 1.0 and nsub == 1
+
+
+def test_empty_cell_is_transparent():
+    """n_H = 0: tau = n_H sigma dL = 0 (Eq. optical_depth), nothing absorbed."""
+    y1, f, nsub, _ = O.chem(0.7, 1e55, 1e13, 0.0, 0.0, 0.0)
+    assert f == 1.0 and y1 == 0.7 and nsub == 0
