@@ -8,7 +8,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/simplexgb.h"
+#include "simplexgb.h"
 #include "sx_internal.cuh"
 
 struct sx_ctx {

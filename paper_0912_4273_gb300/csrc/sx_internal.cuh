@@ -39,8 +39,10 @@ struct StepTables {
   float4 qb[kMaxBins];            // quantised rotated bins (x, y, z), as exact floats
   int32_t inv_off[kMaxBins + 1];  // packets of old bins inv_idx[inv_off[b]..inv_off[b+1])
   int32_t inv_idx[kMaxBins];      //   move to new bin b (ascending old index)
+  uchar4 inv3[kMaxBins];          // the same as up to 3 old bins per new bin, missing = kMaxBins
   int32_t attempts;
   int32_t remap;                  // 0: step 0, no previous orientation
+  int32_t max_fanin;              // largest number of old bins moving into one new bin
 };
 
 enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagCount = 8 };
@@ -135,6 +137,7 @@ struct DevGrid {
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
   double *src_rate;     // kMaxSources
   double *src_share;    // kMaxSources: photons per bin per step of each source, stored units
+  float *src_share_f;   // the same in FP32
   int nsrc;
   unsigned long long *diag;  // kDiagCount
   double *kappa_part;   // nblocks_kappa*2
@@ -152,7 +155,7 @@ struct DevGrid {
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
-      off_M1, off_partials, off_tabs, off_src, off_share, off_diag, off_kpart, off_kappa, off_budget,
+      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       total;
   int64_t nblocks, nblocks_kappa;

@@ -72,11 +72,14 @@ __global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__res
                                                   uint64_t seed, int64_t step, int unrotated,
                                                   StepTables *__restrict__ out, int nsrc,
                                                   const double *__restrict__ src_rate, double dt,
-                                                  double inv_punit, double *__restrict__ share) {
+                                                  double inv_punit, double *__restrict__ share,
+                                                  float *__restrict__ share_f) {
   // photons each source puts in every bin this step, in stored units:
   // ((rate dt) / n) / unit, the unit being a power of two
-  for (int s = threadIdx.x; s < nsrc; s += blockDim.x)
+  for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
     share[s] = __dmul_rn(__ddiv_rn(__dmul_rn(src_rate[s], dt), (double)nbins), inv_punit);
+    share_f[s] = (float)share[s];
+  }
   __shared__ double sR[9], sRp[9];
   __shared__ int s_att;
   __shared__ int s_qn[kMaxBins][3], s_qo[kMaxBins][3];
@@ -118,15 +121,24 @@ __global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__res
   }
   __syncthreads();
   if (t == 0) {
-    int o = 0;
+    int o = 0, mx = 0;
     for (int b2 = 0; b2 < nbins; ++b2) {
       out->inv_off[b2] = o;
+      unsigned char i3[3] = {kMaxBins, kMaxBins, kMaxBins};
+      int c = 0;
       for (int b = 0; b < nbins; ++b)
-        if (s_map[b] == b2) out->inv_idx[o++] = b;
+        if (s_map[b] == b2) {
+          if (c < 3) i3[c] = (unsigned char)b;
+          c++;
+          out->inv_idx[o++] = b;
+        }
+      out->inv3[b2] = make_uchar4(i3[0], i3[1], i3[2], (unsigned char)c);
+      mx = c > mx ? c : mx;
     }
     out->inv_off[nbins] = o;
     out->attempts = s_att;
     out->remap = (!unrotated && step > 0) ? 1 : 0;
+    out->max_fanin = mx;
   }
 }
 
@@ -134,7 +146,7 @@ cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, i
                             int unrotated, double dt, cudaStream_t st) {
   k_rotation<<<1, 128, 0, st>>>(g.nbins, bins_dev, seed, step, unrotated,
                                 g.tabs + (unrotated ? 1 : 0), unrotated ? 0 : g.nsrc, g.src_rate, dt,
-                                1.0 / g.punit, g.src_share);
+                                1.0 / g.punit, g.src_share, g.src_share_f);
   return cudaGetLastError();
 }
 
@@ -255,6 +267,7 @@ struct StepArgs {
   uint32_t *__restrict__ M_next;
   const StepTables *__restrict__ tab;
   const double *__restrict__ src_share;
+  const float *__restrict__ src_share_f;
   double *__restrict__ partials;
   unsigned long long *__restrict__ diag;
 };
@@ -263,20 +276,27 @@ struct StepArgs {
 // vertex walking its own row touches 32 distinct banks.
 __host__ __device__ __forceinline__ int tile_stride(int nbins) { return nbins | 1; }
 
+// Per-lane budget accumulator: FP64 sum, or float-float in FP32 mode (the
+// FP64 pipe is narrow, so FP32-mode tiles combine their partial sums in
+// float-float and convert once).
 template <typename T>
-struct Acc;  // per-lane budget accumulator: FP64 sum, or float-float in FP32 mode
+struct Acc;
 template <>
 struct Acc<double> {
   double v = 0.0;
   __device__ void add(double x) { v = __dadd_rn(v, x); }
-  __device__ double warp_total() { return warp_sum_d(v); }
 };
 template <>
 struct Acc<float> {
   FF v{0.f, 0.f};
   __device__ void add(float x) { v = ff_add(v, x); }
-  __device__ double warp_total() { return ff_to_double(ff_warp_sum(v)); }
 };
+
+// Exact int -> float for |i| < 2^22 without the conversion unit: the integer
+// is placed in the mantissa of 2^23 and 2^23 is subtracted.
+__device__ __forceinline__ float small_int_to_float(int i) {
+  return __int_as_float(0x4B000000 | (i + 0x200000)) - 8388608.f - 2097152.f;
+}
 
 #ifndef SX_STEP_MIN_BLOCKS
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
@@ -288,13 +308,19 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
   __shared__ float4 s_qb[kMaxBins];
   __shared__ int32_t s_inv_off[kMaxBins + 1];
   __shared__ int32_t s_inv_idx[kMaxBins];
-  __shared__ double s_f[kTile];
-  __shared__ float4 s_eq[kWarps][kMaxDeg];
-  __shared__ uint32_t s_am[kWarps][kMaxDeg][MW];
-  __shared__ T s_P[kWarps][kMaxBins];
-  __shared__ unsigned char s_act[kWarps][kMaxBins];
-  __shared__ double s_bud[kWarps][3];
-  __shared__ int s_remap;
+  __shared__ uchar4 s_inv3[kMaxBins];
+  __shared__ T s_f[kTile];
+  __shared__ uint32_t s_occ[kTile][MW];
+  __shared__ T s_budw[kWarps][4];  // per warp: fly hi/lo, esc hi/lo (FP32) or fly, esc (FP64)
+  __shared__ double s_abs, s_sink;
+  __shared__ int s_remap, s_fanin;
+  // Per-warp scratch, used by phase 1 (bin accumulators and the contribution
+  // list) and, after the barrier, by phase 3 (staged edges, masks, bin list).
+  constexpr int kLcap = 64;
+  constexpr int kScr1 = 2 * (kMaxBins + 1) * (int)sizeof(T) + kLcap * 4 + kLcap;
+  constexpr int kScr3 = kMaxDeg * 16 + kMaxDeg * 4 + kMaxDeg * MW * 4 + kMaxBins;
+  constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
+  __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
@@ -304,7 +330,11 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
     s_inv_idx[b] = a.tab->inv_idx[b];
   }
   for (int b = tid; b <= nbins; b += kThreads) s_inv_off[b] = a.tab->inv_off[b];
-  if (tid == 0) s_remap = a.tab->remap;
+  for (int b = tid; b < nbins; b += kThreads) s_inv3[b] = a.tab->inv3[b];
+  if (tid == 0) {
+    s_remap = a.tab->remap;
+    s_fanin = a.tab->max_fanin;
+  }
   __syncthreads();
 
   const int64_t v0 = (int64_t)blockIdx.x * kTile;
@@ -312,73 +342,136 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
   T *__restrict__ Pn = static_cast<T *>(a.P_next);
 
   // ---------------- phase 1: gather, remap, sources ----------------
-  for (int vl = warp; vl < kTile; vl += kWarps) {
-    const int64_t v = v0 + vl;
-    if (v >= a.n) break;
-    T *row = s_I + (size_t)vl * nbs;
-    T acc[MW], cmp[MW];
-#pragma unroll
-    for (int w = 0; w < MW; ++w) acc[w] = cmp[w] = T(0);
-    const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
-    for (int32_t e0 = r0; e0 < r1; e0 += 32) {
-      // lane k fetches in-edge e0 + k: its source and the sender's bin mask
-      int32_t my_src = 0;
-      uint32_t my_m[MW];
-#pragma unroll
-      for (int w = 0; w < MW; ++w) my_m[w] = 0u;
-      if (e0 + lane < r1) {
-        const Edge E = a.edges[e0 + lane];
-        my_src = E.col;
-        load_mask<MW>(a.M_prev, E.twin, my_m);
+  {
+    T *acc_s = reinterpret_cast<T *>(s_scr[warp]);  // [kMaxBins + 1], old orientation
+    T *cmp_s = acc_s + (kMaxBins + 1);                 // Kahan compensation
+    int32_t *lsrc = reinterpret_cast<int32_t *>(cmp_s + (kMaxBins + 1));
+    unsigned char *lbin = reinterpret_cast<unsigned char *>(lsrc + kLcap);
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int vl = warp; vl < kTile; vl += kWarps) {
+      const int64_t v = v0 + vl;
+      if (v >= a.n) break;
+      for (int b = lane; b <= kMaxBins; b += 32) {
+        acc_s[b] = T(0);
+        cmp_s[b] = T(0);
       }
-      uint32_t any = 0u;
+      __syncwarp();
+      const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
+      for (int32_t e0 = r0; e0 < r1; e0 += 32) {
+        // lane k fetches in-edge e0 + k: its source and the sender's bin mask
+        int32_t my_src = 0;
+        uint32_t my_m[MW];
 #pragma unroll
-      for (int w = 0; w < MW; ++w) any |= my_m[w];
-      // in-edges that carry photons, in the fixed (ascending source) order
-      uint32_t live = __ballot_sync(0xffffffffu, any != 0u);
-      while (live) {
-        const int k = __ffs(live) - 1;
-        live &= live - 1u;
-        const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
-        const T *__restrict__ Ps = Pp + (size_t)src * nbp;
+        for (int w = 0; w < MW; ++w) my_m[w] = 0u;
+        if (e0 + lane < r1) {
+          const Edge E = a.edges[e0 + lane];
+          my_src = E.col;
+          load_mask<MW>(a.M_prev, E.twin, my_m);
+        }
+        int cnt = 0;
 #pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          if (w < nwords) {
-            const uint32_t mw = __shfl_sync(0xffffffffu, my_m[w], k);
-            if (mw != 0u && ((mw >> lane) & 1u)) acc_add<T>(acc[w], cmp[w], Ps[lane + 32 * w]);
+        for (int w = 0; w < MW; ++w) cnt += __popc(my_m[w]);
+        int incl = cnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        if (total <= kLcap) {
+          // contribution list (source, bin) in (edge, bin) order; the loads
+          // are independent, and the adds run in rounds of equal rank within
+          // a bin, so every bin sums its contributions in ascending edge order
+          int pos = incl - cnt;
+#pragma unroll
+          for (int w = 0; w < MW; ++w) {
+            uint32_t m = my_m[w];
+            while (m) {
+              const int i = __ffs(m) - 1;
+              m &= m - 1u;
+              lsrc[pos] = my_src;
+              lbin[pos] = (unsigned char)(32 * w + i);
+              ++pos;
+            }
           }
-        }
-      }
-    }
-#pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      const int b = lane + 32 * w;
-      if (b < nbins) row[b] = acc[w];
-    }
-    __syncwarp();
-    // move packets to the closest bin of this step's orientation, add sources
-    T nv[MW];
-    const int src = a.vc[v].src;
-    const T share = src >= 0 ? (T)a.src_share[src] : T(0);
-#pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      const int b = lane + 32 * w;
-      T s = T(0);
-      if (b < nbins) {
-        if (s_remap) {
-          for (int j = s_inv_off[b]; j < s_inv_off[b + 1]; ++j) s = s + row[s_inv_idx[j]];
+          __syncwarp();
+          for (int j0 = 0; j0 < total; j0 += 32) {
+            const int j = j0 + lane;
+            const bool on = j < total;
+            const int b = on ? (int)lbin[j] : (kMaxBins + 1 + lane);  // idle lanes: unique keys
+            T val = T(0);
+            if (on) val = Pp[(size_t)lsrc[j] * nbp + b];
+            const uint32_t grp = __match_any_sync(0xffffffffu, b);
+            const unsigned rank = __popc(grp & lt_mask);
+            const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
+            for (unsigned r = 0; r <= maxr; ++r) {
+              if (on && rank == r) {
+                T A = acc_s[b], Cc = cmp_s[b];
+                acc_add<T>(A, Cc, val);
+                acc_s[b] = A;
+                cmp_s[b] = Cc;
+              }
+              __syncwarp();
+            }
+          }
+          __syncwarp();
         } else {
-          s = row[b];
-        }
-        if (src >= 0) s = s + share;
-      }
-      nv[w] = s;
-    }
-    __syncwarp();
+          // many contributions: lane per bin, one in-edge after the other
+          uint32_t my_wm = 0u;
 #pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      const int b = lane + 32 * w;
-      if (b < nbins) row[b] = nv[w];
+          for (int w = 0; w < MW; ++w) my_wm |= (my_m[w] != 0u ? 1u : 0u) << w;
+          uint32_t live = __ballot_sync(0xffffffffu, my_wm != 0u);
+          while (live) {
+            const int k = __ffs(live) - 1;
+            live &= live - 1u;
+            const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
+            const T *__restrict__ Ps = Pp + (size_t)src * nbp;
+#pragma unroll
+            for (int w = 0; w < MW; ++w) {
+              if (w < nwords) {
+                const uint32_t mw = __shfl_sync(0xffffffffu, my_m[w], k);
+                if ((mw >> lane) & 1u) {
+                  const int b = lane + 32 * w;
+                  T A = acc_s[b], Cc = cmp_s[b];
+                  acc_add<T>(A, Cc, Ps[b]);
+                  acc_s[b] = A;
+                  cmp_s[b] = Cc;
+                }
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      // move packets to the closest bin of this step's orientation (old bins
+      // in ascending order, as the plain definition adds them), add sources
+      T *row = s_I + (size_t)vl * nbs;
+      const int src = a.vc[v].src;
+      T share = T(0);
+      if (src >= 0) {
+        if constexpr (sizeof(T) == 8) share = a.src_share[src]; else share = a.src_share_f[src];
+      }
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        const int b = lane + 32 * w;
+        T s = T(0);
+        if (b < nbins) {
+          if (!s_remap) {
+            s = acc_s[b];
+          } else if (s_fanin <= 3) {
+            const uchar4 i3 = s_inv3[b];
+            s = (acc_s[i3.x] + acc_s[i3.y]) + acc_s[i3.z];
+          } else {
+            for (int j = s_inv_off[b]; j < s_inv_off[b + 1]; ++j) s = s + acc_s[s_inv_idx[j]];
+          }
+          if (src >= 0) s = s + share;
+          row[b] = s;
+        }
+        const uint32_t occ = __ballot_sync(0xffffffffu, s != T(0));
+        if (lane == 0) s_occ[vl][w] = occ;  // bins of the vertex that hold photons
+      }
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -392,14 +485,32 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
     int nsub = 0, capped = 0;
     if (v < a.n) {
       const T *row = s_I + (size_t)vl * nbs;
+      // sum over the occupied bins in ascending order (adding the empty ones
+      // would not change a bit of it)
       double nin;  // stored photon units
       if constexpr (sizeof(T) == 8) {
-        double s = 0.0;  // ascending bins: the order of the plain definition
-        for (int b = 0; b < nbins; ++b) s = __dadd_rn(s, (double)row[b]);
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          uint32_t m = s_occ[vl][w];
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            s = __dadd_rn(s, (double)row[32 * w + i]);
+          }
+        }
         nin = s;
       } else {
         FF s{0.f, 0.f};
-        for (int b = 0; b < nbins; ++b) s = ff_add(s, (float)row[b]);
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          uint32_t m = s_occ[vl][w];
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            s = ff_add(s, (float)row[32 * w + i]);
+          }
+        }
         nin = ff_to_double(s);
       }
       const VConst c = a.vc[v];
@@ -417,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
         bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
       }
     }
-    s_f[vl] = f;
+    s_f[vl] = (T)f;
     unsigned ns = (unsigned)nsub, nc = (unsigned)capped;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -432,7 +543,13 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
   __syncthreads();
 
   // ---------------- phase 3: transmit, associate, route ----------------
+  // Only bins that hold photons are routed.  A bin without photons sets no
+  // mask bit, so no reader ever looks at its stored value: it is not written.
   Acc<T> fly, esc;
+  float4 *s_eq = reinterpret_cast<float4 *>(s_scr[warp]);            // [kMaxDeg]
+  uint32_t *s_st = reinterpret_cast<uint32_t *>(s_eq + kMaxDeg);     // [kMaxDeg]
+  uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_st + kMaxDeg);  // [kMaxDeg][MW]
+  unsigned char *s_act = reinterpret_cast<unsigned char *>(s_am + kMaxDeg);  // [kMaxBins]
   for (int vl = warp; vl < kTile; vl += kWarps) {
     const int64_t v = v0 + vl;
     if (v >= a.n) break;
@@ -441,12 +558,11 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
     const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
     const int deg = r1 - r0;
     const int flags = a.vc[v].flags;
-    const T f = (T)s_f[vl];
+    const T f = s_f[vl];
     if ((flags & 1) || deg == 0 || deg > kMaxDeg) {
       // sinks pass nothing on; a vertex without edges loses what it transmits
       if (!(flags & 1))
         for (int b = lane; b < nbins; b += 32) esc.add(row[b] * f);
-      for (int b = lane; b < nbp; b += 32) Pv[b] = T(0);
       for (int k = lane; k < deg; k += 32) {
         uint32_t z[MW];
 #pragma unroll
@@ -455,98 +571,116 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
       }
       continue;
     }
-    // stage the vertex's edges: q * 256 as exact floats, straight table in w
+    // stage the vertex's edges: 64 q as exact floats and 63 - k in w (the
+    // packed argmax below); the straight table apart
     for (int k = lane; k < deg; k += 32) {
       const Edge E = a.edges[r0 + k];
       uint32_t stw;
       memcpy(&stw, &E.st, 4);
-      s_eq[warp][k] = make_float4((float)E.q.x * 256.f, (float)E.q.y * 256.f,
-                                  (float)E.q.z * 256.f, __uint_as_float(stw));
+      s_eq[k] = make_float4(small_int_to_float(E.q.x) * 64.f, small_int_to_float(E.q.y) * 64.f,
+                            small_int_to_float(E.q.z) * 64.f, small_int_to_float(63 - k));
+      s_st[k] = stw;
 #pragma unroll
-      for (int w = 0; w < MW; ++w) s_am[warp][k][w] = 0u;
+      for (int w = 0; w < MW; ++w) s_am[k][w] = 0u;
     }
-    // transmitted photons per bin; list the bins that carry any
+    // list the occupied bins (ascending)
     int nact = 0;
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
-      if (w < nwords) {
-        const int b = lane + 32 * w;
-        T O = T(0);
-        if (b < nbins) O = row[b] * f;
-        const bool on = O != T(0);
-        const uint32_t bal = __ballot_sync(0xffffffffu, on);
-        if (on) s_act[warp][nact + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)b;
-        if (b < nbins) s_P[warp][b] = O;
-        nact += __popc(bal);
-      }
+      const uint32_t occ = s_occ[vl][w];
+      if ((occ >> lane) & 1u) s_act[nact + __popc(occ & ((1u << lane) - 1u))] = (unsigned char)(lane + 32 * w);
+      nact += __popc(occ);
     }
     __syncwarp();
-    // association and routing of the bins that carry photons (an empty bin
-    // routes nothing: its mask bits stay clear and its stored value is zero)
     for (int j0 = 0; j0 < nact; j0 += 32) {
       const int j = j0 + lane;
       if (j < nact) {
-        const int b = s_act[warp][j];
-        const T O = s_P[warp][b];
-        const float4 qb = s_qb[b];
-        float best = -FLT_MAX;
-        for (int k = 0; k < deg; ++k) {
-          const float4 qe = s_eq[warp][k];
-          // (q_e . q_b) * 256 + (255 - k): an exact integer in FP32; the max
-          // picks the largest dot and, among equal dots, the lowest slot
-          const float d = fmaf(qe.x, qb.x, fmaf(qe.y, qb.y, fmaf(qe.z, qb.z, (float)(255 - k))));
-          best = fmaxf(best, d);
-        }
-        const int kb = 255 - ((int)best & 255);
-        const uint32_t stw = __float_as_uint(s_eq[warp][kb].w);
-        const int cnt = (int)(stw >> 24);
-        T P = T(0);
-        if (cnt == 0) {
-          esc.add(O);
-        } else {
-          if constexpr (sizeof(T) == 8) {
-            P = O / (T)cnt;
-          } else {
-            P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
+        const int b = s_act[j];
+        const T O = row[b] * f;
+        if (O != T(0)) {
+          const float4 qb = s_qb[b];
+          float best = -FLT_MAX;
+          for (int k = 0; k < deg; ++k) {
+            const float4 qe = s_eq[k];
+            // (q_e . q_b) * 64 + (63 - k): an exact integer below 2^22 in FP32;
+            // the max picks the largest dot and, among equal dots, the lowest slot
+            best = fmaxf(best, fmaf(qe.x, qb.x, fmaf(qe.y, qb.y, fmaf(qe.z, qb.z, qe.w))));
           }
-          fly.add(O);
-          const uint32_t bit = 1u << (b & 31);
-          for (int m = 0; m < cnt; ++m) atomicOr(&s_am[warp][(stw >> (8 * m)) & 0xFFu][b >> 5], bit);
+          // low 6 bits of the integer: add 1.5 * 2^23 and read the mantissa
+          const int kb = 63 - (__float_as_int(best + 12582912.f) & 63);
+          const uint32_t stw = s_st[kb];
+          const int cnt = (int)(stw >> 24);
+          if (cnt == 0) {
+            esc.add(O);
+          } else {
+            T P;
+            if constexpr (sizeof(T) == 8) {
+              P = O / (T)cnt;
+            } else {
+              P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
+            }
+            fly.add(O);
+            const uint32_t bit = 1u << (b & 31);
+            for (int m = 0; m < cnt; ++m) atomicOr(&s_am[(stw >> (8 * m)) & 0xFFu][b >> 5], bit);
+            Pv[b] = P;
+          }
         }
-        s_P[warp][b] = P;
       }
     }
     __syncwarp();
-    for (int b = lane; b < nbp; b += 32) Pv[b] = (b < nbins) ? s_P[warp][b] : T(0);
     for (int k = lane; k < deg; k += 32) {
       uint32_t m[MW];
 #pragma unroll
-      for (int w = 0; w < MW; ++w) m[w] = s_am[warp][k][w];
+      for (int w = 0; w < MW; ++w) m[w] = s_am[k][w];
       store_mask<MW>(a.M_next, (int64_t)r0 + k, m);
     }
     __syncwarp();
   }
   // ---------------- budget partials of the tile ----------------
-  const double t_abs = warp_sum_d(bud_abs);
-  const double t_sink = warp_sum_d(bud_sink);
-  const double t_fly = fly.warp_total();
-  const double t_esc = esc.warp_total();
-  if (lane == 0) {
-    s_bud[warp][0] = t_abs;
-    s_bud[warp][1] = __dadd_rn(t_sink, t_esc);
-    s_bud[warp][2] = t_fly;
+  if constexpr (sizeof(T) == 8) {
+    const double t_fly = warp_sum_d(fly.v), t_esc = warp_sum_d(esc.v);
+    if (lane == 0) {
+      s_budw[warp][0] = t_fly;
+      s_budw[warp][2] = t_esc;
+    }
+  } else {
+    const FF t_fly = ff_warp_sum(fly.v), t_esc = ff_warp_sum(esc.v);
+    if (lane == 0) {
+      s_budw[warp][0] = t_fly.hi;
+      s_budw[warp][1] = t_fly.lo;
+      s_budw[warp][2] = t_esc.hi;
+      s_budw[warp][3] = t_esc.lo;
+    }
+  }
+  if (warp < kTile / 32) {  // the chemistry lanes hold absorbed and sink photons
+    const double ab = warp_sum_d(bud_abs), sk = warp_sum_d(bud_sink);
+    if (lane == 0) {
+      s_abs = ab;
+      s_sink = sk;
+    }
   }
   __syncthreads();
   if (tid == 0) {
-    double ab = 0.0, es = 0.0, fl = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      ab += s_bud[w][0];
-      es += s_bud[w][1];
-      fl += s_bud[w][2];
+    double fl, es;
+    if constexpr (sizeof(T) == 8) {
+      fl = 0.0;
+      es = 0.0;
+      for (int w = 0; w < kWarps; ++w) {
+        fl += s_budw[w][0];
+        es += s_budw[w][2];
+      }
+    } else {
+      FF F1{0.f, 0.f}, F2{0.f, 0.f};
+      for (int w = 0; w < kWarps; ++w) {
+        F1 = ff_add(F1, FF{(float)s_budw[w][0], (float)s_budw[w][1]});
+        F2 = ff_add(F2, FF{(float)s_budw[w][2], (float)s_budw[w][3]});
+      }
+      fl = ff_to_double(F1);
+      es = ff_to_double(F2);
     }
     double *p = a.partials + 4 * (int64_t)blockIdx.x;
-    p[0] += ab;
-    p[1] += es;
+    p[0] += s_abs;
+    p[1] += s_sink + es;
     p[2] = fl;
   }
 }
@@ -575,6 +709,7 @@ static cudaError_t launch_step_t(DevGrid &g, int64_t step, double dt, double fc,
   a.M_next = g.M[cur];
   a.tab = g.tabs;
   a.src_share = g.src_share;
+  a.src_share_f = g.src_share_f;
   a.partials = g.partials;
   a.diag = g.diag;
   const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
