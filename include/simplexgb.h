@@ -158,6 +158,37 @@ int sx_get_info(sx_ctx *ctx, sx_info *info);
    enabling resets the sums.  enable = 0: stop timing. */
 int sx_profile(sx_ctx *ctx, int enable);
 
+/* ---------------------------------------------------------------------------
+ * Batched stepping of many grids (a system form of the method, not in the
+ * paper): one rotation launch and one persistent step launch per step cover
+ * every grid of the batch; the CTAs pull (grid, 32-vertex tile) items from a
+ * work queue, so uneven grids share the GPU.  Each grid keeps its own state
+ * and gets results identical to stepping it alone with sx_step.
+ * ------------------------------------------------------------------------- */
+typedef struct sx_batch sx_batch;
+
+/* Device bytes the batch tables need for up to max_grids grids. */
+int sx_batch_workspace_bytes(int32_t max_grids, int64_t *bytes);
+
+/* Create a batch driver on a device and stream (NULL = legacy default
+   stream).  d_workspace (caller-owned, 256-byte aligned, >=
+   sx_batch_workspace_bytes) holds the per-grid argument tables.
+   Errors: SX_EINVAL, SX_ENOMEM, SX_ECUDA. */
+int sx_batch_create(int32_t max_grids, int32_t device, void *stream, void *d_workspace,
+                    int64_t workspace_bytes, sx_batch **out);
+
+/* Advance n loaded contexts by nsteps steps, context i with time step
+   dt_s[i].  All contexts must share nbins, precision and device.  Work is
+   queued on the batch stream after the contexts' pending work; the contexts'
+   streams wait for it before their next call.  Errors: SX_EINVAL (n out of
+   1..max_grids, mixed nbins/precision/device, dt <= 0), SX_ESTATE (a context
+   without grid), SX_ECUDA. */
+int sx_batch_step(sx_batch *batch, sx_ctx *const *ctxs, int32_t n, const double *dt_s,
+                  int32_t nsteps);
+
+void sx_batch_destroy(sx_batch *batch);
+const char *sx_batch_last_error(const sx_batch *batch);
+
 /* Release the context (not the caller's workspace). */
 void sx_destroy(sx_ctx *ctx);
 

@@ -27,12 +27,20 @@ struct sx_ctx {
   int32_t max_degree = 0;
   bool punit_set = false;  // FP32 photons are stored in units of g.punit photons
   bool profiling = false;
+  // CUDA graph of kGraphSteps steps (rotation + step kernels), captured on the
+  // context's stream for a given dt and source count and replayed by sx_step
+  cudaGraphExec_t graph = nullptr;
+  double graph_dt = 0.0;
+  int graph_nsrc = -1;
+  double graph_punit = 0.0;
+  int graph_steps = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   size_t events_used = 0;
   double kernel_ms = 0.0;
   int64_t kernel_launches = 0;
   std::string err;
   ~sx_ctx() {
+    if (graph) cudaGraphExecDestroy(graph);
     for (auto &e : events) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -41,6 +49,7 @@ struct sx_ctx {
 };
 
 static thread_local std::string g_create_err;
+static constexpr int kGraphSteps = 16;
 
 static int fail(sx_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg; else g_create_err = msg;
@@ -56,6 +65,53 @@ static int cuda_fail(sx_ctx *c, cudaError_t e, const char *what) {
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
   } while (0)
+
+// FP32 storage: fix the photon unit at the power of two just above the photons
+// the sources emit in one step, so that packets stay near 1 and the scaling
+// itself is exact.
+static void ensure_punit(sx_ctx *c, double dt) {
+  if (c->punit_set) return;
+  double tot = 0.0;
+  for (double r : c->src_rate) tot += r * dt;
+  if (tot > 0.0) {
+    int ex = 0;
+    std::frexp(tot, &ex);
+    c->g.punit = std::ldexp(1.0, ex);
+    c->punit_set = true;
+  }
+}
+
+struct sx_batch {
+  int32_t max_grids = 0;
+  int32_t device = 0;
+  cudaStream_t stream = nullptr;
+  sx::RotArgs *d_rot = nullptr;
+  sx::StepArgs *d_args = nullptr;
+  int64_t *d_prefix = nullptr;
+  unsigned long long *d_queue = nullptr;
+  std::vector<sx::RotArgs> h_rot;
+  std::vector<sx::StepArgs> h_args;
+  std::vector<int64_t> h_prefix;
+  cudaEvent_t ev = nullptr;       // end of the last queued batch work
+  cudaEvent_t ev_copy = nullptr;  // the argument tables of the last call reached the device
+  bool copy_pending = false;
+  std::string err;
+  ~sx_batch() {
+    if (ev) cudaEventDestroy(ev);
+    if (ev_copy) cudaEventDestroy(ev_copy);
+  }
+};
+
+static size_t batch_bytes(int32_t max_grids) {
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  return up(sizeof(sx::RotArgs) * max_grids) + up(sizeof(sx::StepArgs) * max_grids) +
+         up(sizeof(int64_t) * (max_grids + 1)) + up(sizeof(unsigned long long));
+}
+
+static int bfail(sx_batch *b, int code, const std::string &msg) {
+  if (b) b->err = msg; else g_create_err = msg;
+  return code;
+}
 
 extern "C" {
 
@@ -132,6 +188,10 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
     return fail(c, SX_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
   const cudaStream_t st = c->stream;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
   c->L = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision);
   sx::DevGrid &g = c->g;
   g = sx::DevGrid{};
@@ -151,6 +211,7 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
   SX_CUDA(c, cudaMemsetAsync(base + c->L.off_M0, 0, c->L.off_partials - c->L.off_M0, st));
   SX_CUDA(c, cudaMemsetAsync(base + c->L.off_partials, 0, c->L.off_tabs - c->L.off_partials, st));
   SX_CUDA(c, cudaMemsetAsync(base + c->L.off_diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
+  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_steps, 0, sizeof(unsigned long long), st));
   SX_CUDA(c, cudaMemsetAsync(base + c->L.off_src, 0, sizeof(double) * sx::kMaxSources, st));
   // inputs
   SX_CUDA(c, cudaMemcpyAsync(g.pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
@@ -226,20 +287,43 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
-  if (!c->punit_set) {
-    // FP32 storage: fix the photon unit at the power of two just above the
-    // photons the sources emit in one step, so that packets stay near 1 and
-    // the scaling itself is exact
-    double tot = 0.0;
-    for (double r : c->src_rate) tot += r * dt;
-    if (tot > 0.0) {
-      int ex = 0;
-      std::frexp(tot, &ex);
-      c->g.punit = std::ldexp(1.0, ex);
-      c->punit_set = true;
+  ensure_punit(c, dt);
+  int32_t k0 = 0;
+  if (!c->profiling && c->stream != nullptr && nsteps >= kGraphSteps) {
+    // replay a captured block of steps: identical launches, the step index
+    // lives on the device
+    if (!c->graph || c->graph_dt != dt || c->graph_nsrc != c->g.nsrc || c->graph_punit != c->g.punit) {
+      if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+      }
+      cudaGraph_t gr = nullptr;
+      SX_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = cudaSuccess;
+      for (int k = 0; k < kGraphSteps && ce == cudaSuccess; ++k) {
+        ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, 0, 0, dt, c->stream);
+        if (ce == cudaSuccess)
+          ce = sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, c->stream);
+      }
+      cudaError_t ee = cudaStreamEndCapture(c->stream, &gr);
+      if (ce != cudaSuccess) return cuda_fail(c, ce, "graph capture");
+      if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
+      cudaError_t ie = cudaGraphInstantiate(&c->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) return cuda_fail(c, ie, "cudaGraphInstantiate");
+      c->graph_dt = dt;
+      c->graph_nsrc = c->g.nsrc;
+      c->graph_punit = c->g.punit;
+      c->graph_steps = kGraphSteps;
+    }
+    for (; k0 + c->graph_steps <= nsteps; k0 += c->graph_steps) {
+      SX_CUDA(c, cudaGraphLaunch(c->graph, c->stream));
+      for (int k = 0; k < c->graph_steps; ++k)
+        for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
+      c->step += c->graph_steps;
     }
   }
-  for (int32_t k = 0; k < nsteps; ++k) {
+  for (int32_t k = k0; k < nsteps; ++k) {
     SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, c->step, 0, dt, c->stream));
     if (c->profiling) {
       if (c->events_used == c->events.size()) {
@@ -250,8 +334,8 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
       }
       SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
     }
-    SX_CUDA(c, sx::launch_step(c->g, c->step, dt, c->cfg.chem_frac, c->cfg.chem_tol,
-                               c->cfg.chem_max_sub, c->stream));
+    SX_CUDA(c, sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
+                               c->stream));
     if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
     for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
     c->step++;
@@ -356,6 +440,106 @@ int sx_get_info(sx_ctx *c, sx_info *info) {
   info->nsources = (int32_t)c->src_vertex.size();
   return SX_OK;
 }
+
+int sx_batch_workspace_bytes(int32_t max_grids, int64_t *bytes) {
+  if (max_grids < 1 || !bytes) return bfail(nullptr, SX_EINVAL, "max_grids < 1 or bytes is NULL");
+  *bytes = (int64_t)batch_bytes(max_grids);
+  return SX_OK;
+}
+
+int sx_batch_create(int32_t max_grids, int32_t device, void *stream, void *d_workspace,
+                    int64_t workspace_bytes, sx_batch **out) {
+  if (!out) return bfail(nullptr, SX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (max_grids < 1 || !d_workspace) return bfail(nullptr, SX_EINVAL, "max_grids < 1 or no workspace");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+    return bfail(nullptr, SX_EINVAL, "workspace must be 256-byte aligned");
+  if (workspace_bytes < (int64_t)batch_bytes(max_grids)) return bfail(nullptr, SX_ENOMEM, "workspace too small");
+  if (cudaSetDevice(device) != cudaSuccess) return bfail(nullptr, SX_ECUDA, "cudaSetDevice failed");
+  sx_batch *b = new sx_batch();
+  b->max_grids = max_grids;
+  b->device = device;
+  b->stream = static_cast<cudaStream_t>(stream);
+  char *p = static_cast<char *>(d_workspace);
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  b->d_rot = reinterpret_cast<sx::RotArgs *>(p);
+  p += up(sizeof(sx::RotArgs) * max_grids);
+  b->d_args = reinterpret_cast<sx::StepArgs *>(p);
+  p += up(sizeof(sx::StepArgs) * max_grids);
+  b->d_prefix = reinterpret_cast<int64_t *>(p);
+  p += up(sizeof(int64_t) * (max_grids + 1));
+  b->d_queue = reinterpret_cast<unsigned long long *>(p);
+  if (cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_copy, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return bfail(nullptr, SX_ECUDA, "cudaEventCreate failed");
+  }
+  *out = b;
+  return SX_OK;
+}
+
+#define SX_BCUDA(b, call)                                                                    \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return bfail(b, SX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_s, int32_t nsteps) {
+  if (!b) return SX_EINVAL;
+  if (!ctxs || !dt_s || n < 1 || n > b->max_grids || nsteps < 0)
+    return bfail(b, SX_EINVAL, "bad arguments");
+  const sx_ctx *c0 = ctxs[0];
+  for (int32_t i = 0; i < n; ++i) {
+    const sx_ctx *c = ctxs[i];
+    if (!c) return bfail(b, SX_EINVAL, "NULL context");
+    if (!c->loaded) return bfail(b, SX_ESTATE, "context without grid");
+    if (c->cfg.nbins != c0->cfg.nbins || c->cfg.precision != c0->cfg.precision ||
+        c->cfg.device != b->device)
+      return bfail(b, SX_EINVAL, "contexts differ in nbins, precision or device");
+    if (!(dt_s[i] > 0.0) || !std::isfinite(dt_s[i])) return bfail(b, SX_EINVAL, "dt must be > 0");
+  }
+  if (nsteps == 0) return SX_OK;
+  SX_BCUDA(b, cudaSetDevice(b->device));
+  // the host tables are reused: the previous call's copies must have run
+  if (b->copy_pending) SX_BCUDA(b, cudaEventSynchronize(b->ev_copy));
+  b->h_rot.resize(n);
+  b->h_args.resize(n);
+  b->h_prefix.resize(n + 1);
+  b->h_prefix[0] = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    sx_ctx *c = ctxs[i];
+    ensure_punit(c, dt_s[i]);
+    b->h_rot[i] = sx::make_rot_args(c->g, c->bins_dev, c->cfg.seed, 0, dt_s[i]);
+    b->h_args[i] = sx::make_step_args(c->g, dt_s[i], c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub);
+    b->h_prefix[i + 1] = b->h_prefix[i] + c->g.nblocks;
+    // the batch stream runs after the context's queued work
+    SX_BCUDA(b, cudaEventRecord(b->ev, c->stream));
+    SX_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev, 0));
+  }
+  SX_BCUDA(b, cudaMemcpyAsync(b->d_rot, b->h_rot.data(), sizeof(sx::RotArgs) * n, cudaMemcpyHostToDevice, b->stream));
+  SX_BCUDA(b, cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(sx::StepArgs) * n, cudaMemcpyHostToDevice, b->stream));
+  SX_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+  SX_BCUDA(b, cudaEventRecord(b->ev_copy, b->stream));
+  b->copy_pending = true;
+  for (int32_t k = 0; k < nsteps; ++k) {
+    SX_BCUDA(b, sx::launch_rotation_batch(b->d_rot, n, b->stream));
+    SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.mw, b->d_args, b->d_prefix, n,
+                                      b->h_prefix[n], b->d_queue, c0->cfg.nbins, b->device, b->stream));
+  }
+  SX_BCUDA(b, cudaEventRecord(b->ev, b->stream));
+  for (int32_t i = 0; i < n; ++i) {
+    sx_ctx *c = ctxs[i];
+    for (int32_t k = 0; k < nsteps; ++k)
+      for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt_s[i];
+    c->step += nsteps;
+    SX_BCUDA(b, cudaStreamWaitEvent(c->stream, b->ev, 0));
+  }
+  return SX_OK;
+}
+
+void sx_batch_destroy(sx_batch *b) { delete b; }
+
+const char *sx_batch_last_error(const sx_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
 
 void sx_destroy(sx_ctx *c) { delete c; }
 

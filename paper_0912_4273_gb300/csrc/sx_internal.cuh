@@ -40,9 +40,49 @@ struct StepTables {
   int32_t inv_off[kMaxBins + 1];  // packets of old bins inv_idx[inv_off[b]..inv_off[b+1])
   int32_t inv_idx[kMaxBins];      //   move to new bin b (ascending old index)
   uchar4 inv3[kMaxBins];          // the same as up to 3 old bins per new bin, missing = kMaxBins
+  long long step;                 // the step these tables are for
   int32_t attempts;
   int32_t remap;                  // 0: step 0, no previous orientation
   int32_t max_fanin;              // largest number of old bins moving into one new bin
+};
+
+// Arguments of the rotation kernel for one grid.  The step index lives on the
+// device (*steps_done), so that launches of successive steps are identical and
+// can be captured in a CUDA graph.
+struct RotArgs {
+  const double *bins;              // nbins x 3, unrotated
+  uint64_t seed;
+  unsigned long long *steps_done;  // read, then advanced by one (unless unrotated)
+  StepTables *tab;
+  int nbins;
+  int unrotated;                   // 1: identity orientation (kappa), counter untouched
+  int nsrc;
+  const double *src_rate;
+  double dt;
+  double inv_punit;
+  double *share;
+  float *share_f;
+};
+
+// Arguments of the step kernel for one grid (the batched kernel takes an array).
+struct StepArgs {
+  int64_t n;
+  int nbins, nbp;
+  double dt, inv_dt;
+  double punit;      // photons per stored unit (a power of two; 1 in FP64 mode)
+  double fc, tol;
+  int max_sub;
+  const int32_t *row_ptr;
+  const Edge *edges;
+  const VConst *vc;
+  double *y;
+  void *P[2];        // stored photons, ping-pong by step parity
+  uint32_t *M[2];    // per-edge bin masks, ping-pong by step parity
+  const StepTables *tab;
+  const double *src_share;
+  const float *src_share_f;
+  double *partials;
+  unsigned long long *diag;
 };
 
 enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagCount = 8 };
@@ -135,6 +175,7 @@ struct DevGrid {
   double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
   int64_t nblocks;
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
+  unsigned long long *steps_done;  // device step counter (advanced by the rotation kernel)
   double *src_rate;     // kMaxSources
   double *src_share;    // kMaxSources: photons per bin per step of each source, stored units
   float *src_share_f;   // the same in FP32
@@ -155,7 +196,7 @@ struct DevGrid {
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
-      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_diag, off_kpart, off_kappa, off_budget,
+      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       total;
   int64_t nblocks, nblocks_kappa;
@@ -171,8 +212,16 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
                                     cudaStream_t st);
 cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
                             int unrotated, double dt, cudaStream_t st);
-cudaError_t launch_step(DevGrid &g, int64_t step, double dt, double chem_frac, double chem_tol,
+cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st);
+RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unrotated, double dt);
+StepArgs make_step_args(DevGrid &g, double dt, double chem_frac, double chem_tol, int chem_max_sub);
+// Batched: one rotation CTA per grid, then one persistent launch over the
+// tiles of all grids (work queue).  All grids share nbins and precision.
+cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, cudaStream_t st);
+cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, const int64_t *d_prefix,
+                              int ngrids, int64_t total_tiles, unsigned long long *d_queue,
+                              int nbins, int device, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
 

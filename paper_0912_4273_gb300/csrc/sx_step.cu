@@ -68,42 +68,44 @@ __device__ void rotate_quantise(const double R[9], const double *d, int q[3]) {
   }
 }
 
-__global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__restrict__ bins,
-                                                  uint64_t seed, int64_t step, int unrotated,
-                                                  StepTables *__restrict__ out, int nsrc,
-                                                  const double *__restrict__ src_rate, double dt,
-                                                  double inv_punit, double *__restrict__ share,
-                                                  float *__restrict__ share_f) {
-  // photons each source puts in every bin this step, in stored units:
-  // ((rate dt) / n) / unit, the unit being a power of two
-  for (int s = threadIdx.x; s < nsrc; s += blockDim.x) {
-    share[s] = __dmul_rn(__ddiv_rn(__dmul_rn(src_rate[s], dt), (double)nbins), inv_punit);
-    share_f[s] = (float)share[s];
-  }
+__device__ void rotation_body(const RotArgs &r) {
   __shared__ double sR[9], sRp[9];
   __shared__ int s_att;
+  __shared__ long long s_step;
   __shared__ int s_qn[kMaxBins][3], s_qo[kMaxBins][3];
   __shared__ int s_map[kMaxBins];
   const int t = threadIdx.x;
+  const int nbins = r.nbins;
   if (t == 0) {
     int att = 0, attp = 0;
-    if (unrotated) {
+    long long step = 0;
+    if (r.unrotated) {
       for (int i = 0; i < 9; ++i) sR[i] = sRp[i] = (i % 4 == 0) ? 1.0 : 0.0;
     } else {
-      rotation_matrix(seed, step, sR, &att);
-      if (step > 0) rotation_matrix(seed, step - 1, sRp, &attp);
+      step = (long long)*r.steps_done;
+      *r.steps_done = (unsigned long long)(step + 1);
+      rotation_matrix(r.seed, step, sR, &att);
+      if (step > 0) rotation_matrix(r.seed, step - 1, sRp, &attp);
       else
         for (int i = 0; i < 9; ++i) sRp[i] = sR[i];
     }
     s_att = att;
+    s_step = step;
+  }
+  // photons each source puts in every bin this step, in stored units:
+  // ((rate dt) / n) / unit, the unit being a power of two
+  for (int k = t; k < r.nsrc; k += blockDim.x) {
+    r.share[k] = __dmul_rn(__ddiv_rn(__dmul_rn(r.src_rate[k], r.dt), (double)nbins), r.inv_punit);
+    r.share_f[k] = (float)r.share[k];
   }
   __syncthreads();
+  StepTables *out = r.tab;
   for (int b = t; b < nbins; b += blockDim.x) {
     int q[3];
-    rotate_quantise(sR, bins + 3 * b, q);
+    rotate_quantise(sR, r.bins + 3 * b, q);
     s_qn[b][0] = q[0]; s_qn[b][1] = q[1]; s_qn[b][2] = q[2];
     out->qb[b] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
-    rotate_quantise(sRp, bins + 3 * b, q);
+    rotate_quantise(sRp, r.bins + 3 * b, q);
     s_qo[b][0] = q[0]; s_qo[b][1] = q[1]; s_qo[b][2] = q[2];
   }
   __syncthreads();
@@ -120,33 +122,76 @@ __global__ void __launch_bounds__(128) k_rotation(int nbins, const double *__res
     s_map[b] = best;
   }
   __syncthreads();
+  // inverse of the map: the old bins of every new bin, ascending
+  __shared__ int s_cnt[kMaxBins + 1];
+  for (int b2 = t; b2 < nbins; b2 += blockDim.x) {
+    unsigned char i3[3] = {kMaxBins, kMaxBins, kMaxBins};
+    int c = 0;
+    for (int b = 0; b < nbins; ++b)
+      if (s_map[b] == b2) {
+        if (c < 3) i3[c] = (unsigned char)b;
+        c++;
+      }
+    out->inv3[b2] = make_uchar4(i3[0], i3[1], i3[2], (unsigned char)c);
+    s_cnt[b2] = c;
+  }
+  __syncthreads();
   if (t == 0) {
     int o = 0, mx = 0;
     for (int b2 = 0; b2 < nbins; ++b2) {
-      out->inv_off[b2] = o;
-      unsigned char i3[3] = {kMaxBins, kMaxBins, kMaxBins};
-      int c = 0;
-      for (int b = 0; b < nbins; ++b)
-        if (s_map[b] == b2) {
-          if (c < 3) i3[c] = (unsigned char)b;
-          c++;
-          out->inv_idx[o++] = b;
-        }
-      out->inv3[b2] = make_uchar4(i3[0], i3[1], i3[2], (unsigned char)c);
+      const int c = s_cnt[b2];
+      s_cnt[b2] = o;
+      o += c;
       mx = c > mx ? c : mx;
     }
-    out->inv_off[nbins] = o;
+    s_cnt[nbins] = o;
     out->attempts = s_att;
-    out->remap = (!unrotated && step > 0) ? 1 : 0;
+    out->step = s_step;
+    out->remap = (!r.unrotated && s_step > 0) ? 1 : 0;
     out->max_fanin = mx;
+  }
+  __syncthreads();
+  for (int b2 = t; b2 <= nbins; b2 += blockDim.x) out->inv_off[b2] = s_cnt[b2];
+  for (int b2 = t; b2 < nbins; b2 += blockDim.x) {
+    int o = s_cnt[b2];
+    for (int b = 0; b < nbins; ++b)
+      if (s_map[b] == b2) out->inv_idx[o++] = b;
   }
 }
 
-cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
+__global__ void __launch_bounds__(128) k_rotation(const RotArgs r) { rotation_body(r); }
+
+// one CTA per grid of a batch
+__global__ void __launch_bounds__(128) k_rotation_batch(const RotArgs *__restrict__ ra) {
+  rotation_body(ra[blockIdx.x]);
+}
+
+RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unrotated, double dt) {
+  RotArgs r;
+  r.bins = bins_dev;
+  r.seed = seed;
+  r.steps_done = g.steps_done;
+  r.tab = g.tabs + (unrotated ? 1 : 0);
+  r.nbins = g.nbins;
+  r.unrotated = unrotated;
+  r.nsrc = unrotated ? 0 : g.nsrc;
+  r.src_rate = g.src_rate;
+  r.dt = dt;
+  r.inv_punit = 1.0 / g.punit;
+  r.share = g.src_share;
+  r.share_f = g.src_share_f;
+  return r;
+}
+
+cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t /*step*/,
                             int unrotated, double dt, cudaStream_t st) {
-  k_rotation<<<1, 128, 0, st>>>(g.nbins, bins_dev, seed, step, unrotated,
-                                g.tabs + (unrotated ? 1 : 0), unrotated ? 0 : g.nsrc, g.src_rate, dt,
-                                1.0 / g.punit, g.src_share, g.src_share_f);
+  k_rotation<<<1, 128, 0, st>>>(make_rot_args(g, bins_dev, seed, unrotated, dt));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, cudaStream_t st) {
+  if (ngrids <= 0) return cudaSuccess;
+  k_rotation_batch<<<ngrids, 128, 0, st>>>(d_rot);
   return cudaGetLastError();
 }
 
@@ -250,27 +295,6 @@ __device__ __forceinline__ void acc_add<float>(float &acc, float &c, float x) {
   acc = t;
 }
 
-struct StepArgs {
-  int64_t n;
-  int nbins, nbp;
-  double dt, inv_dt;
-  double punit;      // photons per stored unit (a power of two; 1 in FP64 mode)
-  double fc, tol;
-  int max_sub;
-  const int32_t *__restrict__ row_ptr;
-  const Edge *__restrict__ edges;
-  const VConst *__restrict__ vc;
-  double *__restrict__ y;
-  const void *__restrict__ P_prev;
-  void *__restrict__ P_next;
-  const uint32_t *__restrict__ M_prev;
-  uint32_t *__restrict__ M_next;
-  const StepTables *__restrict__ tab;
-  const double *__restrict__ src_share;
-  const float *__restrict__ src_share_f;
-  double *__restrict__ partials;
-  unsigned long long *__restrict__ diag;
-};
 
 // Row stride (elements) of the shared photon tile: odd, so that a lane per
 // vertex walking its own row touches 32 distinct banks.
@@ -302,7 +326,7 @@ __device__ __forceinline__ float small_int_to_float(int i) {
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
 #endif
 template <typename T, int MW>
-__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][tile_stride(nbins)]
   __shared__ float4 s_qb[kMaxBins];
@@ -314,6 +338,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
   __shared__ T s_budw[kWarps][4];  // per warp: fly hi/lo, esc hi/lo (FP32) or fly, esc (FP64)
   __shared__ double s_abs, s_sink;
   __shared__ int s_remap, s_fanin;
+  __shared__ long long s_step;
   // Per-warp scratch, used by phase 1 (bin accumulators and the contribution
   // list) and, after the barrier, by phase 3 (staged edges, masks, bin list).
   constexpr int kLcap = 64;
@@ -334,12 +359,16 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
   if (tid == 0) {
     s_remap = a.tab->remap;
     s_fanin = a.tab->max_fanin;
+    s_step = a.tab->step;
   }
   __syncthreads();
 
-  const int64_t v0 = (int64_t)blockIdx.x * kTile;
-  const T *__restrict__ Pp = static_cast<const T *>(a.P_prev);
-  T *__restrict__ Pn = static_cast<T *>(a.P_next);
+  const int64_t v0 = tile * kTile;
+  const int cur = (int)(s_step & 1);
+  const T *__restrict__ Pp = static_cast<const T *>(a.P[cur ^ 1]);
+  T *__restrict__ Pn = static_cast<T *>(a.P[cur]);
+  const uint32_t *__restrict__ M_prev = a.M[cur ^ 1];
+  uint32_t *__restrict__ M_next = a.M[cur];
 
   // ---------------- phase 1: gather, remap, sources ----------------
   {
@@ -366,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
         if (e0 + lane < r1) {
           const Edge E = a.edges[e0 + lane];
           my_src = E.col;
-          load_mask<MW>(a.M_prev, E.twin, my_m);
+          load_mask<MW>(M_prev, E.twin, my_m);
         }
         int cnt = 0;
 #pragma unroll
@@ -567,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
         uint32_t z[MW];
 #pragma unroll
         for (int w = 0; w < MW; ++w) z[w] = 0u;
-        store_mask<MW>(a.M_next, (int64_t)r0 + k, z);
+        store_mask<MW>(M_next, (int64_t)r0 + k, z);
       }
       continue;
     }
@@ -632,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
       uint32_t m[MW];
 #pragma unroll
       for (int w = 0; w < MW; ++w) m[w] = s_am[k][w];
-      store_mask<MW>(a.M_next, (int64_t)r0 + k, m);
+      store_mask<MW>(M_next, (int64_t)r0 + k, m);
     }
     __syncwarp();
   }
@@ -678,16 +707,43 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const Ste
       fl = ff_to_double(F1);
       es = ff_to_double(F2);
     }
-    double *p = a.partials + 4 * (int64_t)blockIdx.x;
+    double *p = a.partials + 4 * tile;
     p[0] += s_abs;
     p[1] += s_sink + es;
     p[2] = fl;
   }
+  __syncthreads();  // shared state is reused by the next tile of a persistent CTA
 }
 
 template <typename T, int MW>
-static cudaError_t launch_step_t(DevGrid &g, int64_t step, double dt, double fc, double tol,
-                                 int max_sub, cudaStream_t st) {
+__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
+  step_tile<T, MW>(a, blockIdx.x);
+}
+
+// Persistent CTAs pull (grid, tile) work items of a batch of grids from a
+// queue; a tile is one grid's 32 consecutive vertices.
+template <typename T, int MW>
+__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS)
+    k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
+                 unsigned long long *__restrict__ queue) {
+  __shared__ long long s_item;
+  const int64_t total = prefix[ngrids];
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+    __syncthreads();
+    const int64_t t = s_item;
+    __syncthreads();
+    if (t >= total) break;
+    int lo = 0, hi = ngrids - 1;  // the grid whose tile range holds t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    step_tile<T, MW>(args[lo], t - prefix[lo]);
+  }
+}
+
+StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_sub) {
   StepArgs a;
   a.n = g.n;
   a.nbins = g.nbins;
@@ -702,36 +758,79 @@ static cudaError_t launch_step_t(DevGrid &g, int64_t step, double dt, double fc,
   a.edges = g.edges;
   a.vc = g.vc;
   a.y = g.y;
-  const int cur = (int)(step & 1), prev = cur ^ 1;
-  a.P_prev = g.P[prev];
-  a.P_next = g.P[cur];
-  a.M_prev = g.M[prev];
-  a.M_next = g.M[cur];
+  a.P[0] = g.P[0];
+  a.P[1] = g.P[1];
+  a.M[0] = g.M[0];
+  a.M[1] = g.M[1];
   a.tab = g.tabs;
   a.src_share = g.src_share;
   a.src_share_f = g.src_share_f;
   a.partials = g.partials;
   a.diag = g.diag;
-  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
-  static bool configured = false;
-  if (!configured) {
+  return a;
+}
+
+template <typename T, int MW>
+static void configure_smem() {
+  static bool done = false;
+  if (!done) {
     cudaFuncSetAttribute(k_step<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    configured = true;
+    cudaFuncSetAttribute(k_step_batch<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    done = true;
   }
+}
+
+template <typename T, int MW>
+static cudaError_t launch_step_t(DevGrid &g, double dt, double fc, double tol, int max_sub,
+                                 cudaStream_t st) {
+  const StepArgs a = make_step_args(g, dt, fc, tol, max_sub);
+  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
+  configure_smem<T, MW>();
   k_step<T, MW><<<(unsigned)g.nblocks, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_step(DevGrid &g, int64_t step, double dt, double chem_frac, double chem_tol,
+cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st) {
   if (g.precision == 0) {
-    if (g.mw == 1) return launch_step_t<double, 1>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
-    if (g.mw == 2) return launch_step_t<double, 2>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
-    return launch_step_t<double, 4>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
+    if (g.mw == 1) return launch_step_t<double, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+    if (g.mw == 2) return launch_step_t<double, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+    return launch_step_t<double, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
   }
-  if (g.mw == 1) return launch_step_t<float, 1>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
-  if (g.mw == 2) return launch_step_t<float, 2>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
-  return launch_step_t<float, 4>(g, step, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (g.mw == 1) return launch_step_t<float, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (g.mw == 2) return launch_step_t<float, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  return launch_step_t<float, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+}
+
+template <typename T, int MW>
+static cudaError_t launch_batch_t(const StepArgs *d_args, const int64_t *d_prefix, int ngrids,
+                                  int64_t total, unsigned long long *d_queue, int nbins, int device,
+                                  cudaStream_t st) {
+  configure_smem<T, MW>();
+  int nsm = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(nbins);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<T, MW>, kThreads, smem);
+  int64_t ctas = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+  if (ctas > total) ctas = total;
+  cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  if (ctas <= 0) return cudaSuccess;
+  k_step_batch<T, MW><<<(unsigned)ctas, kThreads, smem, st>>>(d_args, d_prefix, ngrids, d_queue);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, const int64_t *d_prefix,
+                              int ngrids, int64_t total_tiles, unsigned long long *d_queue,
+                              int nbins, int device, cudaStream_t st) {
+  if (precision == 0) {
+    if (mw == 1) return launch_batch_t<double, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+    if (mw == 2) return launch_batch_t<double, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+    return launch_batch_t<double, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  }
+  if (mw == 1) return launch_batch_t<float, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  if (mw == 2) return launch_batch_t<float, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  return launch_batch_t<float, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
 }
 
 // ----------------------------------------------------------------------------

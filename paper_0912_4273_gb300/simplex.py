@@ -76,6 +76,13 @@ _SIGS = [
     ("sx_profile", C.c_int, [C.c_void_p, C.c_int]),
     ("sx_destroy", None, [C.c_void_p]),
     ("sx_last_error", C.c_char_p, [C.c_void_p]),
+    ("sx_batch_workspace_bytes", C.c_int, [C.c_int32, _P(C.c_int64)]),
+    ("sx_batch_create", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64,
+                                  _P(C.c_void_p)]),
+    ("sx_batch_step", C.c_int, [C.c_void_p, _P(C.c_void_p), C.c_int32, _P(C.c_double),
+                                C.c_int32]),
+    ("sx_batch_destroy", None, [C.c_void_p]),
+    ("sx_batch_last_error", C.c_char_p, [C.c_void_p]),
 ]
 
 
@@ -184,6 +191,72 @@ def sx_destroy(ctx):
 def sx_last_error(ctx=None) -> str:
     m = lib().sx_last_error(ctx)
     return m.decode() if m else ""
+
+
+def _bcheck(batch, rc: int):
+    if rc != SX_OK:
+        msg = lib().sx_batch_last_error(batch)
+        raise SimplexError(rc, msg.decode() if msg else "")
+
+
+def sx_batch_workspace_bytes(max_grids: int) -> int:
+    out = C.c_int64()
+    _bcheck(None, lib().sx_batch_workspace_bytes(max_grids, C.byref(out)))
+    return out.value
+
+
+def sx_batch_create(max_grids: int, device: int, stream: int, d_workspace: int,
+                    workspace_bytes: int):
+    out = C.c_void_p()
+    _bcheck(None, lib().sx_batch_create(max_grids, device, C.c_void_p(stream),
+                                        C.c_void_p(d_workspace), workspace_bytes, C.byref(out)))
+    return out
+
+
+def sx_batch_step(batch, ctxs, dts, nsteps: int):
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    d = np.ascontiguousarray(dts, dtype=np.float64)
+    _bcheck(batch, lib().sx_batch_step(batch, arr, n, _ptr(d, C.c_double), nsteps))
+
+
+def sx_batch_destroy(batch):
+    lib().sx_batch_destroy(batch)
+
+
+def sx_batch_last_error(batch=None) -> str:
+    m = lib().sx_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+class Batch:
+    """Steps many :class:`Solver` grids together (one persistent launch per step)."""
+
+    def __init__(self, max_grids: int, device: int = 0, stream=None):
+        import torch
+
+        self.device = torch.device("cuda", device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = sx_batch_workspace_bytes(max_grids)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.handle = sx_batch_create(max_grids, device, self.stream.cuda_stream,
+                                      self.workspace.data_ptr(), nbytes)
+
+    def step(self, solvers, dts, nsteps: int = 1):
+        if np.isscalar(dts):
+            dts = [dts] * len(solvers)
+        sx_batch_step(self.handle, [s.ctx for s in solvers], dts, nsteps)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

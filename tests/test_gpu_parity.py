@@ -178,3 +178,56 @@ def test_invalid_grids_are_rejected():
         s.load(prob, workspace=small)
     assert e.value.code == S.SX_ENOMEM
     s.close()
+
+
+def test_batched_step_equals_single_grid_steps():
+    """Grids stepped together in one persistent launch give bit-identical
+    results to each grid stepped alone (every tile does the same arithmetic
+    whichever CTA takes it)."""
+    bins = I.fibonacci_bins(42)
+    probs = [I.stromgren_problem(n, seed=s) for n, s in ((300, 1), (2048, 2), (5000, 3), (777, 4))]
+    dts = [DT, 0.5 * DT, 2 * DT, DT]
+    alone = []
+    for p, dt in zip(probs, dts):
+        s = S.Solver(bins, seed=7).load(p)
+        s.step(dt, 23)
+        alone.append((s.y, s.budget, s.photons()))
+        s.close()
+    sol = [S.Solver(bins, seed=7).load(p) for p in probs]
+    batch = S.Batch(max_grids=8)
+    batch.step(sol, dts, 10)
+    batch.step(sol, dts, 13)
+    for s, (y, b, ph) in zip(sol, alone):
+        assert s.info["step"] == 23
+        assert np.array_equal(s.y, y)
+        assert s.budget == b
+        assert np.array_equal(s.photons(), ph)
+        s.close()
+    # mixed bin counts are refused
+    other = S.Solver(I.fibonacci_bins(84)).load(probs[0])
+    one = S.Solver(bins).load(probs[0])
+    with pytest.raises(S.SimplexError) as e:
+        batch.step([one, other], DT, 1)
+    assert e.value.code == S.SX_EINVAL
+    batch.close()
+
+
+def test_graph_replay_on_a_stream_matches_direct_launches(c0):
+    """On a non-default stream sx_step replays a captured CUDA graph of 16
+    steps; results are bit-identical to single-step launches."""
+    prob, bins, ref, _ = c0
+    st = torch.cuda.Stream()
+    out = []
+    for chunks in ((1,) * 40, (40,), (16, 3, 21)):
+        s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, stream=st).load(prob)
+        for c in chunks:
+            s.step(DT, c)
+        out.append((s.y, s.budget))
+        s.close()
+    for y, b in out[1:]:
+        assert np.array_equal(y, out[0][0])
+        assert b == out[0][1]
+    # and the oracle agrees
+    r = O.OracleSim(prob, O.Params(nbins=42, seed=0), bins)
+    r.step(DT, 40)
+    assert np.abs(out[1][0] - r.y).max() <= 1e-4
