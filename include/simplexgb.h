@@ -189,6 +189,31 @@ int sx_batch_step(sx_batch *batch, sx_ctx *const *ctxs, int32_t n, const double 
 void sx_batch_destroy(sx_batch *batch);
 const char *sx_batch_last_error(const sx_batch *batch);
 
+/* ---------------------------------------------------------------------------
+ * For callers that cannot allocate device memory.  (The paper has no
+ * counterpart of this entry point: it is an interface of this library.)
+ * ------------------------------------------------------------------------- */
+#define SX_NOALLOC_MAX_VERTICES 16384
+#define SX_NOALLOC_MAX_EDGES 262144
+
+/* The path-length correction kappa of a grid -- the value sx_load_grid
+   computes and sx_get_info reports -- for callers that cannot allocate
+   device memory (code running while another allocator owns the device, or
+   that must not call the allocator): it allocates nothing, and needs no
+   workspace.  Host inputs as for sx_load_grid, bin_dirs as for sx_create.
+   Its device scratch is one fixed array of about 10 MB that every GPU loading
+   this library holds until exit, so n <= SX_NOALLOC_MAX_VERTICES and nnz <=
+   SX_NOALLOC_MAX_EDGES (SX_EINVAL beyond).  The first call on a device looks
+   up that array's address there; make it before any stream capture.  Calls
+   share the array: the call waits for its stream before returning, and calls
+   whose GPU work overlaps would race (the calls of one process are serialised
+   on the host).  Errors: SX_EINVAL, SX_ECUDA; reason from
+   sx_kappa_noalloc_last_error(). */
+int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row_ptr, const int32_t *col,
+                     const uint8_t *flags, int32_t nbins, const double *bin_dirs, int32_t device,
+                     void *stream, double *kappa_out);
+const char *sx_kappa_noalloc_last_error(void);
+
 /* Release the context (not the caller's workspace). */
 void sx_destroy(sx_ctx *ctx);
 

@@ -223,6 +223,7 @@ cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, con
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int device, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
+cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
 
 }  // namespace sx

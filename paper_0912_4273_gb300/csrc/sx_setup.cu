@@ -344,4 +344,13 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
   return cudaGetLastError();
 }
 
+// kappa alone (k_kappa + k_kappa_final on the unrotated tables in g.tabs[1]).
+cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st) {
+  const int T = 256;
+  k_kappa<<<(unsigned)g.nblocks_kappa, T, 0, st>>>(g.n, g.nbins, g.row_ptr, g.edges, g.s_ev,
+                                                   g.s_flags, g.tabs + 1, bins_dev, g.kappa_part);
+  k_kappa_final<<<1, T, 0, st>>>(g.nblocks_kappa, g.kappa_part, 0.0, g.kappa_dev);
+  return cudaGetLastError();
+}
+
 }  // namespace sx

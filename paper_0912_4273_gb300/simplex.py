@@ -83,6 +83,10 @@ _SIGS = [
                                 C.c_int32]),
     ("sx_batch_destroy", None, [C.c_void_p]),
     ("sx_batch_last_error", C.c_char_p, [C.c_void_p]),
+    ("sx_kappa_noalloc", C.c_int, [C.c_int64, _P(C.c_double), _P(C.c_int64), _P(C.c_int32),
+                                   _P(C.c_uint8), C.c_int32, _P(C.c_double), C.c_int32,
+                                   C.c_void_p, _P(C.c_double)]),
+    ("sx_kappa_noalloc_last_error", C.c_char_p, []),
 ]
 
 
@@ -226,6 +230,31 @@ def sx_batch_destroy(batch):
 
 def sx_batch_last_error(batch=None) -> str:
     m = lib().sx_batch_last_error(batch)
+    return m.decode() if m else ""
+
+
+SX_NOALLOC_MAX_VERTICES = 16384
+SX_NOALLOC_MAX_EDGES = 262144
+
+
+def sx_kappa_noalloc(n, pos, row_ptr, col, flags, bin_dirs, device: int = 0, stream: int = 0) -> float:
+    """kappa of a grid without any device allocation (see include/simplexgb.h)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    b = np.ascontiguousarray(bin_dirs, dtype=np.float64)
+    out = C.c_double()
+    rc = lib().sx_kappa_noalloc(n, _ptr(pos, C.c_double), _ptr(rp, C.c_int64), _ptr(cl, C.c_int32),
+                                _ptr(fl, C.c_uint8), len(b), _ptr(b, C.c_double), device,
+                                C.c_void_p(stream), C.byref(out))
+    if rc != SX_OK:
+        raise SimplexError(rc, sx_kappa_noalloc_last_error())
+    return out.value
+
+
+def sx_kappa_noalloc_last_error() -> str:
+    m = lib().sx_kappa_noalloc_last_error()
     return m.decode() if m else ""
 
 
