@@ -49,7 +49,8 @@ WORKLOADS = {
 
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": None, "bytes_per_launch": None, "workload": None}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "c24fb59d7e6882c689385cd602c70a3fc148d693a89ea18cd304d52ee9302e3f",
+               "bytes_per_launch": 996.397312e6 + 375.977472e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
