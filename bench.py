@@ -367,6 +367,138 @@ def run_reference(args, wl, rank, world):
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched (many independent grids) and served (request stream) measurements
+# ---------------------------------------------------------------------------
+def _grid_pool(sizes, seed0=1000):
+    from paper_0912_4273_gb300 import inputs as I
+
+    return {int(n): I.cached(I.stromgren_problem, int(n), seed=seed0 + i) for i, n in enumerate(sizes)}
+
+
+def _sized_problem(base, nH, rate, box_over_rs=2.5):
+    """A Test-1 problem on a pooled grid geometry rescaled to its own medium:
+    the box is box_over_rs Stromgren radii across, with the source at the centre."""
+    import copy
+
+    from paper_0912_4273_gb300 import inputs as I
+
+    rs = (3.0 * rate / (4.0 * math.pi * I.ALPHA_B * nH * nH)) ** (1.0 / 3.0)
+    scale = box_over_rs * rs / base.box
+    p = copy.copy(base)
+    p.pos = base.pos * scale
+    p.volume = base.volume * scale**3
+    p.nH = np.full(base.n, nH)
+    p.src_rate = np.array([rate])
+    p.box = base.box * scale
+    return p
+
+
+def run_batched(args):
+    """256 grids, sizes log-uniform in [4096, 262144], n_H log-uniform in
+    [1e-4, 1e-2], one source each with rate log-uniform in [1e47, 1e49],
+    42 bins, 500 steps of 4 t_rec / 500: one persistent launch per step for
+    all grids (sx_batch_step) against one grid per launch sequence (sx_step)."""
+    import torch
+
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    rng = np.random.default_rng(args.seed)
+    ngrids, steps = args.grids, args.batch_steps
+    pool_sizes = np.unique(np.round(np.geomspace(4096, 262144, args.pool)).astype(int))
+    pool = _grid_pool(pool_sizes)
+    sizes = np.exp(rng.uniform(np.log(4096), np.log(262144), ngrids))
+    pick = [int(pool_sizes[np.argmin(np.abs(np.log(pool_sizes) - np.log(n)))]) for n in sizes]
+    nH = 10 ** rng.uniform(-4, -2, ngrids)
+    rate = 10 ** rng.uniform(47, 49, ngrids)
+    probs = [_sized_problem(pool[k], h, r) for k, h, r in zip(pick, nH, rate)]
+    dts = [4.0 / (I.ALPHA_B * h) / steps for h in nH]
+    bins = I.fibonacci_bins(42)
+    st = torch.cuda.Stream()
+    sol = [S.Solver(bins, seed=i, stream=st).load(p) for i, p in enumerate(probs)]
+    batch = S.Batch(ngrids, stream=st)
+    batch.step(sol, dts, 3)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(sol, dts, steps)
+    for s in sol:
+        s.sync()
+    t_batch = time.perf_counter() - t0
+    y_batch = [s.y for s in sol]
+    for s in sol:
+        s.close()
+    batch.close()
+    # one grid per launch sequence (sx_step, CUDA graphs), same work; loads
+    # are outside the timed region as for the batch
+    sol = [S.Solver(bins, seed=i, stream=st).load(p) for i, p in enumerate(probs)]
+    for s, dt in zip(sol, dts):
+        s.step(dt, 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, dt in zip(sol, dts):
+        s.step(dt, steps)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    y_plain = [s.y for s in sol]
+    for s in sol:
+        s.close()
+    same = all(np.array_equal(a, b) for a, b in zip(y_batch, y_plain))
+    nv = int(sum(int(p.interior.sum()) for p in probs))
+    print(json.dumps({
+        "mode": "batched", "grids": ngrids, "steps": steps, "interior_vertices": nv,
+        "pool_geometries": len(pool_sizes), "nbins": 42,
+        "batched": {"seconds": t_batch, "solves_per_s": ngrids / t_batch,
+                    "updates_per_s": nv * 42 * steps / t_batch},
+        "one_grid_per_launch": {"seconds": t_plain, "solves_per_s": ngrids / t_plain,
+                                "updates_per_s": nv * 42 * steps / t_plain},
+        "identical_results": same}), flush=True)
+
+
+def run_served(args):
+    """Poisson request stream: sizes log-uniform in [1e4, n_max] on pooled
+    geometries, uniform or clumpy-free Test-1 media, 42 or 84 bins, steps
+    uniform in [100, steps_max]; continuous batching under an HBM budget
+    against serving one request at a time."""
+    import torch
+
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import serve as SV
+
+    rng = np.random.default_rng(args.seed)
+    pool_sizes = np.unique(np.round(np.geomspace(1e4, args.serve_nmax, args.pool)).astype(int))
+    pool = _grid_pool(pool_sizes, seed0=2000)
+    t = 0.0
+    reqs = []
+    for rid in range(args.requests):
+        t += rng.exponential(1.0 / args.rate)
+        n = np.exp(rng.uniform(np.log(1e4), np.log(args.serve_nmax)))
+        k = int(pool_sizes[np.argmin(np.abs(np.log(pool_sizes) - np.log(n)))])
+        nH = 1e-3
+        rate = 10 ** rng.uniform(47.5, 49)
+        prob = _sized_problem(pool[k], nH, rate)
+        nb = int(rng.choice([42, 84]))
+        steps = int(rng.integers(100, args.serve_steps_max + 1))
+        dt = 4.0 / (I.ALPHA_B * nH) / steps
+        reqs.append(SV.Request(rid=rid, problem=prob, bins=I.fibonacci_bins(nb), steps=steps,
+                               dt=dt, seed=rid, arrival=t))
+    be = SV.GpuBackend()
+    free, total = torch.cuda.mem_get_info()
+    srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk)
+    srv.run(reqs)
+    be.close()
+    st_b = srv.stats()
+    res_b = {r.rid: r.y for r in reqs}
+    for r in reqs:
+        r.y = None
+    st_p = SV.serve_one_at_a_time(reqs)
+    same = all(np.array_equal(res_b[r.rid], r.y) for r in reqs)
+    print(json.dumps({"mode": "served", "requests": len(reqs), "rate_per_s": args.rate,
+                      "n_range": [1e4, args.serve_nmax], "pool_geometries": len(pool_sizes),
+                      "continuous_batching": st_b, "one_at_a_time": st_p,
+                      "identical_results": same}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +508,23 @@ def main(argv=None):
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["step", "batched", "served"], default="step")
+    ap.add_argument("--grids", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--pool", type=int, default=8)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--rate", type=float, default=50.0)
+    ap.add_argument("--serve-nmax", type=float, default=4e5)
+    ap.add_argument("--serve-steps-max", type=int, default=400)
+    ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args(argv)
+    if args.mode == "batched":
+        run_batched(args)
+        return
+    if args.mode == "served":
+        run_served(args)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank, world, local_rank = dist_env()

@@ -1,0 +1,111 @@
+"""Host-side logic of the serving loop, on the CPU with a fake backend:
+admission by HBM footprint, continuous batching by (bins, precision),
+rejection, load failures, cancellation."""
+import numpy as np
+import pytest
+
+from paper_0912_4273_gb300 import serve as SV
+
+
+class FakeProblem:
+    def __init__(self, n):
+        self.n = n
+        self.nnz = 16 * n
+
+
+class FakeBackend:
+    """Steps are counted, not computed; footprint = 100 B per vertex."""
+
+    def __init__(self, fail_rids=()):
+        self.steps = []        # (key, [rids], nsteps)
+        self.loaded = []
+        self.released = []
+        self.fail = set(fail_rids)
+
+    def footprint(self, req):
+        return 100 * req.problem.n
+
+    def load(self, req):
+        if req.rid in self.fail:
+            raise RuntimeError("simulated out of memory")
+        self.loaded.append(req.rid)
+        return {"rid": req.rid, "steps": 0}
+
+    def step(self, key, solvers, dts, n):
+        self.steps.append((key, [s["rid"] for s in solvers], n))
+        for s in solvers:
+            s["steps"] += n
+
+    def finish(self, s):
+        self.released.append(s["rid"])
+        return np.full(3, float(s["steps"])), {"emitted": 1.0}
+
+    def release(self, s):
+        self.released.append(s["rid"])
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-3
+        return self.t
+
+
+def req(rid, n, steps, nbins=42, arrival=0.0):
+    return SV.Request(rid=rid, problem=FakeProblem(n), bins=np.zeros((nbins, 3)), steps=steps,
+                      dt=1.0, arrival=arrival)
+
+
+def test_admission_respects_the_hbm_budget_and_batches_by_key():
+    be = FakeBackend()
+    srv = SV.Server(be, hbm_budget=100 * 3000, chunk_steps=8, clock=Clock())
+    rs = [req(0, 1000, 20), req(1, 1500, 12), req(2, 1000, 30, nbins=84), req(3, 400, 5)]
+    out = srv.run(rs)
+    assert all(r.status == "done" for r in out)
+    assert srv.peak_used <= 100 * 3000
+    # every grid got exactly its number of steps
+    for r in out:
+        assert r.y[0] == r.steps
+    # request 2 (84 bins) never shares a launch with 42-bin grids
+    for key, rids, n in be.steps:
+        assert all(key == ((84, 1) if rid == 2 else (42, 1)) for rid in rids)
+    # first fit: request 3 (small) passes request 2, which waits until memory frees
+    by = {r.rid: r for r in out}
+    assert by[3].t_admit < by[2].t_admit
+    assert by[2].t_admit > min(by[0].t_done, by[1].t_done, by[3].t_done)
+    assert srv.used == 0
+    st = srv.stats()
+    assert st["solves"] == 4 and st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_continuous_batching_joins_running_requests():
+    be = FakeBackend()
+    srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock())
+    srv.run([req(0, 100, 40), req(1, 100, 8, arrival=0.005)])
+    together = [rids for _, rids, _ in be.steps if len(rids) == 2]
+    assert together, "the later request must join the running batch"
+
+
+def test_rejection_failure_and_cancellation():
+    be = FakeBackend(fail_rids={1})
+    srv = SV.Server(be, hbm_budget=100 * 1000, clock=Clock())
+    srv.submit(req(5, 10, 100, arrival=1e9))  # far in the future, cancelled before it arrives
+    assert srv.cancel(5)
+    out = srv.run([req(0, 5000, 10), req(1, 100, 10), req(2, 100, 10)])
+    st = {r.rid: r.status for r in out}
+    assert st == {5: "cancelled", 0: "rejected", 1: "failed", 2: "done"}
+    assert srv.used == 0
+    assert "exceeds" in next(r for r in out if r.rid == 0).error
+
+
+def test_cancel_a_running_request_releases_its_memory():
+    be = FakeBackend()
+    srv = SV.Server(be, hbm_budget=10**9, clock=Clock())
+    srv.t0 = 0.0
+    srv.submit(req(0, 100, 1000))
+    srv._admit()
+    assert srv.used == 100 * 100
+    assert srv.cancel(0)
+    assert srv.used == 0 and be.released == [0]
