@@ -153,6 +153,32 @@ int sx_read_photons(sx_ctx *ctx, double *per_vertex, sx_budget *budget);
 /* Counters of the grid; synchronises the stream if kernel timing is on. */
 int sx_get_info(sx_ctx *ctx, sx_info *info);
 
+/* Dynamic grid, Sect. 2.1.4: where the optical depth fell, vertices are removed
+   down to a minimum resolution and the survivors are re-triangulated.
+   sx_grid_update_mark lists the vertices to remove: not sinks, not sources,
+   neutral fraction < y_thresh (the cell became transparent) and mean edge
+   length < min_spacing_cm (finer than the minimum resolution), keeping only
+   those whose such neighbours all have larger ids, so that no two removed
+   vertices are adjacent.  removed: caller buffer of capacity n, filled in
+   ascending order; *n_removed its length.  Errors: SX_EINVAL, SX_ESTATE. */
+int sx_grid_update_mark(sx_ctx *ctx, double y_thresh, double min_spacing_cm, int32_t *removed,
+                        int64_t *n_removed);
+
+/* Replace the grid by the survivors of the last sx_grid_update_mark (which must
+   come right before, without steps in between).  The caller re-triangulates
+   the survivors and passes their grid as for sx_load_grid, with old_of_new[i]
+   = the old id of new vertex i (n_new = n - n_removed entries, each survivor
+   once).  Photons in flight towards a removed vertex go to its nearest
+   surviving neighbour, same bin; neutral fractions, photons, sources, the
+   step count and the photon budget carry over; kappa is recomputed unless
+   fixed in sx_config.  d_workspace: a new caller-owned workspace for the new
+   grid (the old one may be released after the call).  Errors: SX_EINVAL,
+   SX_ENOMEM, SX_ESTATE, SX_ECUDA. */
+int sx_grid_update_apply(sx_ctx *ctx, int64_t n_new, const double *pos, const int64_t *row_ptr,
+                         const int32_t *col, const double *nH, const double *volume,
+                         const uint8_t *flags, const int32_t *old_of_new, void *d_workspace,
+                         int64_t workspace_bytes);
+
 /* enable = 1: bracket every step-kernel launch with a CUDA event pair on the
    context's stream and accumulate the durations (reported by sx_get_info);
    enabling resets the sums.  enable = 0: stop timing. */

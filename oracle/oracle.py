@@ -80,6 +80,11 @@ def lib():
             L.ox_get_vertex_consts.argtypes = [C.c_void_p, P(d), P(d), P(d)]
             L.ox_get_tables.argtypes = [C.c_void_p, P(i32), P(u8), P(d)]
             L.ox_associate_all.argtypes = [C.c_void_p, i64, P(i32)]
+            L.ox_mark_removal.argtypes = [C.c_void_p, d, d, P(i32)]
+            L.ox_mark_removal.restype = i64
+            L.ox_hand_over.argtypes = [C.c_void_p, i64, P(i32), P(d)]
+            L.ox_set_step.argtypes = [C.c_void_p, i64]
+            L.ox_set_budget.argtypes = [C.c_void_p, P(d)]
             L.dl_triangulate.argtypes = [i64, P(d), P(P(i32))]
             L.dl_triangulate.restype = i64
             L.dl_free.argtypes = [P(i32)]
@@ -268,6 +273,29 @@ class OracleSim:
         ml = np.zeros(self.n)
         lib().ox_get_tables(self.h, _p(q, C.c_int32), _p(st, C.c_uint8), _p(ml, C.c_double))
         return q[:nnz], st[:nnz], ml
+
+    def mark_removal(self, y_thresh: float, min_spacing: float) -> np.ndarray:
+        """Vertices the dynamic grid update removes (Sect. 2.1.4), ascending."""
+        out = np.zeros(self.n, dtype=np.int32)
+        k = lib().ox_mark_removal(self.h, y_thresh, min_spacing, _p(out, C.c_int32))
+        return out[:k].copy()
+
+    def rebuild(self, removed, problem_new, old_of_new, params=None):
+        """The state after the dynamic update on the re-triangulated survivors:
+        photons of removed vertices handed over, neutral fractions, step count,
+        budget and sources carried to the new grid (a new OracleSim)."""
+        removed = np.ascontiguousarray(removed, dtype=np.int32)
+        I = np.ascontiguousarray(self.I)
+        lib().ox_hand_over(self.h, len(removed), _p(removed, C.c_int32), _p(I, C.c_double))
+        old_of_new = np.asarray(old_of_new, dtype=np.int64)
+        y = self.y[old_of_new]
+        new = OracleSim(problem_new, params or self.p, self._keep["bins"], y0=y)
+        new.I = np.ascontiguousarray(I[old_of_new])
+        lib().ox_set_step(new.h, self.step_count)
+        b = np.array([self.budget[k] for k in ("emitted", "absorbed", "escaped", "in_flight")])
+        b[3] = float(new.I.sum())
+        lib().ox_set_budget(new.h, _p(np.ascontiguousarray(b), C.c_double))
+        return new
 
     def associate_all(self, step: int) -> np.ndarray:
         out = np.zeros((self.n, self.nbins), dtype=np.int32)

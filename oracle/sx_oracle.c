@@ -538,3 +538,66 @@ void ox_associate_all(const ox_sim *s, int64_t step, int32_t *assoc /* n*nbins *
                     : -1;
     free(qb);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Dynamic grid (Sect. 2.1.4): vertices where the optical depth fell are     */
+/* removed, but not below a minimum resolution.                              */
+/*   candidate: not a sink, not a source, neutral fraction y < y_thresh (the */
+/*   cell became transparent) and local spacing (mean edge length) below     */
+/*   min_spacing (finer than the minimum resolution);                        */
+/*   removed: a candidate all of whose candidate neighbours have larger ids  */
+/*   (no two removed vertices are adjacent).                                 */
+/* Returns the number removed; their ids, ascending, in removed_out.         */
+/* ------------------------------------------------------------------------ */
+int64_t ox_mark_removal(const ox_sim *s, double y_thresh, double min_spacing,
+                        int32_t *removed_out) {
+    const int64_t n = s->n;
+    uint8_t *cand = (uint8_t *)calloc((size_t)n + 1, 1);
+    for (int64_t i = 0; i < n; ++i) {
+        int is_src = 0;
+        for (int k = 0; k < s->nsrc; ++k) is_src |= (s->src_v[k] == i);
+        cand[i] = !(s->flags[i] & 1) && !is_src && s->y[i] < y_thresh && s->mean_len[i] < min_spacing;
+    }
+    int64_t nr = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!cand[i]) continue;
+        int ok = 1;
+        for (int64_t e = s->row_ptr[i]; e < s->row_ptr[i + 1]; ++e) {
+            int64_t j = s->col[e];
+            if (cand[j] && j < i) ok = 0;
+        }
+        if (ok) removed_out[nr++] = (int32_t)i;
+    }
+    free(cand);
+    return nr;
+}
+
+/* Photons arriving at a removed vertex go to its nearest surviving neighbour,
+   bin by bin (ties -> lowest id), removed vertices in ascending order.
+   I is n x nbins (the state between steps). */
+void ox_hand_over(const ox_sim *s, int64_t nr, const int32_t *removed, double *I) {
+    uint8_t *rem = (uint8_t *)calloc((size_t)s->n + 1, 1);
+    for (int64_t k = 0; k < nr; ++k) rem[removed[k]] = 1;
+    for (int64_t k = 0; k < nr; ++k) {
+        int64_t r = removed[k];
+        int64_t best = -1;
+        double bestd = 0.0;
+        for (int64_t e = s->row_ptr[r]; e < s->row_ptr[r + 1]; ++e) {
+            int64_t j = s->col[e];
+            if (rem[j]) continue;
+            double dx = s->pos[3 * j] - s->pos[3 * r], dy = s->pos[3 * j + 1] - s->pos[3 * r + 1],
+                   dz = s->pos[3 * j + 2] - s->pos[3 * r + 2];
+            double d2 = (dx * dx + dy * dy) + dz * dz;
+            if (best < 0 || d2 < bestd || (d2 == bestd && j < best)) {
+                best = j;
+                bestd = d2;
+            }
+        }
+        if (best < 0) continue;
+        for (int b = 0; b < s->nbins; ++b) I[(size_t)best * s->nbins + b] += I[(size_t)r * s->nbins + b];
+    }
+    free(rem);
+}
+
+void ox_set_step(ox_sim *s, int64_t step) { s->step = step; }
+void ox_set_budget(ox_sim *s, const double *b) { memcpy(s->budget, b, sizeof(double) * 4); }

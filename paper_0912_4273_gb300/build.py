@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBNAME = "libsimplexgb.so"
-SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_noalloc.cu"]
+SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_update.cu", "sx_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE]

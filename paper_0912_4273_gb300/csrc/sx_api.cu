@@ -27,6 +27,12 @@ struct sx_ctx {
   int32_t max_degree = 0;
   bool punit_set = false;  // FP32 photons are stored in units of g.punit photons
   bool profiling = false;
+  // dynamic grid update
+  bool marked = false;
+  int64_t mark_step = -1;
+  std::vector<int32_t> removed;
+  double carry_abs = 0.0, carry_esc = 0.0, carry_fly = 0.0;  // budget of replaced grids
+  bool fresh_update = false;  // no step since the last grid update
   // CUDA graph of kGraphSteps steps (rotation + step kernels), captured on the
   // context's stream for a given dt and source count and replayed by sx_step
   cudaGraphExec_t graph = nullptr;
@@ -113,6 +119,80 @@ static int bfail(sx_batch *b, int code, const std::string &msg) {
   return code;
 }
 
+// Copy a grid to the device workspace and build its tables (used by the load
+// and by the dynamic grid update).  Leaves the context's step and sources alone.
+static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr,
+                      const int32_t *col, const double *nH, const double *volume,
+                      const uint8_t *flags, const double *y0, void *d_workspace,
+                      int64_t workspace_bytes, sx::DevGrid &g, sx::Layout &L, double **bins_dev) {
+  if (n < 1 || !pos || !row_ptr || !nH || !volume || !flags || !d_workspace)
+    return fail(c, SX_EINVAL, "n < 1 or a required pointer is NULL");
+  const int64_t nnz = row_ptr[n];
+  if (row_ptr[0] != 0 || nnz < 0) return fail(c, SX_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (nnz > 0 && !col) return fail(c, SX_EINVAL, "col is NULL");
+  if (nnz >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "nnz must be < 2^31");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+    return fail(c, SX_EINVAL, "workspace must be 256-byte aligned");
+  const sx::Layout Lw = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision);
+  const int64_t need = (int64_t)(Lw.total + sizeof(double) * 3 * sx::kMaxBins + 256);
+  if (workspace_bytes < need)
+    return fail(c, SX_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  const cudaStream_t st = c->stream;
+  L = Lw;
+  g = sx::DevGrid{};
+  sx::bind_layout(g, d_workspace, L);
+  g.n = n;
+  g.nnz = nnz;
+  g.nbins = c->cfg.nbins;
+  g.nbp = (g.nbins + 3) / 4 * 4;
+  g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
+  g.precision = c->cfg.precision;
+  g.punit = 1.0;
+  *bins_dev = reinterpret_cast<double *>(static_cast<char *>(d_workspace) + L.total);
+  char *base = static_cast<char *>(d_workspace);
+  // zero the state that must start at zero
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_P0, 0, L.off_M0 - L.off_P0, st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_M0, 0, L.off_partials - L.off_M0, st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_partials, 0, L.off_tabs - L.off_partials, st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_steps, 0, sizeof(unsigned long long), st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_incoming, 0, sizeof(int), st));
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_src, 0, sizeof(double) * sx::kMaxSources, st));
+  // inputs
+  SX_CUDA(c, cudaMemcpyAsync(g.pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  if (nnz) SX_CUDA(c, cudaMemcpyAsync(g.s_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_nH, nH, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_vol, volume, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(g.s_flags, flags, n, cudaMemcpyHostToDevice, st));
+  if (y0) SX_CUDA(c, cudaMemcpyAsync(g.s_y0, y0, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(*bins_dev, c->bins.data(), sizeof(double) * c->bins.size(),
+                             cudaMemcpyHostToDevice, st));
+  // tables
+  SX_CUDA(c, sx::launch_setup(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
+  SX_CUDA(c, sx::launch_rotation(g, *bins_dev, c->cfg.seed, 0, 1, 1.0, st));
+  SX_CUDA(c, sx::launch_kappa_and_consts(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
+                                          y0 ? g.s_y0 : nullptr, st));
+  unsigned long long diag[sx::kDiagCount];
+  SX_CUDA(c, cudaMemcpyAsync(diag, g.diag, sizeof(diag), cudaMemcpyDeviceToHost, st));
+  SX_CUDA(c, cudaStreamSynchronize(st));
+  const unsigned long long errb = diag[sx::kDiagError];
+  c->max_degree = (int32_t)diag[sx::kDiagMaxDeg];
+  if (errb) {
+    std::string m = "malformed grid:";
+    if (errb & sx::kErrColRange) m += " neighbour id out of range;";
+    if (errb & sx::kErrSelfLoop) m += " self loop;";
+    if (errb & sx::kErrUnsorted) m += " row not sorted strictly ascending;";
+    if (errb & sx::kErrAsym) m += " CSR not symmetric;";
+    if (errb & sx::kErrRowPtr) m += " row_ptr not monotone;";
+    if (errb & sx::kErrDegree) m += " non-sink degree > " + std::to_string(SX_MAX_DEGREE) + ";";
+    return fail(c, SX_EINVAL, m);
+  }
+  SX_CUDA(c, cudaMemsetAsync(g.diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
+  return SX_OK;
+}
+
 extern "C" {
 
 void sx_config_default(sx_config *cfg) {
@@ -174,83 +254,151 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
                  const double *y0, void *d_workspace, int64_t workspace_bytes) {
   if (!c) return SX_EINVAL;
   c->loaded = false;
-  if (n < 1 || !pos || !row_ptr || !nH || !volume || !flags || !d_workspace)
-    return fail(c, SX_EINVAL, "n < 1 or a required pointer is NULL");
-  const int64_t nnz = row_ptr[n];
-  if (row_ptr[0] != 0 || nnz < 0) return fail(c, SX_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
-  if (nnz > 0 && !col) return fail(c, SX_EINVAL, "col is NULL");
-  if (nnz >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "nnz must be < 2^31");
-  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
-    return fail(c, SX_EINVAL, "workspace must be 256-byte aligned");
-  int64_t need = 0;
-  sx_workspace_bytes(c, n, nnz, &need);
-  if (workspace_bytes < need)
-    return fail(c, SX_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
-  SX_CUDA(c, cudaSetDevice(c->cfg.device));
-  const cudaStream_t st = c->stream;
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  c->L = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision);
-  sx::DevGrid &g = c->g;
-  g = sx::DevGrid{};
-  sx::bind_layout(g, d_workspace, c->L);
-  g.n = n;
-  g.nnz = nnz;
-  g.nbins = c->cfg.nbins;
-  g.nbp = (g.nbins + 3) / 4 * 4;
-  g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
-  g.precision = c->cfg.precision;
-  g.punit = 1.0;
+  int rc = build_grid(c, n, pos, row_ptr, col, nH, volume, flags, y0, d_workspace, workspace_bytes,
+                      c->g, c->L, &c->bins_dev);
+  if (rc) return rc;
+  c->g.punit = 1.0;
   c->punit_set = c->cfg.precision == SX_FP64;
-  c->bins_dev = reinterpret_cast<double *>(static_cast<char *>(d_workspace) + c->L.total);
-  char *base = static_cast<char *>(d_workspace);
-  // zero the state that must start at zero
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_P0, 0, c->L.off_M0 - c->L.off_P0, st));
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_M0, 0, c->L.off_partials - c->L.off_M0, st));
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_partials, 0, c->L.off_tabs - c->L.off_partials, st));
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_steps, 0, sizeof(unsigned long long), st));
-  SX_CUDA(c, cudaMemsetAsync(base + c->L.off_src, 0, sizeof(double) * sx::kMaxSources, st));
-  // inputs
-  SX_CUDA(c, cudaMemcpyAsync(g.pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-  SX_CUDA(c, cudaMemcpyAsync(g.s_row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
-  if (nnz) SX_CUDA(c, cudaMemcpyAsync(g.s_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
-  SX_CUDA(c, cudaMemcpyAsync(g.s_nH, nH, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  SX_CUDA(c, cudaMemcpyAsync(g.s_vol, volume, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  SX_CUDA(c, cudaMemcpyAsync(g.s_flags, flags, n, cudaMemcpyHostToDevice, st));
-  if (y0) SX_CUDA(c, cudaMemcpyAsync(g.s_y0, y0, sizeof(double) * n, cudaMemcpyHostToDevice, st));
-  SX_CUDA(c, cudaMemcpyAsync(c->bins_dev, c->bins.data(), sizeof(double) * c->bins.size(),
-                             cudaMemcpyHostToDevice, st));
-  // tables
-  SX_CUDA(c, sx::launch_setup(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
-  SX_CUDA(c, sx::launch_rotation(g, c->bins_dev, c->cfg.seed, 0, 1, 1.0, st));
-  SX_CUDA(c, sx::launch_kappa_and_consts(g, c->bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
-                                          y0 ? g.s_y0 : nullptr, st));
-  unsigned long long diag[sx::kDiagCount];
-  SX_CUDA(c, cudaMemcpyAsync(diag, g.diag, sizeof(diag), cudaMemcpyDeviceToHost, st));
-  SX_CUDA(c, cudaStreamSynchronize(st));
-  const unsigned long long errb = diag[sx::kDiagError];
-  c->max_degree = (int32_t)diag[sx::kDiagMaxDeg];
-  if (errb) {
-    std::string m = "malformed grid:";
-    if (errb & sx::kErrColRange) m += " neighbour id out of range;";
-    if (errb & sx::kErrSelfLoop) m += " self loop;";
-    if (errb & sx::kErrUnsorted) m += " row not sorted strictly ascending;";
-    if (errb & sx::kErrAsym) m += " CSR not symmetric;";
-    if (errb & sx::kErrRowPtr) m += " row_ptr not monotone;";
-    if (errb & sx::kErrDegree) m += " non-sink degree > " + std::to_string(SX_MAX_DEGREE) + ";";
-    return fail(c, SX_EINVAL, m);
-  }
-  SX_CUDA(c, cudaMemsetAsync(g.diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
   c->step = 0;
   c->emitted = 0.0;
+  c->carry_abs = c->carry_esc = c->carry_fly = 0.0;
+  c->fresh_update = false;
+  c->marked = false;
   c->src_vertex.clear();
   c->src_rate.clear();
   c->src_slot.clear();
-  g.nsrc = 0;
+  c->g.nsrc = 0;
   c->loaded = true;
+  return SX_OK;
+}
+
+int sx_grid_update_mark(sx_ctx *c, double y_thresh, double min_spacing, int32_t *removed,
+                        int64_t *n_removed) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!removed || !n_removed) return fail(c, SX_EINVAL, "NULL argument");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  sx::DevGrid &g = c->g;
+  // load-time scratch regions are free after the load
+  uint8_t *cand = g.s_flags;
+  uint8_t *rem = reinterpret_cast<uint8_t *>(g.s_y0);
+  int64_t *blk = reinterpret_cast<int64_t *>(g.s_nH);
+  int64_t *total_d = reinterpret_cast<int64_t *>(g.s_vol);
+  int32_t *ids = reinterpret_cast<int32_t *>(g.s_out);
+  SX_CUDA(c, sx::launch_mark(g, y_thresh, min_spacing, cand, rem, blk, total_d, ids, c->stream));
+  int64_t total = 0;
+  SX_CUDA(c, cudaMemcpyAsync(&total, total_d, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (total)
+    SX_CUDA(c, cudaMemcpyAsync(removed, ids, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, c->stream));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  *n_removed = total;
+  c->removed.assign(removed, removed + total);
+  c->marked = true;
+  c->mark_step = c->step;
+  return SX_OK;
+}
+
+int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int64_t *row_ptr,
+                         const int32_t *col, const double *nH, const double *volume,
+                         const uint8_t *flags, const int32_t *old_of_new, void *d_workspace,
+                         int64_t workspace_bytes) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!c->marked || c->mark_step != c->step)
+    return fail(c, SX_ESTATE, "sx_grid_update_mark must come right before sx_grid_update_apply");
+  if (!old_of_new) return fail(c, SX_EINVAL, "old_of_new is NULL");
+  sx::DevGrid &go = c->g;
+  if (n_new != go.n - (int64_t)c->removed.size())
+    return fail(c, SX_EINVAL, "n_new must be n minus the marked vertices");
+  std::vector<int32_t> new_of_old(go.n, -1);
+  {
+    std::vector<uint8_t> is_rem(go.n, 0);
+    for (int32_t r : c->removed) is_rem[r] = 1;
+    for (int64_t i = 0; i < n_new; ++i) {
+      const int32_t o = old_of_new[i];
+      if (o < 0 || o >= go.n || is_rem[o] || new_of_old[o] >= 0)
+        return fail(c, SX_EINVAL, "old_of_new must list every surviving vertex once");
+      new_of_old[o] = (int32_t)i;
+    }
+  }
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  const cudaStream_t st = c->stream;
+  // photons in flight towards every old vertex, per bin, into the old grid's
+  // free buffer; then the removed vertices hand theirs over
+  const int last = (int)((c->step + 1) & 1), freeb = last ^ 1;
+  const size_t tsz = c->cfg.precision == SX_FP64 ? sizeof(double) : sizeof(float);
+  if (c->step > 0) {
+    SX_CUDA(c, sx::launch_incoming_bins(go, last, go.P[freeb], st));
+  } else {
+    SX_CUDA(c, cudaMemsetAsync(go.P[freeb], 0, tsz * go.nbp * go.n, st));
+  }
+  SX_CUDA(c, sx::launch_hand_over(go, reinterpret_cast<uint8_t *>(go.s_y0),
+                                  reinterpret_cast<int32_t *>(go.s_out), go.P[freeb], st));
+  // budget so far
+  double tmp[3] = {0, 0, 0};
+  SX_CUDA(c, sx::launch_budget(go, st));
+  SX_CUDA(c, cudaMemcpyAsync(tmp, go.budget_dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
+  SX_CUDA(c, cudaStreamSynchronize(st));
+  // the new grid
+  sx::DevGrid gn{};
+  sx::Layout Ln{};
+  double *bins_new = nullptr;
+  int rc = build_grid(c, n_new, pos, row_ptr, col, nH, volume, flags, nullptr, d_workspace,
+                      workspace_bytes, gn, Ln, &bins_new);
+  if (rc) return rc;
+  gn.punit = go.punit;
+  const int64_t s = c->step;
+  const int prev_new = (int)((s & 1) ^ 1);
+  int32_t *d_map = reinterpret_cast<int32_t *>(gn.s_out);
+  SX_CUDA(c, cudaMemcpyAsync(d_map, old_of_new, sizeof(int32_t) * n_new, cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, sx::launch_carry(c->cfg.precision, n_new, gn.nbp, d_map, go.y, go.P[freeb], gn.y,
+                              gn.P[prev_new], st));
+  const unsigned long long sd = (unsigned long long)s;
+  const int inc = s > 0 ? 1 : 0;
+  SX_CUDA(c, cudaMemcpyAsync(gn.steps_done, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaMemcpyAsync(gn.incoming, &inc, sizeof(int), cudaMemcpyHostToDevice, st));
+  // sources keep their slots at their new ids (a source is never removed)
+  for (size_t k = 0; k < c->src_vertex.size(); ++k) {
+    const int32_t nv = new_of_old[c->src_vertex[k]];
+    const int32_t slot = (int32_t)k;
+    SX_CUDA(c, cudaMemcpyAsync(reinterpret_cast<char *>(gn.vc + nv) + offsetof(sx::VConst, src), &slot,
+                               sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    SX_CUDA(c, cudaMemcpyAsync(gn.src_rate + k, &c->src_rate[k], sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  gn.nsrc = (int)c->src_vertex.size();
+  // photons now in flight (the carried field)
+  const int nblk = 128;
+  double parts[nblk];
+  SX_CUDA(c, sx::launch_sum_rows(c->cfg.precision, n_new, gn.nbins, gn.nbp, gn.P[prev_new],
+                                 reinterpret_cast<double *>(gn.s_nH), nblk, st));
+  SX_CUDA(c, cudaMemcpyAsync(parts, gn.s_nH, sizeof(parts), cudaMemcpyDeviceToHost, st));
+  SX_CUDA(c, cudaStreamSynchronize(st));
+  double fly = 0.0;
+  for (int k = 0; k < nblk; ++k) fly += parts[k];
+  std::unordered_map<int32_t, int> slots;
+  for (size_t k = 0; k < c->src_vertex.size(); ++k) {
+    c->src_vertex[k] = new_of_old[c->src_vertex[k]];
+    slots[c->src_vertex[k]] = (int)k;
+  }
+  c->src_slot.swap(slots);
+  c->carry_abs += tmp[0] * go.punit;
+  c->carry_esc += tmp[1] * go.punit;
+  c->carry_fly = fly * go.punit;
+  c->fresh_update = true;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->g = gn;
+  c->L = Ln;
+  c->bins_dev = bins_new;
+  c->marked = false;
+  c->removed.clear();
   return SX_OK;
 }
 
@@ -288,6 +436,7 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
   ensure_punit(c, dt);
+  if (nsteps > 0) c->fresh_update = false;
   int32_t k0 = 0;
   if (!c->profiling && c->stream != nullptr && nsteps >= kGraphSteps) {
     // replay a captured block of steps: identical launches, the step index
@@ -369,12 +518,19 @@ int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
     SX_CUDA(c, cudaMemcpyAsync(tmp, c->g.budget_dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
     SX_CUDA(c, cudaStreamSynchronize(c->stream));
     b->emitted = c->emitted;
-    b->absorbed = tmp[0] * c->g.punit;
-    b->escaped = tmp[1] * c->g.punit;
-    b->in_flight = c->step > 0 ? tmp[2] * c->g.punit : 0.0;
+    b->absorbed = tmp[0] * c->g.punit + c->carry_abs;
+    b->escaped = tmp[1] * c->g.punit + c->carry_esc;
+    b->in_flight = c->fresh_update ? c->carry_fly : (c->step > 0 ? tmp[2] * c->g.punit : 0.0);
   }
   if (per_vertex) {
-    if (c->step == 0) {
+    if (c->fresh_update) {
+      const int prev = (int)((c->step & 1) ^ 1);
+      SX_CUDA(c, sx::launch_row_totals(c->cfg.precision, c->g.n, c->g.nbins, c->g.nbp, c->g.P[prev],
+                                       c->g.s_out, c->stream));
+      SX_CUDA(c, cudaMemcpyAsync(per_vertex, c->g.s_out, sizeof(double) * c->g.n, cudaMemcpyDeviceToHost, c->stream));
+      SX_CUDA(c, cudaStreamSynchronize(c->stream));
+      for (int64_t i = 0; i < c->g.n; ++i) per_vertex[i] *= c->g.punit;
+    } else if (c->step == 0) {
       std::memset(per_vertex, 0, sizeof(double) * c->g.n);
     } else {
       SX_CUDA(c, sx::launch_inflight(c->g, c->step, c->stream));
@@ -529,6 +685,7 @@ int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_
   SX_BCUDA(b, cudaEventRecord(b->ev, b->stream));
   for (int32_t i = 0; i < n; ++i) {
     sx_ctx *c = ctxs[i];
+    c->fresh_update = false;
     for (int32_t k = 0; k < nsteps; ++k)
       for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt_s[i];
     c->step += nsteps;

@@ -44,6 +44,8 @@ struct StepTables {
   int32_t attempts;
   int32_t remap;                  // 0: step 0, no previous orientation
   int32_t max_fanin;              // largest number of old bins moving into one new bin
+  int32_t incoming;               // 1: the stored photons of the previous buffer are this
+                                  //    step's incoming photons (after a grid update)
 };
 
 // Arguments of the rotation kernel for one grid.  The step index lives on the
@@ -62,6 +64,7 @@ struct RotArgs {
   double inv_punit;
   double *share;
   float *share_f;
+  int *incoming;                   // one-shot flag handed to the step tables, then cleared
 };
 
 // Arguments of the step kernel for one grid (the batched kernel takes an array).
@@ -176,6 +179,7 @@ struct DevGrid {
   int64_t nblocks;
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
   unsigned long long *steps_done;  // device step counter (advanced by the rotation kernel)
+  int *incoming;        // set by a grid update: the next step takes P[prev] as incoming photons
   double *src_rate;     // kMaxSources
   double *src_share;    // kMaxSources: photons per bin per step of each source, stored units
   float *src_share_f;   // the same in FP32
@@ -196,7 +200,7 @@ struct DevGrid {
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
-      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_diag, off_kpart, off_kappa, off_budget,
+      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       total;
   int64_t nblocks, nblocks_kappa;
@@ -224,6 +228,20 @@ cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, con
                               int nbins, int device, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
+// dynamic grid update (sx_update.cu)
+cudaError_t launch_mark(DevGrid &g, double y_thresh, double min_spacing, uint8_t *cand,
+                        uint8_t *rem, int64_t *blk, int64_t *total, int32_t *out,
+                        cudaStream_t st);
+cudaError_t launch_incoming_bins(DevGrid &g, int last, void *I, cudaStream_t st);
+cudaError_t launch_hand_over(DevGrid &g, const uint8_t *rem, int32_t *target, void *I,
+                             cudaStream_t st);
+cudaError_t launch_carry(int precision, int64_t n_new, int nbp, const int32_t *old_of_new,
+                         const double *y_old, const void *I_old, double *y_new, void *I_new,
+                         cudaStream_t st);
+cudaError_t launch_row_totals(int precision, int64_t n, int nbins, int nbp, const void *I,
+                              double *out, cudaStream_t st);
+cudaError_t launch_sum_rows(int precision, int64_t n, int nbins, int nbp, const void *I,
+                            double *part, int nblk, cudaStream_t st);
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
 
 }  // namespace sx

@@ -39,6 +39,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
   L.off_share = take(sizeof(double) * kMaxSources);
   L.off_share_f = take(sizeof(float) * kMaxSources);
   L.off_steps = take(sizeof(unsigned long long));
+  L.off_incoming = take(sizeof(int));
   L.off_diag = take(sizeof(unsigned long long) * kDiagCount);
   L.off_kpart = take(sizeof(double) * 2 * L.nblocks_kappa);
   L.off_kappa = take(sizeof(double));
@@ -74,6 +75,7 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.src_share = reinterpret_cast<double *>(b + L.off_share);
   g.src_share_f = reinterpret_cast<float *>(b + L.off_share_f);
   g.steps_done = reinterpret_cast<unsigned long long *>(b + L.off_steps);
+  g.incoming = reinterpret_cast<int *>(b + L.off_incoming);
   g.diag = reinterpret_cast<unsigned long long *>(b + L.off_diag);
   g.kappa_part = reinterpret_cast<double *>(b + L.off_kpart);
   g.nblocks_kappa = L.nblocks_kappa;

@@ -149,6 +149,12 @@ __device__ void rotation_body(const RotArgs &r) {
     out->step = s_step;
     out->remap = (!r.unrotated && s_step > 0) ? 1 : 0;
     out->max_fanin = mx;
+    int inc = 0;
+    if (!r.unrotated && r.incoming) {
+      inc = *r.incoming;
+      *r.incoming = 0;
+    }
+    out->incoming = inc;
   }
   __syncthreads();
   for (int b2 = t; b2 <= nbins; b2 += blockDim.x) out->inv_off[b2] = s_cnt[b2];
@@ -180,6 +186,7 @@ RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unr
   r.inv_punit = 1.0 / g.punit;
   r.share = g.src_share;
   r.share_f = g.src_share_f;
+  r.incoming = unrotated ? nullptr : g.incoming;
   return r;
 }
 
@@ -337,7 +344,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __shared__ uint32_t s_occ[kTile][MW];
   __shared__ T s_budw[kWarps][4];  // per warp: fly hi/lo, esc hi/lo (FP32) or fly, esc (FP64)
   __shared__ double s_abs, s_sink;
-  __shared__ int s_remap, s_fanin;
+  __shared__ int s_remap, s_fanin, s_incoming;
   __shared__ long long s_step;
   // Per-warp scratch, used by phase 1 (bin accumulators and the contribution
   // list) and, after the barrier, by phase 3 (staged edges, masks, bin list).
@@ -360,6 +367,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     s_remap = a.tab->remap;
     s_fanin = a.tab->max_fanin;
     s_step = a.tab->step;
+    s_incoming = a.tab->incoming;
   }
   __syncthreads();
 
@@ -383,6 +391,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
       for (int b = lane; b <= kMaxBins; b += 32) {
         acc_s[b] = T(0);
         cmp_s[b] = T(0);
+      }
+      if (s_incoming) {
+        // after a grid update the photons in flight arrive as a field in the
+        // previous buffer (the masks are all clear: no gather this step)
+        const T *__restrict__ Pin = Pp + (size_t)v * nbp;
+        for (int b = lane; b < nbins; b += 32) acc_s[b] = Pin[b];
       }
       __syncwarp();
       const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];

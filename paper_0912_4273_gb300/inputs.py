@@ -243,6 +243,25 @@ def cached(recipe, *args, cache_dir: str | None = None, **kw) -> Problem:
     return p
 
 
+def survivor_problem(problem: Problem, removed) -> tuple:
+    """The grid of the vertices that survive a removal (Sect. 2.1.4): the
+    survivors in their old order, re-triangulated by QHull, with their media,
+    flags and sources.  Returns (problem, old_of_new)."""
+    rem = np.zeros(problem.n, dtype=bool)
+    rem[np.asarray(removed, dtype=np.int64)] = True
+    keep = np.nonzero(~rem)[0]
+    new_of_old = np.full(problem.n, -1, dtype=np.int64)
+    new_of_old[keep] = np.arange(len(keep))
+    pts = np.ascontiguousarray(problem.pos[keep])
+    g = delaunay_graph(pts)
+    assert np.all(new_of_old[problem.src_vertex] >= 0), "sources are never removed"
+    p = Problem(pos=pts, row_ptr=g.row_ptr, col=g.col, nH=problem.nH[keep].copy(),
+                volume=g.volume, flags=problem.flags[keep].copy(),
+                src_vertex=new_of_old[problem.src_vertex].astype(np.int32),
+                src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta))
+    return p, keep.astype(np.int32)
+
+
 def point_process_problem(points: np.ndarray, nH, sink_mask=None, sources=()) -> Problem:
     """Wrap an explicit point set (tests): Delaunay graph + uniform volumes."""
     pts = np.ascontiguousarray(points, dtype=np.float64)

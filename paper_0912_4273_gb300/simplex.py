@@ -74,6 +74,11 @@ _SIGS = [
     ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
     ("sx_get_info", C.c_int, [C.c_void_p, _P(sx_info)]),
     ("sx_profile", C.c_int, [C.c_void_p, C.c_int]),
+    ("sx_grid_update_mark", C.c_int, [C.c_void_p, C.c_double, C.c_double, _P(C.c_int32),
+                                      _P(C.c_int64)]),
+    ("sx_grid_update_apply", C.c_int, [C.c_void_p, C.c_int64, _P(C.c_double), _P(C.c_int64),
+                                       _P(C.c_int32), _P(C.c_double), _P(C.c_double),
+                                       _P(C.c_uint8), _P(C.c_int32), C.c_void_p, C.c_int64]),
     ("sx_destroy", None, [C.c_void_p]),
     ("sx_last_error", C.c_char_p, [C.c_void_p]),
     ("sx_batch_workspace_bytes", C.c_int, [C.c_int32, _P(C.c_int64)]),
@@ -186,6 +191,23 @@ def sx_get_info(ctx) -> sx_info:
 
 def sx_profile(ctx, enable: bool):
     _check(ctx, lib().sx_profile(ctx, 1 if enable else 0))
+
+
+def sx_grid_update_mark(ctx, y_thresh: float, min_spacing: float, n: int) -> np.ndarray:
+    out = np.empty(max(n, 1), dtype=np.int32)
+    k = C.c_int64()
+    _check(ctx, lib().sx_grid_update_mark(ctx, y_thresh, min_spacing, _ptr(out, C.c_int32),
+                                          C.byref(k)))
+    return out[:k.value].copy()
+
+
+def sx_grid_update_apply(ctx, n_new, pos, row_ptr, col, nH, volume, flags, old_of_new,
+                         d_workspace: int, workspace_bytes: int):
+    _check(ctx, lib().sx_grid_update_apply(ctx, n_new, _ptr(pos, C.c_double),
+                                           _ptr(row_ptr, C.c_int64), _ptr(col, C.c_int32),
+                                           _ptr(nH, C.c_double), _ptr(volume, C.c_double),
+                                           _ptr(flags, C.c_uint8), _ptr(old_of_new, C.c_int32),
+                                           C.c_void_p(d_workspace), workspace_bytes))
 
 
 def sx_destroy(ctx):
@@ -377,6 +399,27 @@ class Solver:
         out = np.empty(self.n, dtype=np.float64)
         sx_read_photons(self.ctx, out)
         return out
+
+    def mark_removal(self, y_thresh: float, min_spacing: float) -> np.ndarray:
+        """Vertices the dynamic grid update would remove (ascending ids)."""
+        return sx_grid_update_mark(self.ctx, y_thresh, min_spacing, self.n)
+
+    def apply_update(self, problem_new, old_of_new):
+        """Continue on the re-triangulated survivors (state carried over)."""
+        pos = np.ascontiguousarray(problem_new.pos, dtype=np.float64)
+        rp = np.ascontiguousarray(problem_new.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(problem_new.col, dtype=np.int32)
+        nH = np.ascontiguousarray(problem_new.nH, dtype=np.float64)
+        vol = np.ascontiguousarray(problem_new.volume, dtype=np.float64)
+        fl = np.ascontiguousarray(problem_new.flags, dtype=np.uint8)
+        o2n = np.ascontiguousarray(old_of_new, dtype=np.int32)
+        nbytes = self.workspace_bytes(len(pos), int(rp[-1]))
+        ws = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        sx_grid_update_apply(self.ctx, len(pos), pos, rp, col, nH, vol, fl, o2n, ws.data_ptr(),
+                             ws.numel())
+        self.workspace = ws
+        self.n = len(pos)
+        return self
 
     def profile(self, enable: bool = True):
         sx_profile(self.ctx, enable)

@@ -231,3 +231,40 @@ def test_graph_replay_on_a_stream_matches_direct_launches(c0):
     r = O.OracleSim(prob, O.Params(nbins=42, seed=0), bins)
     r.step(DT, 40)
     assert np.abs(out[1][0] - r.y).max() <= 1e-4
+
+
+@pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
+                                                 (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
+def test_dynamic_update_parity(precision, ytol, btol):
+    """Mark, hand over, re-triangulate, carry on: removal set, budget and
+    neutral fractions agree with the oracle through the update."""
+    prob = I.stromgren_problem(4096, seed=11)
+    bins = I.fibonacci_bins(42)
+    ref = O.OracleSim(prob, O.Params(nbins=42, seed=11), bins)
+    kappa = ref.kappa
+    s = S.Solver(bins, precision=precision, seed=11, kappa=kappa).load(prob)
+    ref.step(DT, 80)
+    s.step(DT, 80)
+    _, _, ml = ref.tables()
+    spacing = float(np.median(ml) * 1.2)
+    rem = ref.mark_removal(1e-2, spacing)
+    rem_gpu = s.mark_removal(1e-2, spacing)
+    assert len(rem) > 10
+    assert np.array_equal(rem, rem_gpu)
+    p2, o2n = I.survivor_problem(prob, rem)
+    ref2 = ref.rebuild(rem, p2, o2n, params=O.Params(nbins=42, seed=11, kappa=kappa))
+    s.apply_update(p2, o2n)
+    assert s.info["step"] == 80 and s.n == p2.n
+    assert budget_err(s.budget, ref2.budget) <= btol
+    assert np.abs(s.photons() - ref2.I.sum(axis=1)).max() <= btol * ref2.budget["emitted"]
+    assert np.abs(s.y - ref2.y).max() <= ytol
+    for _ in range(2):
+        ref2.step(DT, 20)
+        s.step(DT, 20)
+        assert np.abs(s.y - ref2.y).max() <= ytol
+        assert budget_err(s.budget, ref2.budget) <= btol
+    # refused out of order: apply without a fresh mark
+    with pytest.raises(S.SimplexError) as e:
+        s.apply_update(p2, o2n)
+    assert e.value.code == S.SX_ESTATE
+    s.close()
