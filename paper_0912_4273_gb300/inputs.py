@@ -243,6 +243,68 @@ def cached(recipe, *args, cache_dir: str | None = None, **kw) -> Problem:
     return p
 
 
+def gaussian_random_field(mesh: int, slope: float = -3.0, seed: int = 0) -> np.ndarray:
+    """Zero-mean, unit-variance Gaussian random field on a periodic mesh^3
+    with power spectrum P(k) ~ k^slope (white noise shaped in Fourier space)."""
+    rng = np.random.default_rng(seed)
+    white = rng.standard_normal((mesh, mesh, mesh))
+    k1 = np.fft.fftfreq(mesh)
+    k3 = np.fft.rfftfreq(mesh)
+    kk = np.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + k3[None, None, :] ** 2)
+    amp = np.zeros_like(kk)
+    nz = kk > 0
+    amp[nz] = kk[nz] ** (slope / 2.0)
+    f = np.fft.irfftn(np.fft.rfftn(white) * amp, s=white.shape, axes=(0, 1, 2))
+    f -= f.mean()
+    return f / f.std()
+
+
+def lognormal_density(mesh: int = 128, sigma_ln: float = 1.5, slope: float = -3.0,
+                      nbar: float = 1e-3, seed: int = 0) -> np.ndarray:
+    """n = nbar exp(sigma delta - sigma^2 / 2) of a Gaussian field delta."""
+    d = gaussian_random_field(mesh, slope, seed)
+    return nbar * np.exp(sigma_ln * d - 0.5 * sigma_ln**2)
+
+
+def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13.2,
+                   nbar: float = 1e-3, sigma_ln: float = 1.5, nsrc: int = 16, seed: int = 0,
+                   margin_spacings: float = 1.5) -> Problem:
+    """Clumpy medium: a lognormal density on a mesh^3 grid, vertices drawn with
+    probability ~ n^(1/3) per cell and placed uniformly inside their cell
+    (n_H of the cell, nearest grid point), a sink shell around the box, and
+    nsrc sources at the centres of the nsrc densest cells with rates
+    log-uniform in [1e47, 1e49] photons/s."""
+    rng = np.random.default_rng(seed + 7)
+    rho = lognormal_density(mesh, sigma_ln, -3.0, nbar, seed)
+    L = box_kpc * KPC_CM
+    h = L / mesh
+    w = np.cbrt(rho).ravel()
+    counts = rng.multinomial(n_points - nsrc, w / w.sum())
+    cell = np.repeat(np.arange(mesh**3), counts)
+    ijk = np.stack(np.unravel_index(cell, (mesh,) * 3), axis=1)
+    pts = (ijk + rng.random((len(cell), 3))) * h
+    dens = np.argsort(rho.ravel())[::-1][:nsrc]
+    sijk = np.stack(np.unravel_index(dens, (mesh,) * 3), axis=1)
+    spts = (sijk + 0.5) * h
+    interior = np.concatenate([spts, pts])
+    nh_int = np.concatenate([rho.ravel()[dens], rho.ravel()[cell]])
+    shell = _sink_shell(rng, n_points, L, margin_spacings)
+    allp = np.concatenate([interior, shell])
+    nh = np.concatenate([nh_int, np.full(len(shell), nbar)])
+    flags = np.zeros(len(allp), dtype=np.uint8)
+    flags[len(interior):] = FLAG_SINK
+    order = morton_order(allp)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(len(order))
+    allp = np.ascontiguousarray(allp[order])
+    g = delaunay_graph(allp)
+    rates = 10.0 ** rng.uniform(47.0, 49.0, nsrc)
+    return Problem(pos=allp, row_ptr=g.row_ptr, col=g.col, nH=nh[order], volume=g.volume,
+                   flags=flags[order], src_vertex=inv[:nsrc].astype(np.int32), src_rate=rates,
+                   box=L, meta=dict(kind="clumpy", n_points=n_points, mesh=mesh, box_kpc=box_kpc,
+                                    nbar=nbar, sigma_ln=sigma_ln, nsrc=nsrc, seed=seed))
+
+
 def survivor_problem(problem: Problem, removed) -> tuple:
     """The grid of the vertices that survive a removal (Sect. 2.1.4): the
     survivors in their old order, re-triangulated by QHull, with their media,

@@ -268,3 +268,20 @@ def test_dynamic_update_parity(precision, ytol, btol):
         s.apply_update(p2, o2n)
     assert e.value.code == S.SX_ESTATE
     s.close()
+
+
+@pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
+                                                 (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
+def test_clumpy_medium_with_16_sources(precision, ytol, btol):
+    """Config-2 style medium (lognormal field, 16 sources) at a small size."""
+    prob = I.clumpy_problem(12000, mesh=24, nsrc=16, seed=4)
+    bins = I.fibonacci_bins(84)
+    ref = O.OracleSim(prob, O.Params(nbins=84, seed=4), bins)
+    s = S.Solver(bins, precision=precision, seed=4, kappa=ref.kappa).load(prob)
+    for _ in range(3):
+        ref.step(0.5 * I.MYR_S, 15)
+        s.step(0.5 * I.MYR_S, 15)
+        assert np.abs(s.y - ref.y).max() <= ytol
+        assert budget_err(s.budget, ref.budget) <= btol
+    assert s.info["nsources"] == 16
+    s.close()
