@@ -37,13 +37,12 @@ struct __align__(16) VConst {
 // Written once per step by the rotation kernel, read by every CTA.
 struct StepTables {
   float4 qb[kMaxBins];            // quantised rotated bins (x, y, z), as exact floats
-  int32_t inv_off[kMaxBins + 1];  // packets of old bins inv_idx[inv_off[b]..inv_off[b+1])
-  int32_t inv_idx[kMaxBins];      //   move to new bin b (ascending old index)
-  uchar4 inv3[kMaxBins];          // the same as up to 3 old bins per new bin, missing = kMaxBins
+  uint32_t qbq[kMaxBins];         // the same as signed bytes (x, y, z, 0), for byte dot products
+  unsigned char fwd[kMaxBins];    // closest bin of this step's orientation for every bin of
+                                  //   the previous one (identity when nothing is remapped)
   long long step;                 // the step these tables are for
   int32_t attempts;
   int32_t remap;                  // 0: step 0, no previous orientation
-  int32_t max_fanin;              // largest number of old bins moving into one new bin
   int32_t incoming;               // 1: the stored photons of the previous buffer are this
                                   //    step's incoming photons (after a grid update)
 };

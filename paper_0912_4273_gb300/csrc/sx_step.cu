@@ -6,19 +6,20 @@
 //               orientation (Sect. 2.2.3).
 //  k_step<T,MW> one launch per step, pull formulation.  A CTA owns a tile of
 //               32 consecutive vertices:
-//     phase 1   warp per vertex: gather the photons routed to it in the
-//               previous step (reverse edges, per-edge bin masks, fixed order,
-//               Kahan in FP32), move them to the new orientation, add the
-//               sources (Sect. 4.3), sum N_in;
-//     phase 2   lane per vertex: subcycled photoionisation / recombination in
-//               FP64 (Sect. 4.5), transmitted fraction f;
-//     phase 3   warp per vertex: O = f I; associate every bin with the edge of
-//               largest quantised dot product; split O over the <= 3 most
-//               straightforward neighbours of that edge (store O / |S| once
-//               and one bin mask per outgoing edge); budget partials.
+//     phase 1   warp per vertex, lane per in-edge: gather the packets routed
+//               to it in the previous step (per-edge bin masks), each moved to
+//               the closest bin of the new orientation and added in a fixed
+//               order (Kahan in FP32); add the sources (Sect. 4.3);
+//     phase 2   lane per vertex: N_in and the subcycled photoionisation /
+//               recombination in FP64 (Sect. 4.5), transmitted fraction f;
+//     phase 3   warp per vertex, lanes over (bin, edge): O = f I; associate
+//               every bin holding photons with the edge of largest quantised
+//               dot product; split O over the <= 3 most straightforward
+//               neighbours of that edge (store O / |S| once and one bin mask
+//               per outgoing edge); budget partials.
 //  k_budget     deterministic reduction of the per-CTA budget partials.
 //  k_inflight   photons in flight towards every vertex (readout).
-#include <float.h>
+#include <limits.h>
 
 #include "sx_internal.cuh"
 
@@ -105,6 +106,7 @@ __device__ void rotation_body(const RotArgs &r) {
     rotate_quantise(sR, r.bins + 3 * b, q);
     s_qn[b][0] = q[0]; s_qn[b][1] = q[1]; s_qn[b][2] = q[2];
     out->qb[b] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
+    out->qbq[b] = (uint32_t)(q[0] & 0xFF) | ((uint32_t)(q[1] & 0xFF) << 8) | ((uint32_t)(q[2] & 0xFF) << 16);
     rotate_quantise(sRp, r.bins + 3 * b, q);
     s_qo[b][0] = q[0]; s_qo[b][1] = q[1]; s_qo[b][2] = q[2];
   }
@@ -122,46 +124,20 @@ __device__ void rotation_body(const RotArgs &r) {
     s_map[b] = best;
   }
   __syncthreads();
-  // inverse of the map: the old bins of every new bin, ascending
-  __shared__ int s_cnt[kMaxBins + 1];
-  for (int b2 = t; b2 < nbins; b2 += blockDim.x) {
-    unsigned char i3[3] = {kMaxBins, kMaxBins, kMaxBins};
-    int c = 0;
-    for (int b = 0; b < nbins; ++b)
-      if (s_map[b] == b2) {
-        if (c < 3) i3[c] = (unsigned char)b;
-        c++;
-      }
-    out->inv3[b2] = make_uchar4(i3[0], i3[1], i3[2], (unsigned char)c);
-    s_cnt[b2] = c;
-  }
-  __syncthreads();
+  // packets of an old bin move to its closest new bin; nothing moves at step 0
+  const bool remap = !r.unrotated && s_step > 0;
+  for (int b = t; b < kMaxBins; b += blockDim.x)
+    out->fwd[b] = (unsigned char)((remap && b < nbins) ? s_map[b] : b);
   if (t == 0) {
-    int o = 0, mx = 0;
-    for (int b2 = 0; b2 < nbins; ++b2) {
-      const int c = s_cnt[b2];
-      s_cnt[b2] = o;
-      o += c;
-      mx = c > mx ? c : mx;
-    }
-    s_cnt[nbins] = o;
     out->attempts = s_att;
     out->step = s_step;
-    out->remap = (!r.unrotated && s_step > 0) ? 1 : 0;
-    out->max_fanin = mx;
+    out->remap = remap ? 1 : 0;
     int inc = 0;
     if (!r.unrotated && r.incoming) {
       inc = *r.incoming;
       *r.incoming = 0;
     }
     out->incoming = inc;
-  }
-  __syncthreads();
-  for (int b2 = t; b2 <= nbins; b2 += blockDim.x) out->inv_off[b2] = s_cnt[b2];
-  for (int b2 = t; b2 < nbins; b2 += blockDim.x) {
-    int o = s_cnt[b2];
-    for (int b = 0; b < nbins; ++b)
-      if (s_map[b] == b2) out->inv_idx[o++] = b;
   }
 }
 
@@ -262,7 +238,9 @@ __device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt,
 }
 
 // ----------------------------------------------------------------------------
-// Mask words of one edge.
+// Mask words of one edge: bin b is bit b % 32 of word b / 32.  Memory holds
+// 1, 2 or 4 words per edge; 65..96 bins are handled as 3 words in registers
+// and kept at the 16-byte stride of 4 (the fourth word is zero).
 // ----------------------------------------------------------------------------
 template <int MW>
 __device__ __forceinline__ void load_mask(const uint32_t *__restrict__ M, int64_t e, uint32_t m[MW]) {
@@ -273,7 +251,8 @@ __device__ __forceinline__ void load_mask(const uint32_t *__restrict__ M, int64_
     m[0] = v.x; m[1] = v.y;
   } else {
     const uint4 v = __ldg(reinterpret_cast<const uint4 *>(M) + e);
-    m[0] = v.x; m[1] = v.y; m[2] = v.z; m[3] = v.w;
+    m[0] = v.x; m[1] = v.y; m[2] = v.z;
+    if constexpr (MW == 4) m[3] = v.w;
   }
 }
 template <int MW>
@@ -282,6 +261,8 @@ __device__ __forceinline__ void store_mask(uint32_t *__restrict__ M, int64_t e, 
     M[e] = m[0];
   } else if constexpr (MW == 2) {
     reinterpret_cast<uint2 *>(M)[e] = make_uint2(m[0], m[1]);
+  } else if constexpr (MW == 3) {
+    reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], 0u);  // 16-byte stride
   } else {
     reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], m[3]);
   }
@@ -323,197 +304,201 @@ struct Acc<float> {
   __device__ void add(float x) { v = ff_add(v, x); }
 };
 
-// Exact int -> float for |i| < 2^22 without the conversion unit: the integer
-// is placed in the mantissa of 2^23 and 2^23 is subtracted.
-__device__ __forceinline__ float small_int_to_float(int i) {
-  return __int_as_float(0x4B000000 | (i + 0x200000)) - 8388608.f - 2097152.f;
-}
-
 #ifndef SX_STEP_MIN_BLOCKS
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
 #endif
+
+constexpr int kGroup = kTile / kWarps;  // consecutive vertices a warp works on together
+constexpr int kGroupCap = 96;           // out-edges of a group staged at once in phase 3
+constexpr int kLcap = 64;               // packets listed at once in phase 1
+
+// One round of photon packets arriving at the vertices of a warp's group:
+// lane i adds `val` to bin `key & 127` of group vertex `key >> 7` (if `on`).
+// Lanes of equal key add in lane order, one rank at a time, so every bin
+// sums its packets in list order.  The rows start at zero.
+template <typename T, int MW>
+__device__ __forceinline__ void add_round(T *grow, int nbs, uint32_t (*gocc)[MW], bool on,
+                                          int key, T val, uint32_t lt_mask) {
+  const int k = on ? key : (1 << 12) + (int)(threadIdx.x & 31);  // idle lanes: unique keys
+  const uint32_t grp = __match_any_sync(0xffffffffu, k);
+  const unsigned rank = __popc(grp & lt_mask);
+  const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
+  T *dst = grow + (k >> 7) * nbs + (k & 127);
+  for (unsigned r = 0; r <= maxr; ++r) {
+    if (on && rank == r) *dst += val;
+    __syncwarp();
+  }
+  if (on) atomicOr(&gocc[k >> 7][(k & 127) >> 5], 1u << (k & 31));
+}
+
+// Bins 0..nbins-1 that fall in mask word w.
+__device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
+  const int n = nbins - 32 * w;
+  return n >= 32 ? 0xffffffffu : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+// One tile of kTile consecutive vertices; warp w owns the group of kGroup
+// vertices kGroup w .. kGroup w + kGroup - 1 in phases 1 and 3, whose edges
+// are one contiguous range of the CSR arrays.
+//   phase 1  lanes over the group's in-edges: gather the packets routed to
+//            the group last step (per-edge bin masks), each moved to the
+//            closest bin of this step's orientation and added in a fixed
+//            order; add the sources.
+//   phase 2  lane per vertex: N_in, chemistry, transmitted fraction f.
+//   phase 3  lanes over the group's (vertex, bin) pairs holding photons: the
+//            edge closest to the bin, its straight set, O / |S|; then lanes
+//            over the group's out-edges write the bin masks at the receivers'
+//            in-edges.
+// Only bins that hold photons are touched: a bin without photons sets no mask
+// bit, so no reader looks at its stored value, and it is not written.
 template <typename T, int MW>
 __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][tile_stride(nbins)]
-  __shared__ float4 s_qb[kMaxBins];
-  __shared__ int32_t s_inv_off[kMaxBins + 1];
-  __shared__ int32_t s_inv_idx[kMaxBins];
-  __shared__ uchar4 s_inv3[kMaxBins];
+  __shared__ uint32_t s_qbq[kMaxBins];
+  __shared__ unsigned char s_fwd[kMaxBins];
   __shared__ T s_f[kTile];
   __shared__ uint32_t s_occ[kTile][MW];
+  __shared__ int32_t s_R[kWarps][kGroup + 1];  // row pointers of each warp's group
   __shared__ T s_budw[kWarps][4];  // per warp: fly hi/lo, esc hi/lo (FP32) or fly, esc (FP64)
   __shared__ double s_abs, s_sink;
-  __shared__ int s_remap, s_fanin, s_incoming;
+  __shared__ int s_incoming;
   __shared__ long long s_step;
-  // Per-warp scratch, used by phase 1 (bin accumulators and the contribution
-  // list) and, after the barrier, by phase 3 (staged edges, masks, bin list).
-  constexpr int kLcap = 64;
-  constexpr int kScr1 = 2 * (kMaxBins + 1) * (int)sizeof(T) + kLcap * 4 + kLcap;
-  constexpr int kScr3 = kMaxDeg * 16 + kMaxDeg * 4 + kMaxDeg * MW * 4 + kMaxBins;
+  // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
+  // phase 3 (the group's staged out-edges and masks, its occupied bins).
+  constexpr int kScr1 = kLcap * 4 + kLcap * 2;
+  constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * kMaxBins * 2;
   constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
-  const int nwords = (nbins + 31) >> 5;
-  for (int b = tid; b < nbins; b += kThreads) {
-    s_qb[b] = a.tab->qb[b];
-    s_inv_idx[b] = a.tab->inv_idx[b];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int b = tid; b < kMaxBins; b += kThreads) {
+    s_qbq[b] = a.tab->qbq[b];
+    s_fwd[b] = a.tab->fwd[b];
   }
-  for (int b = tid; b <= nbins; b += kThreads) s_inv_off[b] = a.tab->inv_off[b];
-  for (int b = tid; b < nbins; b += kThreads) s_inv3[b] = a.tab->inv3[b];
   if (tid == 0) {
-    s_remap = a.tab->remap;
-    s_fanin = a.tab->max_fanin;
     s_step = a.tab->step;
     s_incoming = a.tab->incoming;
   }
+  const int64_t v0 = tile * kTile;
+  const int g0 = warp * kGroup;          // first tile vertex of the warp's group
+  const int64_t vg = v0 + g0;            // its grid index
+  T *grow = s_I + (size_t)g0 * nbs;      // the group's rows
+  uint32_t(*gocc)[MW] = s_occ + g0;      // and occupancy
+  for (int i = lane; i < kGroup * nbs; i += 32) grow[i] = T(0);
+  if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
+  if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
+  // the tile's running budget, read now so that the load overlaps the tile
+  double run_abs = 0.0, run_esc = 0.0;
+  if (tid == 0) {
+    run_abs = a.partials[4 * tile];
+    run_esc = a.partials[4 * tile + 1];
+  }
   __syncthreads();
 
-  const int64_t v0 = tile * kTile;
   const int cur = (int)(s_step & 1);
   const T *__restrict__ Pp = static_cast<const T *>(a.P[cur ^ 1]);
   T *__restrict__ Pn = static_cast<T *>(a.P[cur]);
   const uint32_t *__restrict__ M_prev = a.M[cur ^ 1];
   uint32_t *__restrict__ M_next = a.M[cur];
+  int32_t R[kGroup + 1];
+#pragma unroll
+  for (int g = 0; g <= kGroup; ++g) R[g] = s_R[warp][g];
 
   // ---------------- phase 1: gather, remap, sources ----------------
   {
-    T *acc_s = reinterpret_cast<T *>(s_scr[warp]);  // [kMaxBins + 1], old orientation
-    T *cmp_s = acc_s + (kMaxBins + 1);                 // Kahan compensation
-    int32_t *lsrc = reinterpret_cast<int32_t *>(cmp_s + (kMaxBins + 1));
-    unsigned char *lbin = reinterpret_cast<unsigned char *>(lsrc + kLcap);
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int vl = warp; vl < kTile; vl += kWarps) {
-      const int64_t v = v0 + vl;
-      if (v >= a.n) break;
-      for (int b = lane; b <= kMaxBins; b += 32) {
-        acc_s[b] = T(0);
-        cmp_s[b] = T(0);
-      }
-      if (s_incoming) {
-        // after a grid update the photons in flight arrive as a field in the
-        // previous buffer (the masks are all clear: no gather this step)
-        const T *__restrict__ Pin = Pp + (size_t)v * nbp;
-        for (int b = lane; b < nbins; b += 32) acc_s[b] = Pin[b];
-      }
-      __syncwarp();
-      const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
-      for (int32_t e0 = r0; e0 < r1; e0 += 32) {
-        // lane k fetches in-edge e0 + k: its source and the sender's bin mask
-        int32_t my_src = 0;
-        uint32_t my_m[MW];
-#pragma unroll
-        for (int w = 0; w < MW; ++w) my_m[w] = 0u;
-        if (e0 + lane < r1) {
-          const Edge E = a.edges[e0 + lane];
-          my_src = E.col;
-          load_mask<MW>(M_prev, E.twin, my_m);
+    int32_t *lsrc = reinterpret_cast<int32_t *>(s_scr[warp]);     // [kLcap] sender
+    uint16_t *lkey = reinterpret_cast<uint16_t *>(lsrc + kLcap);  // [kLcap] vertex << 7 | old bin
+    if (s_incoming) {
+      // after a grid update the photons in flight arrive as a field in the
+      // previous buffer (the masks are all clear: no gather this step)
+      for (int g = 0; g < kGroup; ++g) {
+        if (vg + g >= a.n) break;
+        const T *__restrict__ Pin = Pp + (size_t)(vg + g) * nbp;
+        for (int b0 = 0; b0 < nbins; b0 += 32) {
+          const int b = b0 + lane;
+          const T val = b < nbins ? Pin[b] : T(0);
+          const bool on = val != T(0);
+          add_round<T, MW>(grow, nbs, gocc, on, on ? ((g << 7) | s_fwd[b]) : 0, val, lt_mask);
         }
-        int cnt = 0;
+      }
+    }
+    for (int32_t e0 = R[0]; e0 < R[kGroup]; e0 += 32) {
+      // lane: in-edge e of group vertex g, its sender and the bins the
+      // sender routed along it (written at this edge's index)
+      const int32_t e = e0 + lane;
+      int g = 0;
 #pragma unroll
-        for (int w = 0; w < MW; ++w) cnt += __popc(my_m[w]);
-        int incl = cnt;
+      for (int q = 1; q < kGroup; ++q) g += (e >= R[q]) ? 1 : 0;
+      int32_t my_src = 0;
+      uint32_t my_m[MW];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const int t = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += t;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        if (total <= kLcap) {
-          // contribution list (source, bin) in (edge, bin) order; the loads
-          // are independent, and the adds run in rounds of equal rank within
-          // a bin, so every bin sums its contributions in ascending edge order
-          int pos = incl - cnt;
+      for (int w = 0; w < MW; ++w) my_m[w] = 0u;
+      if (e < R[kGroup]) {
+        my_src = a.edges[e].col;
+        load_mask<MW>(M_prev, (int64_t)e, my_m);
+      }
+      int cnt = 0;
 #pragma unroll
-          for (int w = 0; w < MW; ++w) {
-            uint32_t m = my_m[w];
-            while (m) {
-              const int i = __ffs(m) - 1;
-              m &= m - 1u;
+      for (int w = 0; w < MW; ++w) cnt += __popc(my_m[w]);
+      int incl = cnt;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      // the packets as a list (sender, vertex, old bin) in (edge, bin) order,
+      // kLcap entries at a time
+      for (int p0 = 0; p0 < total; p0 += kLcap) {
+        int pos = incl - cnt - p0;
+        const bool all = total <= kLcap;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          uint32_t m = my_m[w];
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            if (all || (pos >= 0 && pos < kLcap)) {
               lsrc[pos] = my_src;
-              lbin[pos] = (unsigned char)(32 * w + i);
-              ++pos;
+              lkey[pos] = (uint16_t)((g << 7) | (32 * w + i));
             }
+            ++pos;
           }
-          __syncwarp();
-          for (int j0 = 0; j0 < total; j0 += 32) {
-            const int j = j0 + lane;
-            const bool on = j < total;
-            const int b = on ? (int)lbin[j] : (kMaxBins + 1 + lane);  // idle lanes: unique keys
-            T val = T(0);
-            if (on) val = Pp[(size_t)lsrc[j] * nbp + b];
-            const uint32_t grp = __match_any_sync(0xffffffffu, b);
-            const unsigned rank = __popc(grp & lt_mask);
-            const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
-            for (unsigned r = 0; r <= maxr; ++r) {
-              if (on && rank == r) {
-                T A = acc_s[b], Cc = cmp_s[b];
-                acc_add<T>(A, Cc, val);
-                acc_s[b] = A;
-                cmp_s[b] = Cc;
-              }
-              __syncwarp();
-            }
-          }
-          __syncwarp();
-        } else {
-          // many contributions: lane per bin, one in-edge after the other
-          uint32_t my_wm = 0u;
-#pragma unroll
-          for (int w = 0; w < MW; ++w) my_wm |= (my_m[w] != 0u ? 1u : 0u) << w;
-          uint32_t live = __ballot_sync(0xffffffffu, my_wm != 0u);
-          while (live) {
-            const int k = __ffs(live) - 1;
-            live &= live - 1u;
-            const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
-            const T *__restrict__ Ps = Pp + (size_t)src * nbp;
-#pragma unroll
-            for (int w = 0; w < MW; ++w) {
-              if (w < nwords) {
-                const uint32_t mw = __shfl_sync(0xffffffffu, my_m[w], k);
-                if ((mw >> lane) & 1u) {
-                  const int b = lane + 32 * w;
-                  T A = acc_s[b], Cc = cmp_s[b];
-                  acc_add<T>(A, Cc, Ps[b]);
-                  acc_s[b] = A;
-                  cmp_s[b] = Cc;
-                }
-              }
-            }
-          }
-          __syncwarp();
         }
-      }
-      // move packets to the closest bin of this step's orientation (old bins
-      // in ascending order, as the plain definition adds them), add sources
-      T *row = s_I + (size_t)vl * nbs;
-      const int src = a.vc[v].src;
-      T share = T(0);
-      if (src >= 0) {
-        if constexpr (sizeof(T) == 8) share = a.src_share[src]; else share = a.src_share_f[src];
-      }
-#pragma unroll
-      for (int w = 0; w < MW; ++w) {
-        const int b = lane + 32 * w;
-        T s = T(0);
-        if (b < nbins) {
-          if (!s_remap) {
-            s = acc_s[b];
-          } else if (s_fanin <= 3) {
-            const uchar4 i3 = s_inv3[b];
-            s = (acc_s[i3.x] + acc_s[i3.y]) + acc_s[i3.z];
-          } else {
-            for (int j = s_inv_off[b]; j < s_inv_off[b + 1]; ++j) s = s + acc_s[s_inv_idx[j]];
+        __syncwarp();
+        const int nl = min(total - p0, kLcap);
+        for (int j0 = 0; j0 < nl; j0 += 32) {
+          const int j = j0 + lane;
+          const bool on = j < nl;
+          int key = 0;
+          T val = T(0);
+          if (on) {
+            const int kk = lkey[j];
+            const int bo = kk & 127;
+            val = Pp[(size_t)lsrc[j] * nbp + bo];
+            key = (kk & ~127) | s_fwd[bo];
           }
-          if (src >= 0) s = s + share;
-          row[b] = s;
+          add_round<T, MW>(grow, nbs, gocc, on, key, val, lt_mask);
         }
-        const uint32_t occ = __ballot_sync(0xffffffffu, s != T(0));
-        if (lane == 0) s_occ[vl][w] = occ;  // bins of the vertex that hold photons
+        __syncwarp();
       }
+    }
+    // a source puts its share in every bin
+    int vsrc = -1;
+    if (lane < kGroup && vg + lane < a.n) vsrc = a.vc[vg + lane].src;
+    uint32_t srcs = __ballot_sync(0xffffffffu, vsrc >= 0);
+    while (srcs) {
+      const int g = __ffs(srcs) - 1;
+      srcs &= srcs - 1u;
+      const int slot = __shfl_sync(0xffffffffu, vsrc, g);
+      T share;
+      if constexpr (sizeof(T) == 8) share = a.src_share[slot]; else share = a.src_share_f[slot];
+      T *row = grow + (size_t)g * nbs;
+      for (int b = lane; b < nbins; b += 32) row[b] += share;
+      if (lane < MW) gocc[g][lane] = word_bins(nbins, lane);
       __syncwarp();
     }
   }
@@ -586,98 +571,93 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __syncthreads();
 
   // ---------------- phase 3: transmit, associate, route ----------------
-  // Only bins that hold photons are routed.  A bin without photons sets no
-  // mask bit, so no reader ever looks at its stored value: it is not written.
   Acc<T> fly, esc;
-  float4 *s_eq = reinterpret_cast<float4 *>(s_scr[warp]);            // [kMaxDeg]
-  uint32_t *s_st = reinterpret_cast<uint32_t *>(s_eq + kMaxDeg);     // [kMaxDeg]
-  uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_st + kMaxDeg);  // [kMaxDeg][MW]
-  unsigned char *s_act = reinterpret_cast<unsigned char *>(s_am + kMaxDeg);  // [kMaxBins]
-  for (int vl = warp; vl < kTile; vl += kWarps) {
-    const int64_t v = v0 + vl;
-    if (v >= a.n) break;
-    const T *row = s_I + (size_t)vl * nbs;
-    T *__restrict__ Pv = Pn + (size_t)v * nbp;
-    const int32_t r0 = a.row_ptr[v], r1 = a.row_ptr[v + 1];
-    const int deg = r1 - r0;
-    const int flags = a.vc[v].flags;
-    const T f = s_f[vl];
-    if ((flags & 1) || deg == 0 || deg > kMaxDeg) {
-      // sinks pass nothing on; a vertex without edges loses what it transmits
-      if (!(flags & 1))
-        for (int b = lane; b < nbins; b += 32) esc.add(row[b] * f);
-      for (int k = lane; k < deg; k += 32) {
-        uint32_t z[MW];
+  {
+    uint2 *s_qs = reinterpret_cast<uint2 *>(s_scr[warp]);                        // [kGroupCap] q bytes, straight set
+    uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_qs + kGroupCap);  // [kGroupCap][MW]
+    uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * kMaxBins]
+    int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
+    if (lane < kGroup && vg + lane < a.n) vflags = a.vc[vg + lane].flags;
+    const uint32_t sinks = __ballot_sync(0xffffffffu, vflags & 1);
+    // consecutive vertices ga .. gb - 1 whose out-edges fit in the staging area
+    for (int ga = 0; ga < kGroup;) {
+      int gb = ga + 1;
+      while (gb < kGroup && s_R[warp][gb + 1] - s_R[warp][ga] <= kGroupCap) ++gb;
+      const int32_t EA = s_R[warp][ga], EB = s_R[warp][gb];
+      for (int32_t e = EA + lane; e < EB; e += 32) {
+        const int idx = e - EA;
+        if (idx < kGroupCap) {
+          const Edge E = a.edges[e];
+          uint32_t qw, stw;
+          memcpy(&qw, &E.q, 4);
+          memcpy(&stw, &E.st, 4);
+          s_qs[idx] = make_uint2(qw, stw);
 #pragma unroll
-        for (int w = 0; w < MW; ++w) z[w] = 0u;
-        store_mask<MW>(M_next, (int64_t)r0 + k, z);
+          for (int w = 0; w < MW; ++w) s_am[idx][w] = 0u;
+        }
       }
-      continue;
-    }
-    // stage the vertex's edges: 64 q as exact floats and 63 - k in w (the
-    // packed argmax below); the straight table apart
-    for (int k = lane; k < deg; k += 32) {
-      const Edge E = a.edges[r0 + k];
-      uint32_t stw;
-      memcpy(&stw, &E.st, 4);
-      s_eq[k] = make_float4(small_int_to_float(E.q.x) * 64.f, small_int_to_float(E.q.y) * 64.f,
-                            small_int_to_float(E.q.z) * 64.f, small_int_to_float(63 - k));
-      s_st[k] = stw;
+      // the (vertex, bin) pairs holding photons, vertex-major, bins ascending;
+      // sinks pass nothing on
+      int np = 0;
+      for (int g = ga; g < gb; ++g) {
+        if ((sinks >> g) & 1u) continue;
 #pragma unroll
-      for (int w = 0; w < MW; ++w) s_am[k][w] = 0u;
-    }
-    // list the occupied bins (ascending)
-    int nact = 0;
-#pragma unroll
-    for (int w = 0; w < MW; ++w) {
-      const uint32_t occ = s_occ[vl][w];
-      if ((occ >> lane) & 1u) s_act[nact + __popc(occ & ((1u << lane) - 1u))] = (unsigned char)(lane + 32 * w);
-      nact += __popc(occ);
-    }
-    __syncwarp();
-    for (int j0 = 0; j0 < nact; j0 += 32) {
-      const int j = j0 + lane;
-      if (j < nact) {
-        const int b = s_act[j];
-        const T O = row[b] * f;
-        if (O != T(0)) {
-          const float4 qb = s_qb[b];
-          float best = -FLT_MAX;
-          for (int k = 0; k < deg; ++k) {
-            const float4 qe = s_eq[k];
-            // (q_e . q_b) * 64 + (63 - k): an exact integer below 2^22 in FP32;
-            // the max picks the largest dot and, among equal dots, the lowest slot
-            best = fmaxf(best, fmaf(qe.x, qb.x, fmaf(qe.y, qb.y, fmaf(qe.z, qb.z, qe.w))));
-          }
-          // low 6 bits of the integer: add 1.5 * 2^23 and read the mantissa
-          const int kb = 63 - (__float_as_int(best + 12582912.f) & 63);
-          const uint32_t stw = s_st[kb];
-          const int cnt = (int)(stw >> 24);
-          if (cnt == 0) {
-            esc.add(O);
-          } else {
-            T P;
-            if constexpr (sizeof(T) == 8) {
-              P = O / (T)cnt;
+        for (int w = 0; w < MW; ++w) {
+          const uint32_t occ = gocc[g][w];
+          if ((occ >> lane) & 1u) s_pair[np + __popc(occ & lt_mask)] = (uint16_t)((g << 7) | (32 * w + lane));
+          np += __popc(occ);
+        }
+      }
+      __syncwarp();
+      for (int j0 = 0; j0 < np; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < np) {
+          const int pk = s_pair[j];
+          const int g = pk >> 7, b = pk & 127;
+          const T O = grow[(size_t)g * nbs + b] * s_f[g0 + g];
+          if (O != T(0)) {
+            const int ka = s_R[warp][g] - EA;
+            const int dg = s_R[warp][g + 1] - s_R[warp][g];
+            if (dg == 0 || dg > kMaxDeg) {
+              esc.add(O);  // a vertex without (usable) edges loses what it transmits
             } else {
-              P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
+              // key (q_e . q_b) * 64 + 2^22 + (63 - k): largest for the largest
+              // dot and, among equal dots, the lowest slot
+              const int qb = (int)s_qbq[b];
+              int key = INT_MIN, c = (1 << 22) + 63;
+              for (int k = 0; k < dg; ++k, --c) key = max(key, __dp4a((int)s_qs[ka + k].x, qb, 0) * 64 + c);
+              const int kst = 63 - (key & 63);
+              const uint32_t stw = s_qs[ka + kst].y;
+              const int cnt = (int)(stw >> 24);
+              if (cnt == 0) {
+                esc.add(O);
+              } else {
+                T P;
+                if constexpr (sizeof(T) == 8) {
+                  P = O / (T)cnt;
+                } else {
+                  P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
+                }
+                fly.add(O);
+                Pn[(size_t)(vg + g) * nbp + b] = P;
+                const uint32_t bit = 1u << (b & 31);
+                for (int m = 0; m < cnt; ++m) atomicOr(&s_am[ka + ((stw >> (8 * m)) & 0xFFu)][b >> 5], bit);
+              }
             }
-            fly.add(O);
-            const uint32_t bit = 1u << (b & 31);
-            for (int m = 0; m < cnt; ++m) atomicOr(&s_am[(stw >> (8 * m)) & 0xFFu][b >> 5], bit);
-            Pv[b] = P;
           }
         }
       }
-    }
-    __syncwarp();
-    for (int k = lane; k < deg; k += 32) {
-      uint32_t m[MW];
+      __syncwarp();
+      for (int32_t e = EA + lane; e < EB; e += 32) {
+        const int idx = e - EA;
+        uint32_t m[MW];
 #pragma unroll
-      for (int w = 0; w < MW; ++w) m[w] = s_am[k][w];
-      store_mask<MW>(M_next, (int64_t)r0 + k, m);
+        for (int w = 0; w < MW; ++w) m[w] = idx < kGroupCap ? s_am[idx][w] : 0u;
+        store_mask<MW>(M_next, (int64_t)a.edges[e].twin, m);  // at the receiver's in-edge index
+      }
+      __syncwarp();
+      ga = gb;
     }
-    __syncwarp();
   }
   // ---------------- budget partials of the tile ----------------
   if constexpr (sizeof(T) == 8) {
@@ -696,10 +676,21 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     }
   }
   if (warp < kTile / 32) {  // the chemistry lanes hold absorbed and sink photons
-    const double ab = warp_sum_d(bud_abs), sk = warp_sum_d(bud_sink);
-    if (lane == 0) {
-      s_abs = ab;
-      s_sink = sk;
+    if constexpr (sizeof(T) == 8) {
+      const double ab = warp_sum_d(bud_abs), sk = warp_sum_d(bud_sink);
+      if (lane == 0) {
+        s_abs = ab;
+        s_sink = sk;
+      }
+    } else {
+      // float-float of each lane's FP64 value, summed on the FP32 pipe
+      const float ah = (float)bud_abs, sh = (float)bud_sink;
+      const FF fa = ff_warp_sum(FF{ah, (float)(bud_abs - (double)ah)});
+      const FF fs = ff_warp_sum(FF{sh, (float)(bud_sink - (double)sh)});
+      if (lane == 0) {
+        s_abs = ff_to_double(fa);
+        s_sink = ff_to_double(fs);
+      }
     }
   }
   __syncthreads();
@@ -722,8 +713,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
       es = ff_to_double(F2);
     }
     double *p = a.partials + 4 * tile;
-    p[0] += s_abs;
-    p[1] += s_sink + es;
+    p[0] = run_abs + s_abs;
+    p[1] = run_esc + (s_sink + es);
     p[2] = fl;
   }
   __syncthreads();  // shared state is reused by the next tile of a persistent CTA
@@ -794,6 +785,9 @@ static void configure_smem() {
   }
 }
 
+// Mask words a step kernel works with for nbins bins.
+static int compute_words(int nbins) { return nbins <= 32 ? 1 : nbins <= 64 ? 2 : nbins <= 96 ? 3 : 4; }
+
 template <typename T, int MW>
 static cudaError_t launch_step_t(DevGrid &g, double dt, double fc, double tol, int max_sub,
                                  cudaStream_t st) {
@@ -806,13 +800,16 @@ static cudaError_t launch_step_t(DevGrid &g, double dt, double fc, double tol, i
 
 cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st) {
+  const int w = compute_words(g.nbins);
   if (g.precision == 0) {
-    if (g.mw == 1) return launch_step_t<double, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-    if (g.mw == 2) return launch_step_t<double, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+    if (w == 1) return launch_step_t<double, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+    if (w == 2) return launch_step_t<double, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+    if (w == 3) return launch_step_t<double, 3>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
     return launch_step_t<double, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
   }
-  if (g.mw == 1) return launch_step_t<float, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-  if (g.mw == 2) return launch_step_t<float, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (w == 1) return launch_step_t<float, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (w == 2) return launch_step_t<float, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (w == 3) return launch_step_t<float, 3>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
   return launch_step_t<float, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
 }
 
@@ -837,13 +834,17 @@ static cudaError_t launch_batch_t(const StepArgs *d_args, const int64_t *d_prefi
 cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int device, cudaStream_t st) {
+  (void)mw;  // the memory words follow from nbins
+  const int w = compute_words(nbins);
   if (precision == 0) {
-    if (mw == 1) return launch_batch_t<double, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-    if (mw == 2) return launch_batch_t<double, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+    if (w == 1) return launch_batch_t<double, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+    if (w == 2) return launch_batch_t<double, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+    if (w == 3) return launch_batch_t<double, 3>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
     return launch_batch_t<double, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
   }
-  if (mw == 1) return launch_batch_t<float, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-  if (mw == 2) return launch_batch_t<float, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  if (w == 1) return launch_batch_t<float, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  if (w == 2) return launch_batch_t<float, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  if (w == 3) return launch_batch_t<float, 3>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
   return launch_batch_t<float, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
 }
 
@@ -891,7 +892,7 @@ __global__ void k_inflight(int64_t n, int nbins, int nbp, const int32_t *__restr
   for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
     const Edge E = edges[e];
     uint32_t m[MW];
-    load_mask<MW>(M, E.twin, m);
+    load_mask<MW>(M, e, m);
 #pragma unroll
     for (int w = 0; w < MW; ++w) {
       const int b = lane + 32 * w;

@@ -125,12 +125,12 @@ __global__ void k_incoming_bins(int64_t n, int nbins, int nbp, const int32_t *__
     const Edge E = edges[e];
     uint32_t m[MW];
     if constexpr (MW == 1) {
-      m[0] = M[E.twin];
+      m[0] = M[e];
     } else if constexpr (MW == 2) {
-      const uint2 q = reinterpret_cast<const uint2 *>(M)[E.twin];
+      const uint2 q = reinterpret_cast<const uint2 *>(M)[e];
       m[0] = q.x; m[1] = q.y;
     } else {
-      const uint4 q = reinterpret_cast<const uint4 *>(M)[E.twin];
+      const uint4 q = reinterpret_cast<const uint4 *>(M)[e];
       m[0] = q.x; m[1] = q.y; m[2] = q.z; m[3] = q.w;
     }
 #pragma unroll
