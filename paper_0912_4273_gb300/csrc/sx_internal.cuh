@@ -78,6 +78,7 @@ struct StepArgs {
   const Edge *edges;
   const VConst *vc;
   double *y;
+  const int32_t *col;  // sender of every in-edge (the CSR neighbour array)
   void *P[2];        // stored photons, ping-pong by step parity
   uint32_t *M[2];    // per-edge bin masks, ping-pong by step parity
   const StepTables *tab;
@@ -151,6 +152,12 @@ __device__ __forceinline__ FF ff_warp_sum(FF a) {
   return a;  // lane 0
 }
 __device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+// a * b for b >= 0, as float-float (the product of hi exactly by FMA)
+__device__ __forceinline__ FF ff_mul(FF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return FF{p, __fmaf_rn(a.lo, b, e)};
+}
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -190,7 +197,7 @@ struct DevGrid {
   double *budget_dev;   // 4
   // load-time scratch
   int64_t *s_row_ptr;
-  int32_t *s_col;
+  int32_t *s_col;       // nnz neighbour ids as loaded; kept: the step kernel reads the senders here
   double *s_nH, *s_vol, *s_y0;
   uint8_t *s_flags;
   float4 *s_ev;         // nnz: edge vector (x, y, z) and length (w), FP32

@@ -238,6 +238,65 @@ __device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt,
 }
 
 // ----------------------------------------------------------------------------
+// The same subcycles for FP32 transport: rates, subcycle lengths and the
+// exponentials in FP32 (the photon field is FP32 already), the neutral
+// fraction accumulated in FP64, from float copies of y and x = 1 - y that
+// follow the FP32 increments.  The transmitted and the absorbed time
+// integrals are summed apart, each accurate where it is small, and the
+// returned f is taken from the smaller: e^-tau in thick cells, 1 - absorbed
+// in thin ones; *absf is the absorbed fraction, f + absf = 1 up to rounding.
+// Fa = F / A, photoionisations per atom per second at full absorption.
+// ----------------------------------------------------------------------------
+__device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau, float R0, float fc,
+                             float tol, int max_sub, int &nsub, int &capped, float &absf) {
+  double y = y_io;
+  float yf = (float)y, xf = (float)(1.0 - y);
+  nsub = 0;
+  capped = 0;
+  float t_left = dt, trans = 0.f, absd = 0.f;
+  while (t_left > 0.f) {
+    const float ty = tau * yf;
+    const float ab = -expm1f(-ty);  // absorbed fraction
+    const float tr = expf(-ty);     // transmitted fraction
+    const float ion = Fa * ab;
+    const float r0x = R0 * xf;
+    const float rec = r0x * xf;
+    float h = t_left;
+    if (yf > 0.f) {
+      const float den = ion + r0x * yf;
+      if (den > 0.f && fc * yf < den * t_left) h = __fdividef(fc * yf, den);
+    } else {
+      const float rate = Fa * tau + r0x;
+      if (rate > 0.f && fc < rate * t_left) h = __fdividef(fc, rate);
+    }
+    const float dy = (rec - ion) * h;
+    y += (double)dy;
+    yf += dy;
+    xf -= dy;
+    trans += tr * h;
+    absd += ab * h;
+    t_left = (h == t_left) ? 0.f : t_left - h;
+    nsub++;
+    const bool eq = fabsf(dy) <= tol * yf;
+    if (t_left > 0.f && (eq || nsub >= max_sub)) {
+      if (!eq) capped = 1;
+      trans += tr * t_left;
+      absd += ab * t_left;
+      t_left = 0.f;
+    }
+  }
+  y_io = y;
+  const float inv_dt = 1.f / dt;
+  const float fa = absd * inv_dt, ft = trans * inv_dt;
+  if (fa < ft) {
+    absf = fa;
+    return 1.f - fa;
+  }
+  absf = 1.f - ft;
+  return ft;
+}
+
+// ----------------------------------------------------------------------------
 // Mask words of one edge: bin b is bit b % 32 of word b / 32.  Memory holds
 // 1, 2 or 4 words per edge; 65..96 bins are handled as 3 words in registers
 // and kept at the 16-byte stride of 4 (the fourth word is zero).
@@ -387,7 +446,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   const int64_t vg = v0 + g0;            // its grid index
   T *grow = s_I + (size_t)g0 * nbs;      // the group's rows
   uint32_t(*gocc)[MW] = s_occ + g0;      // and occupancy
-  for (int i = lane; i < kGroup * nbs; i += 32) grow[i] = T(0);
+  // the group's rows are kGroup * nbs * sizeof(T) bytes, a multiple of 16
+  // (nbs odd, kGroup = 4), at a 16-byte aligned offset
+  for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 16; i += 32)
+    reinterpret_cast<uint4 *>(grow)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
   // the tile's running budget, read now so that the load overlaps the tile
@@ -437,7 +499,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
 #pragma unroll
       for (int w = 0; w < MW; ++w) my_m[w] = 0u;
       if (e < R[kGroup]) {
-        my_src = a.edges[e].col;
+        my_src = a.col[e];
         load_mask<MW>(M_prev, (int64_t)e, my_m);
       }
       int cnt = 0;
@@ -505,58 +567,85 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __syncthreads();
 
   // ---------------- phase 2: N_in and chemistry, lane per vertex ----------------
+  // photons absorbed in the tile's cells and passed to sinks, in stored units
+  // (FP64 sums, or float-float in FP32 mode)
   double bud_abs = 0.0, bud_sink = 0.0;
+  FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f};
   if (warp < kTile / 32) {
     const int vl = warp * 32 + lane;
     const int64_t v = v0 + vl;
-    double f = 0.0;
+    T f = T(0);
     int nsub = 0, capped = 0;
     if (v < a.n) {
       const T *row = s_I + (size_t)vl * nbs;
       // sum over the occupied bins in ascending order (adding the empty ones
       // would not change a bit of it)
-      double nin;  // stored photon units
       if constexpr (sizeof(T) == 8) {
-        double s = 0.0;
+        double nin = 0.0;
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
           uint32_t m = s_occ[vl][w];
           while (m) {
             const int i = __ffs(m) - 1;
             m &= m - 1u;
-            s = __dadd_rn(s, (double)row[32 * w + i]);
+            nin = __dadd_rn(nin, row[32 * w + i]);
           }
         }
-        nin = s;
-      } else {
-        FF s{0.f, 0.f};
-#pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          uint32_t m = s_occ[vl][w];
-          while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            s = ff_add(s, (float)row[32 * w + i]);
-          }
-        }
-        nin = ff_to_double(s);
-      }
-      const VConst c = a.vc[v];
-      if (c.flags & 1) {
-        bud_sink = nin;  // a sink passes nothing on
-      } else {
-        double yv = a.y[v];
-        if (nin == 0.0 && yv == 1.0) {
-          f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
+        const VConst c = a.vc[v];
+        if (c.flags & 1) {
+          bud_sink = nin;  // a sink passes nothing on
         } else {
-          f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0, a.fc,
-                        a.tol, a.max_sub, nsub, capped);
-          a.y[v] = yv;
+          double yv = a.y[v];
+          if (nin == 0.0 && yv == 1.0) {
+            f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
+          } else {
+            f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
+                          a.fc, a.tol, a.max_sub, nsub, capped);
+            a.y[v] = yv;
+          }
+          bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
         }
-        bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
+      } else {
+        FF nin{0.f, 0.f};
+#pragma unroll
+        for (int w = 0; w < MW; ++w) {
+          uint32_t m = s_occ[vl][w];
+          while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            nin = ff_add(nin, row[32 * w + i]);
+          }
+        }
+        const VConst c = a.vc[v];
+        if (c.flags & 1) {
+          bud_sink_ff = nin;  // a sink passes nothing on
+        } else {
+          double yv = a.y[v];
+          float absf = 0.f;
+          if (nin.hi == 0.f && yv == 1.0) {
+            f = 1.f;  // no photons and nothing to recombine: the state is a fixed point
+          } else {
+            const double Fa = __dmul_rn(__dmul_rn(ff_to_double(nin), a.punit),
+                                        __dmul_rn(c.invA, a.inv_dt));
+            if (c.invA == 0.0) {
+              f = 1.f;  // no atoms: transparent, nothing to ionise
+            } else if (Fa < 1e30 && c.tau_max < 1e30 && c.R0 < 1e30 && a.dt < 1e30) {
+              f = chem_cell_f(yv, (float)Fa, (float)a.dt, (float)c.tau_max, (float)c.R0,
+                              (float)a.fc, (float)a.tol, a.max_sub, nsub, capped, absf);
+            } else {  // rates beyond the FP32 range: the FP64 subcycles
+              const double fd = chem_cell(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
+                                          c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub,
+                                          capped);
+              f = (float)fd;
+              absf = (float)(1.0 - fd);
+            }
+            a.y[v] = yv;
+          }
+          bud_abs_ff = ff_mul(nin, absf);
+        }
       }
     }
-    s_f[vl] = (T)f;
+    s_f[vl] = f;
     unsigned ns = (unsigned)nsub, nc = (unsigned)capped;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -683,10 +772,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
         s_sink = sk;
       }
     } else {
-      // float-float of each lane's FP64 value, summed on the FP32 pipe
-      const float ah = (float)bud_abs, sh = (float)bud_sink;
-      const FF fa = ff_warp_sum(FF{ah, (float)(bud_abs - (double)ah)});
-      const FF fs = ff_warp_sum(FF{sh, (float)(bud_sink - (double)sh)});
+      const FF fa = ff_warp_sum(bud_abs_ff);
+      const FF fs = ff_warp_sum(bud_sink_ff);
       if (lane == 0) {
         s_abs = ff_to_double(fa);
         s_sink = ff_to_double(fs);
@@ -765,6 +852,7 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
   a.y = g.y;
   a.P[0] = g.P[0];
   a.P[1] = g.P[1];
+  a.col = g.s_col;
   a.M[0] = g.M[0];
   a.M[1] = g.M[1];
   a.tab = g.tabs;
