@@ -1,0 +1,120 @@
+"""Parity at the full size of the benchmark workload: the Test-1 grid of
+Sect. 5.1 with 2^20 interior vertices, 84 bins, FP32 transport, dt = 0.5 Myr,
+1000 steps, through the same launches the benchmark times.
+
+The FP64 oracle cannot follow 1000 steps of 2^20 vertices inside a test, so
+at this size the checks are the ones it can make:
+  * every vertex, element by element, for the first steps from a partly
+    ionised start (the oracle sweeps the whole grid in about 2 s a step);
+  * the chemistry of sampled vertices one by one at late steps: the photons
+    in flight towards a vertex after step s are its N_in in step s + 1
+    (Sect. 4.5), so the oracle's one-cell update from (y_s, N_in) must give
+    the device's y_{s+1};
+  * properties that hold at any size: the photon budget (emitted = absorbed
+    + escaped + in flight), 0 <= y <= 1, the FP32 run against the FP64
+    device path (itself pinned to the oracle element by element), and the
+    I-front against the equilibrium Stromgren solution (Sect. 5.1).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_0912_4273_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_0912_4273_gb300 import simplex as S  # noqa: E402
+
+DT = 0.5 * I.MYR_S
+NBINS = 84
+NDOT, NH, ALPHA = 5e48, 1e-3, 2.59e-13
+
+
+@pytest.fixture(scope="module")
+def grid():
+    return I.cached(I.stromgren_problem, 1 << 20, seed=0)
+
+
+@pytest.fixture(scope="module")
+def oracle_setup(grid):
+    """The oracle's tables of the full grid: its own kappa and per-vertex
+    constants (A = n_H V, tau_max = n_H sigma kappa <L>, R0 = alpha_B n_H)."""
+    bins = I.fibonacci_bins(NBINS)
+    y0 = np.random.default_rng(7).uniform(0.5, 1.0, grid.n)
+    ref = O.OracleSim(grid, O.Params(nbins=NBINS, seed=3), bins, y0=y0)
+    return bins, y0, ref
+
+
+def budget_residual(b):
+    return (b["emitted"] - b["absorbed"] - b["escaped"] - b["in_flight"]) / b["emitted"]
+
+
+def test_first_steps_every_vertex(grid, oracle_setup):
+    bins, y0, ref = oracle_setup
+    sim = O.OracleSim(grid, O.Params(nbins=NBINS, seed=3, kappa=ref.kappa), bins, y0=y0)
+    sim.step(DT, 3)
+    rb = sim.budget
+    for precision, ytol, btol in ((S.SX_FP64, 1e-9, 1e-9), (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)):
+        s = S.Solver(bins, precision=precision, seed=3, kappa=ref.kappa).load(grid, y0=y0)
+        s.step(DT, 3)
+        assert np.abs(s.y - sim.y).max() <= ytol
+        b = s.budget
+        assert max(abs(b[k] - rb[k]) for k in rb) <= btol * rb["emitted"]
+        assert np.abs(s.photons() - sim.I.sum(axis=1)).max() <= btol * rb["emitted"]
+        s.close()
+
+
+def test_thousand_steps(grid, oracle_setup):
+    bins, _, ref = oracle_setup
+    A, tau, R0 = ref.vertex_consts()
+    s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa).load(grid)
+    ordinary = grid.interior.copy()
+    ordinary[grid.src_vertex] = False
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    done = 0
+    tr = O.recombination_time(NH, ALPHA)
+    r, yp, _ = O.equilibrium_profile(1.6 * O.stromgren_radius(NDOT, NH, ALPHA), NDOT, NH, ALPHA,
+                                     I.SIGMA_H)
+    r_eq = (3 * np.trapezoid((1 - yp) * r * r, r)) ** (1 / 3)
+    fronts = []
+    for stop in (300, 600, 800, 999):
+        s.step(DT, stop - done)
+        y_prev, n_in = s.y, s.photons()
+        s.step(DT, 1)
+        done = stop + 1
+        y_new = s.y
+        # the chemistry of sampled ordinary vertices, one by one
+        lit = np.flatnonzero(ordinary & (n_in > 0))
+        for v in rng.choice(lit, size=min(2000, len(lit)), replace=False):
+            y_or, _, _, _ = O.chem(float(y_prev[v]), float(n_in[v]), DT, float(A[v]),
+                                   float(tau[v]), float(R0[v]))
+            worst = max(worst, abs(y_new[v] - y_or))
+        assert worst <= 1e-4, (stop, worst)
+        assert y_new.min() >= 0.0 and y_new.max() <= 1.0
+        assert abs(budget_residual(s.budget)) <= 1e-5
+        t = done * DT
+        fronts.append((t, O.ionised_radius_sphere(y_new, grid.volume, grid.interior)
+                       / (r_eq * (1 - math.exp(-t / tr)) ** (1 / 3))))
+    assert s.info["step"] == 1000
+    assert s.info["capped"] == 0
+    # the I-front (ionised-volume radius) against the equilibrium solution:
+    # within 2% from 2.4 recombination times on, 1% at the end
+    for t, ratio in fronts:
+        if t >= 2.4 * tr:
+            assert abs(ratio - 1) < 0.02, (t / I.MYR_S, ratio)
+    assert abs(fronts[-1][1] - 1) < 0.01, fronts
+    # the FP32 run against the FP64 device path over all 1000 steps
+    y32 = s.y
+    s.close()
+    s64 = S.Solver(bins, precision=S.SX_FP64, seed=0, kappa=ref.kappa).load(grid)
+    s64.step(DT, 1000)
+    assert np.abs(y32 - s64.y).max() <= 1e-4
+    assert abs(budget_residual(s64.budget)) <= 1e-10
+    s64.close()

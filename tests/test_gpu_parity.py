@@ -6,8 +6,9 @@ Tolerances (element by element):
     as the oracle's except exp/expm1 (1-2 ulp between libraries) and the
     order of the budget sums -> |dy| <= 1e-9, budget 1e-9 relative.
   * SX_FP32_TRANSPORT: photons are rounded to FP32 at every hop (2^-24
-    relative) -> |dy| <= 1e-4 per vertex and 1e-5 of the emitted photons for
-    each budget term.
+    relative) and the chemistry's rates, subcycle lengths and exponentials
+    are FP32 (y accumulated in FP64) -> |dy| <= 1e-4 per vertex and 1e-5 of
+    the emitted photons for each budget term.
 Routing decisions (association, straight table, bin remap) are integer on
 both sides and therefore identical.
 """
