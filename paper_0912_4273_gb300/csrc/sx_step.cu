@@ -363,6 +363,24 @@ struct Acc<float> {
   __device__ void add(float x) { v = ff_add(v, x); }
 };
 
+// A budget term of one lane (the type of Acc<T>::v) and its sums.
+template <typename T>
+struct Bud;
+template <>
+struct Bud<double> {
+  using type = double;
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double warp_sum(double v) { return warp_sum_d(v); }
+  __device__ static double to_double(double v) { return v; }
+};
+template <>
+struct Bud<float> {
+  using type = FF;
+  __device__ static FF add(FF a, FF b) { return ff_add(a, b); }
+  __device__ static FF warp_sum(FF v) { return ff_warp_sum(v); }
+  __device__ static double to_double(FF v) { return ff_to_double(v); }
+};
+
 #ifndef SX_STEP_MIN_BLOCKS
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
 #endif
@@ -419,14 +437,13 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __shared__ T s_f[kTile];
   __shared__ uint32_t s_occ[kTile][MW];
   __shared__ int32_t s_R[kWarps][kGroup + 1];  // row pointers of each warp's group
-  __shared__ T s_budw[kWarps][4];  // per warp: fly hi/lo, esc hi/lo (FP32) or fly, esc (FP64)
-  __shared__ double s_abs, s_sink;
   __shared__ int s_incoming;
   __shared__ long long s_step;
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
   constexpr int kScr1 = kLcap * 4 + kLcap * 2;
   constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * kMaxBins * 2;
+  static_assert(kScr3 >= 96 * 16, "the budget terms of a warp fit in its scratch");
   constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
@@ -452,12 +469,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     reinterpret_cast<uint4 *>(grow)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
-  // the tile's running budget, read now so that the load overlaps the tile
-  double run_abs = 0.0, run_esc = 0.0;
-  if (tid == 0) {
-    run_abs = a.partials[4 * tile];
-    run_esc = a.partials[4 * tile + 1];
-  }
+  // the tile's running budget (escaped, absorbed), read now so that the load
+  // overlaps the tile, by the lanes that write it back
+  double run_part = 0.0;
+  if (lane == 0 && (warp == 1 || warp == 2)) run_part = a.partials[4 * tile + (warp == 1 ? 1 : 0)];
   __syncthreads();
 
   const int cur = (int)(s_step & 1);
@@ -662,8 +677,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   // ---------------- phase 3: transmit, associate, route ----------------
   Acc<T> fly, esc;
   {
-    uint2 *s_qs = reinterpret_cast<uint2 *>(s_scr[warp]);                        // [kGroupCap] q bytes, straight set
-    uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_qs + kGroupCap);  // [kGroupCap][MW]
+    uint32_t *s_q = reinterpret_cast<uint32_t *>(s_scr[warp]);                   // [kGroupCap] q bytes
+    uint32_t *s_st = s_q + kGroupCap;                                             // [kGroupCap] straight sets
+    uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_st + kGroupCap);  // [kGroupCap][MW]
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * kMaxBins]
     int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
     if (lane < kGroup && vg + lane < a.n) vflags = a.vc[vg + lane].flags;
@@ -680,7 +696,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
           uint32_t qw, stw;
           memcpy(&qw, &E.q, 4);
           memcpy(&stw, &E.st, 4);
-          s_qs[idx] = make_uint2(qw, stw);
+          s_q[idx] = qw;
+          s_st[idx] = stw;
 #pragma unroll
           for (int w = 0; w < MW; ++w) s_am[idx][w] = 0u;
         }
@@ -713,10 +730,19 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
               // key (q_e . q_b) * 64 + 2^22 + (63 - k): largest for the largest
               // dot and, among equal dots, the lowest slot
               const int qb = (int)s_qbq[b];
-              int key = INT_MIN, c = (1 << 22) + 63;
-              for (int k = 0; k < dg; ++k, --c) key = max(key, __dp4a((int)s_qs[ka + k].x, qb, 0) * 64 + c);
+              const int *qk = reinterpret_cast<const int *>(s_q + ka);
+              int key = INT_MIN, k = 0;
+              for (; k + 4 <= dg; k += 4) {
+                const int c = (1 << 22) + 63 - k;
+                const int k0 = __dp4a(qk[k], qb, 0) * 64 + c;
+                const int k1 = __dp4a(qk[k + 1], qb, 0) * 64 + (c - 1);
+                const int k2 = __dp4a(qk[k + 2], qb, 0) * 64 + (c - 2);
+                const int k3 = __dp4a(qk[k + 3], qb, 0) * 64 + (c - 3);
+                key = max(key, max(max(k0, k1), max(k2, k3)));
+              }
+              for (; k < dg; ++k) key = max(key, __dp4a(qk[k], qb, 0) * 64 + ((1 << 22) + 63 - k));
               const int kst = 63 - (key & 63);
-              const uint32_t stw = s_qs[ka + kst].y;
+              const uint32_t stw = s_st[ka + kst];
               const int cnt = (int)(stw >> 24);
               if (cnt == 0) {
                 esc.add(O);
@@ -749,60 +775,40 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     }
   }
   // ---------------- budget partials of the tile ----------------
-  if constexpr (sizeof(T) == 8) {
-    const double t_fly = warp_sum_d(fly.v), t_esc = warp_sum_d(esc.v);
-    if (lane == 0) {
-      s_budw[warp][0] = t_fly;
-      s_budw[warp][2] = t_esc;
-    }
-  } else {
-    const FF t_fly = ff_warp_sum(fly.v), t_esc = ff_warp_sum(esc.v);
-    if (lane == 0) {
-      s_budw[warp][0] = t_fly.hi;
-      s_budw[warp][1] = t_fly.lo;
-      s_budw[warp][2] = t_esc.hi;
-      s_budw[warp][3] = t_esc.lo;
-    }
-  }
-  if (warp < kTile / 32) {  // the chemistry lanes hold absorbed and sink photons
+  // every lane's terms go to its warp's scratch; then warp 0 sums the photons
+  // in flight, warp 1 the escaped ones (and those passed to sinks), warp 2
+  // the absorbed ones, each in a fixed order
+  {
+    using BT = typename Bud<T>::type;
+    BT *s_b = reinterpret_cast<BT *>(s_scr[warp]);  // [0..31] in flight, [32..63] escaped, [64..95] absorbed
     if constexpr (sizeof(T) == 8) {
-      const double ab = warp_sum_d(bud_abs), sk = warp_sum_d(bud_sink);
-      if (lane == 0) {
-        s_abs = ab;
-        s_sink = sk;
-      }
+      s_b[lane] = fly.v;
+      s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink);
+      if (warp == 0) s_b[64 + lane] = bud_abs;
     } else {
-      const FF fa = ff_warp_sum(bud_abs_ff);
-      const FF fs = ff_warp_sum(bud_sink_ff);
+      s_b[lane] = fly.v;
+      s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink_ff);
+      if (warp == 0) s_b[64 + lane] = bud_abs_ff;
+    }
+    __syncthreads();
+    if (warp < 3) {
+      BT acc;
+      if (warp < 2) {
+        acc = reinterpret_cast<const BT *>(s_scr[0])[32 * warp + lane];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w)
+          acc = Bud<T>::add(acc, reinterpret_cast<const BT *>(s_scr[w])[32 * warp + lane]);
+      } else {
+        acc = reinterpret_cast<const BT *>(s_scr[0])[64 + lane];
+      }
+      acc = Bud<T>::warp_sum(acc);
       if (lane == 0) {
-        s_abs = ff_to_double(fa);
-        s_sink = ff_to_double(fs);
+        double *p = a.partials + 4 * tile;
+        const double t = Bud<T>::to_double(acc);
+        if (warp == 0) p[2] = t;
+        else p[warp == 1 ? 1 : 0] = run_part + t;
       }
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double fl, es;
-    if constexpr (sizeof(T) == 8) {
-      fl = 0.0;
-      es = 0.0;
-      for (int w = 0; w < kWarps; ++w) {
-        fl += s_budw[w][0];
-        es += s_budw[w][2];
-      }
-    } else {
-      FF F1{0.f, 0.f}, F2{0.f, 0.f};
-      for (int w = 0; w < kWarps; ++w) {
-        F1 = ff_add(F1, FF{(float)s_budw[w][0], (float)s_budw[w][1]});
-        F2 = ff_add(F2, FF{(float)s_budw[w][2], (float)s_budw[w][3]});
-      }
-      fl = ff_to_double(F1);
-      es = ff_to_double(F2);
-    }
-    double *p = a.partials + 4 * tile;
-    p[0] = run_abs + s_abs;
-    p[1] = run_esc + (s_sink + es);
-    p[2] = fl;
   }
   __syncthreads();  // shared state is reused by the next tile of a persistent CTA
 }
