@@ -166,6 +166,22 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // ----------------------------------------------------------------------------
+// Asynchronous copies global -> shared (sm_80 and later): issued by a thread,
+// completed by the same thread's wait; other lanes see the data after a
+// warp barrier.  Addresses aligned to the copy size.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ----------------------------------------------------------------------------
 // Host-side launch wrappers (defined in the .cu files)
 // ----------------------------------------------------------------------------
 struct DevGrid {

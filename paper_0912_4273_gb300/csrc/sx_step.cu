@@ -372,6 +372,7 @@ struct Bud<double> {
   __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
   __device__ static double warp_sum(double v) { return warp_sum_d(v); }
   __device__ static double to_double(double v) { return v; }
+  __device__ static double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 };
 template <>
 struct Bud<float> {
@@ -379,6 +380,9 @@ struct Bud<float> {
   __device__ static FF add(FF a, FF b) { return ff_add(a, b); }
   __device__ static FF warp_sum(FF v) { return ff_warp_sum(v); }
   __device__ static double to_double(FF v) { return ff_to_double(v); }
+  __device__ static FF shfl_xor(FF v, int o) {
+    return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+  }
 };
 
 #ifndef SX_STEP_MIN_BLOCKS
@@ -437,13 +441,18 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __shared__ T s_f[kTile];
   __shared__ uint32_t s_occ[kTile][MW];
   __shared__ int32_t s_R[kWarps][kGroup + 1];  // row pointers of each warp's group
+  // the chemistry's inputs: per-vertex constants and y (copied in while
+  // phase 1 runs), N_in (written by phase 1)
+  __shared__ __align__(16) VConst s_vc[kTile];
+  __shared__ __align__(16) double s_y[kTile];
+  __shared__ typename Bud<T>::type s_nin[kTile];
   __shared__ int s_incoming;
   __shared__ long long s_step;
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
   constexpr int kScr1 = kLcap * 4 + kLcap * 2;
-  constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * kMaxBins * 2;
-  static_assert(kScr3 >= 96 * 16, "the budget terms of a warp fit in its scratch");
+  constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
+  static_assert(kScr3 >= 96 * (int)sizeof(typename Bud<T>::type), "the budget terms of a warp fit in its scratch");
   constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
@@ -459,6 +468,15 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     s_incoming = a.tab->incoming;
   }
   const int64_t v0 = tile * kTile;
+  if (warp < kTile / 32) {  // the chemistry warps fetch their vertices' constants and y
+    const int64_t nv = min((int64_t)32, a.n - v0 - 32 * warp);
+    const int64_t vw = v0 + 32 * warp;
+    for (int i = lane; i < 2 * nv; i += 32)
+      cp_async16(reinterpret_cast<char *>(s_vc + 32 * warp) + 16 * i,
+                 reinterpret_cast<const char *>(a.vc + vw) + 16 * i);
+    if (lane < nv) cp_async8(s_y + 32 * warp + lane, a.y + vw + lane);
+    cp_async_commit();
+  }
   const int g0 = warp * kGroup;          // first tile vertex of the warp's group
   const int64_t vg = v0 + g0;            // its grid index
   T *grow = s_I + (size_t)g0 * nbs;      // the group's rows
@@ -578,6 +596,22 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
       if (lane < MW) gocc[g][lane] = word_bins(nbins, lane);
       __syncwarp();
     }
+    // N_in of the group's vertices in stored units (empty bins hold zero):
+    // eight lanes per vertex, each summing every eighth bin, then a
+    // reduction over the eight lanes
+    __syncwarp();
+    {
+      using BT = typename Bud<T>::type;
+      const int g = lane >> 3, j = lane & 7;
+      const T *row = grow + (size_t)g * nbs;
+      BT sum{};
+      for (int b = j; b < nbins; b += 8) {
+        if constexpr (sizeof(T) == 8) sum = __dadd_rn(sum, row[b]); else sum = ff_add(sum, row[b]);
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) sum = Bud<T>::add(sum, Bud<T>::shfl_xor(sum, o));
+      if (j == 0) s_nin[g0 + g] = sum;
+    }
   }
   __syncthreads();
 
@@ -587,30 +621,20 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   double bud_abs = 0.0, bud_sink = 0.0;
   FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f};
   if (warp < kTile / 32) {
+    cp_async_wait_all();
+    __syncwarp();
     const int vl = warp * 32 + lane;
     const int64_t v = v0 + vl;
     T f = T(0);
     int nsub = 0, capped = 0;
     if (v < a.n) {
-      const T *row = s_I + (size_t)vl * nbs;
-      // sum over the occupied bins in ascending order (adding the empty ones
-      // would not change a bit of it)
+      const VConst c = s_vc[vl];
       if constexpr (sizeof(T) == 8) {
-        double nin = 0.0;
-#pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          uint32_t m = s_occ[vl][w];
-          while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            nin = __dadd_rn(nin, row[32 * w + i]);
-          }
-        }
-        const VConst c = a.vc[v];
+        const double nin = s_nin[vl];
         if (c.flags & 1) {
           bud_sink = nin;  // a sink passes nothing on
         } else {
-          double yv = a.y[v];
+          double yv = s_y[vl];
           if (nin == 0.0 && yv == 1.0) {
             f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
           } else {
@@ -621,21 +645,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
           bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
         }
       } else {
-        FF nin{0.f, 0.f};
-#pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          uint32_t m = s_occ[vl][w];
-          while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            nin = ff_add(nin, row[32 * w + i]);
-          }
-        }
-        const VConst c = a.vc[v];
+        const FF nin = s_nin[vl];
         if (c.flags & 1) {
           bud_sink_ff = nin;  // a sink passes nothing on
         } else {
-          double yv = a.y[v];
+          double yv = s_y[vl];
           float absf = 0.f;
           if (nin.hi == 0.f && yv == 1.0) {
             f = 1.f;  // no photons and nothing to recombine: the state is a fixed point
@@ -680,9 +694,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
     uint32_t *s_q = reinterpret_cast<uint32_t *>(s_scr[warp]);                   // [kGroupCap] q bytes
     uint32_t *s_st = s_q + kGroupCap;                                             // [kGroupCap] straight sets
     uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_st + kGroupCap);  // [kGroupCap][MW]
-    uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * kMaxBins]
+    uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * 32 * MW]
     int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
-    if (lane < kGroup && vg + lane < a.n) vflags = a.vc[vg + lane].flags;
+    if (lane < kGroup && vg + lane < a.n) vflags = s_vc[g0 + lane].flags;
     const uint32_t sinks = __ballot_sync(0xffffffffu, vflags & 1);
     // consecutive vertices ga .. gb - 1 whose out-edges fit in the staging area
     for (int ga = 0; ga < kGroup;) {

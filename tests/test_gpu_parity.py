@@ -2,9 +2,10 @@
 the same seeded inputs.
 
 Tolerances (element by element):
-  * SX_FP64: every arithmetic step of the path is the same IEEE FP64 sequence
-    as the oracle's except exp/expm1 (1-2 ulp between libraries) and the
-    order of the budget sums -> |dy| <= 1e-9, budget 1e-9 relative.
+  * SX_FP64: the same IEEE FP64 operations as the oracle's, some added in
+    another fixed order (packets summed per new bin in edge order, N_in and
+    the budget as reductions) and exp/expm1 from another library (1-2 ulp)
+    -> |dy| <= 1e-9, budget 1e-9 relative.
   * SX_FP32_TRANSPORT: photons are rounded to FP32 at every hop (2^-24
     relative) and the chemistry's rates, subcycle lengths and exponentials
     are FP32 (y accumulated in FP64) -> |dy| <= 1e-4 per vertex and 1e-5 of
