@@ -198,7 +198,7 @@ struct DevGrid {
   void *P[2];           // n*nbp photons (T), ping-pong
   uint32_t *M[2];       // nnz*mw masks, ping-pong
   double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
-  int64_t nblocks;
+  int64_t nblocks;      // tiles of kTile vertices
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
   unsigned long long *steps_done;  // device step counter (advanced by the rotation kernel)
   int *incoming;        // set by a grid update: the next step takes P[prev] as incoming photons

@@ -21,6 +21,8 @@
 //  k_inflight   photons in flight towards every vertex (readout).
 #include <limits.h>
 
+#include <algorithm>
+
 #include "sx_internal.cuh"
 
 namespace sx {
@@ -390,7 +392,7 @@ struct Bud<float> {
 #endif
 
 constexpr int kGroup = kTile / kWarps;  // consecutive vertices a warp works on together
-constexpr int kGroupCap = 96;           // out-edges of a group staged at once in phase 3
+constexpr int kGroupCap = 72;           // out-edges of a group staged at once in phase 3
 constexpr int kLcap = 64;               // packets listed at once in phase 1
 
 // One round of photon packets arriving at the vertices of a warp's group:
@@ -433,7 +435,7 @@ __device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
 // Only bins that hold photons are touched: a bin without photons sets no mask
 // bit, so no reader looks at its stored value, and it is not written.
 template <typename T, int MW>
-__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
+__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool reload) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][tile_stride(nbins)]
   __shared__ uint32_t s_qbq[kMaxBins];
@@ -459,13 +461,15 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int b = tid; b < kMaxBins; b += kThreads) {
-    s_qbq[b] = a.tab->qbq[b];
-    s_fwd[b] = a.tab->fwd[b];
-  }
-  if (tid == 0) {
-    s_step = a.tab->step;
-    s_incoming = a.tab->incoming;
+  if (reload) {  // this step's tables (a CTA keeps them from tile to tile of one grid)
+    for (int b = tid; b < kMaxBins; b += kThreads) {
+      s_qbq[b] = a.tab->qbq[b];
+      s_fwd[b] = a.tab->fwd[b];
+    }
+    if (tid == 0) {
+      s_step = a.tab->step;
+      s_incoming = a.tab->incoming;
+    }
   }
   const int64_t v0 = tile * kTile;
   if (warp < kTile / 32) {  // the chemistry warps fetch their vertices' constants and y
@@ -491,7 +495,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   // overlaps the tile, by the lanes that write it back
   double run_part = 0.0;
   if (lane == 0 && (warp == 1 || warp == 2)) run_part = a.partials[4 * tile + (warp == 1 ? 1 : 0)];
-  __syncthreads();
+  if (reload) __syncthreads(); else __syncwarp();  // the rest of the prologue is the warp's own
 
   const int cur = (int)(s_step & 1);
   const T *__restrict__ Pp = static_cast<const T *>(a.P[cur ^ 1]);
@@ -827,9 +831,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile) {
   __syncthreads();  // shared state is reused by the next tile of a persistent CTA
 }
 
+// One grid, one CTA per tile (the hardware hands tiles to SMs as they free up,
+// which balances tiles of unequal cost).
 template <typename T, int MW>
 __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
-  step_tile<T, MW>(a, blockIdx.x);
+  step_tile<T, MW>(a, blockIdx.x, true);
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
@@ -840,6 +846,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS)
                  unsigned long long *__restrict__ queue) {
   __shared__ long long s_item;
   const int64_t total = prefix[ngrids];
+  int cur_grid = -1;
   for (;;) {
     if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
     __syncthreads();
@@ -851,7 +858,8 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS)
       const int mid = (lo + hi + 1) >> 1;
       if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    step_tile<T, MW>(args[lo], t - prefix[lo]);
+    step_tile<T, MW>(args[lo], t - prefix[lo], lo != cur_grid);
+    cur_grid = lo;
   }
 }
 
@@ -885,12 +893,12 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
 
 template <typename T, int MW>
 static void configure_smem() {
-  static bool done = false;
-  if (!done) {
+  static const bool done = [] {  // once per instantiation (thread-safe initialisation)
     cudaFuncSetAttribute(k_step<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(k_step_batch<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    done = true;
-  }
+    return true;
+  }();
+  (void)done;
 }
 
 // Mask words a step kernel works with for nbins bins.
@@ -902,6 +910,7 @@ static cudaError_t launch_step_t(DevGrid &g, double dt, double fc, double tol, i
   const StepArgs a = make_step_args(g, dt, fc, tol, max_sub);
   const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
   configure_smem<T, MW>();
+  if (g.nblocks <= 0) return cudaSuccess;
   k_step<T, MW><<<(unsigned)g.nblocks, kThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
