@@ -3,9 +3,10 @@
 
 Metric: DCT vertex-direction updates per second (interior vertices x bins x
 steps / time) on the Test-1 Stromgren workload at 2^20 interior vertices and
-84 bins, FP32 transport with FP64 chemistry (the configuration the headline
-metric is quoted on).  One step is one pass of the whole hot path: rotation
-and bin remap, gather, sources, chemistry, association and routing, budget.
+84 bins, FP32 transport (the configuration the headline metric is quoted on;
+the chemistry evaluates its rates in FP32 and keeps y in FP64).  One step is
+one pass of the whole hot path: rotation and bin remap, gather, sources,
+chemistry, association and routing, budget.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -40,7 +41,8 @@ WORKLOADS = {
     # 2^20 interior vertices of the Test-1 grid (Sect. 5.1), 84 bins, 1000 steps over 500 Myr
     "c1": dict(n=1 << 20, nbins=84, precision="fp32", dt_myr=0.5, seed=0,
                name="Test-1 Stromgren grid, 2^20 interior Poisson-Delaunay vertices + sink shell, "
-                    "84 direction bins, FP32 transport / FP64 chemistry, dt = 0.5 Myr"),
+                    "84 direction bins, FP32 transport (FP32 chemistry rates, FP64 neutral fraction), "
+                    "dt = 0.5 Myr"),
     # the small FP64 case
     "c0": dict(n=8192, nbins=42, precision="fp64", dt_myr=2.5, seed=0,
                name="Test-1 Stromgren grid, 8192 interior vertices + sink shell, 42 bins, FP64, "
@@ -48,9 +50,10 @@ WORKLOADS = {
 }
 
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum), valid only for the kernel source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "c24fb59d7e6882c689385cd602c70a3fc148d693a89ea18cd304d52ee9302e3f",
-               "bytes_per_launch": 996.397312e6 + 375.977472e6, "workload": "c1"}
+# dram__bytes_write.sum, the launch of step 300), valid only for the kernel
+# source it was taken on.
+NCU_TRAFFIC = {"sx_step.cu_sha256": "110913ba5ce9b18ab1bfa807e4eb8dc4f165d702b5fb5709a7f5ad8c259e1294",
+               "bytes_per_launch": 1059.694e6 + 382.124e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
@@ -258,7 +261,7 @@ def run_ours(args, wl, rank, world, local_rank):
         "data": "synthetic (seeded Poisson-Delaunay Test-1 grid)",
         "config": {"workload": wl["name"], "n_interior": n_int, "n_vertices": prob.n,
                    "nnz": prob.nnz, "nbins": wl["nbins"],
-                   "chemistry": "f64", "transport": "f64" if fp64 else "f32",
+                   "chemistry": "f64" if fp64 else "f32 rates, f64 y", "transport": "f64" if fp64 else "f32",
                    "l2": f"no flush: per-grid state {info['workspace_bytes'] / 1e9:.2f} GB > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
