@@ -185,6 +185,39 @@ int sx_grid_update_apply(sx_ctx *ctx, int64_t n_new, const double *pos, const in
 int sx_profile(sx_ctx *ctx, int enable);
 
 /* ---------------------------------------------------------------------------
+ * Launch shape of the step kernel (a system choice, no counterpart in the
+ * paper).  A step launch works on 32-vertex tiles; its variant is the number
+ * of consecutive vertices one warp works on: 4 (8 warps per tile, the
+ * default) or 2 (16 warps per tile).  Both compute the same step; sums whose
+ * order follows the warps (N_in, the budget) can differ in the last bits, so
+ * results are reproducible for a given variant.  A batch steps with the
+ * variant of its first grid.
+ * ------------------------------------------------------------------------- */
+#define SX_TUNE_MAX_CANDIDATES 4
+
+typedef struct sx_tune_result {
+  int32_t variant;                        /* chosen: vertices per warp */
+  int32_t ncandidates;                    /* variants tried */
+  int32_t candidates[SX_TUNE_MAX_CANDIDATES];
+  double ms_per_step[SX_TUNE_MAX_CANDIDATES]; /* mean step time of each (rotation + step) */
+} sx_tune_result;
+
+/* Set (2 or 4) or read the variant of a context.  Errors: SX_EINVAL. */
+int sx_set_variant(sx_ctx *ctx, int32_t variant);
+int sx_get_variant(sx_ctx *ctx, int32_t *variant);
+
+/* Autotuner: times every variant for nsteps steps of size dt_s on the loaded
+   grid, from its current state, and keeps the fastest.  The grid's state is
+   saved in `scratch` (device memory owned by the caller, at least
+   sx_workspace_bytes of the loaded grid, 256-byte aligned) and restored
+   after every trial, so the call leaves the simulation exactly where it was
+   (step count, budget, every device buffer).  Waits for the context's
+   stream.  1 <= nsteps <= 1000.  Errors: SX_EINVAL (arguments, scratch too
+   small), SX_ESTATE (no grid), SX_ECUDA. */
+int sx_autotune(sx_ctx *ctx, double dt_s, int32_t nsteps, void *scratch, size_t scratch_bytes,
+                sx_tune_result *out);
+
+/* ---------------------------------------------------------------------------
  * Batched stepping of many grids (a system form of the method, not in the
  * paper): one rotation launch and one persistent step launch per step cover
  * every grid of the batch; the CTAs pull (grid, 32-vertex tile) items from a

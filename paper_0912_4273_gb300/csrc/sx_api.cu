@@ -18,6 +18,8 @@ struct sx_ctx {
   sx::DevGrid g{};
   sx::Layout L{};
   double *bins_dev = nullptr;  // inside the workspace
+  void *ws_base = nullptr;     // the caller's workspace of the loaded grid
+  size_t ws_used = 0;          // bytes of it the grid uses
   bool loaded = false;
   int64_t step = 0;
   double emitted = 0.0;
@@ -150,6 +152,8 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   g.precision = c->cfg.precision;
   g.punit = 1.0;
   *bins_dev = reinterpret_cast<double *>(static_cast<char *>(d_workspace) + L.total);
+  c->ws_base = d_workspace;
+  c->ws_used = L.total + sizeof(double) * 3 * (size_t)c->cfg.nbins;
   char *base = static_cast<char *>(d_workspace);
   // zero the state that must start at zero
   SX_CUDA(c, cudaMemsetAsync(base + L.off_P0, 0, L.off_M0 - L.off_P0, st));
@@ -568,6 +572,87 @@ int sx_profile(sx_ctx *c, int enable) {
   return SX_OK;
 }
 
+int sx_set_variant(sx_ctx *c, int32_t variant) {
+  if (!c) return SX_EINVAL;
+  if (variant != 2 && variant != 4) return fail(c, SX_EINVAL, "variant must be 2 or 4 vertices per warp");
+  if (c->g.group != variant && c->graph) {  // a captured graph holds the old kernel
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->g.group = variant;
+  return SX_OK;
+}
+
+int sx_get_variant(sx_ctx *c, int32_t *variant) {
+  if (!c || !variant) return SX_EINVAL;
+  *variant = c->g.group == 2 ? 2 : 4;
+  return SX_OK;
+}
+
+int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scratch_bytes,
+                sx_tune_result *out) {
+  if (!c) return SX_EINVAL;
+  if (!out || !scratch) return fail(c, SX_EINVAL, "NULL argument");
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || nsteps > 1000)
+    return fail(c, SX_EINVAL, "dt must be > 0 and 1 <= nsteps <= 1000");
+  if (scratch_bytes < c->ws_used) return fail(c, SX_EINVAL, "scratch smaller than the grid's workspace");
+  if (reinterpret_cast<uintptr_t>(scratch) % 256 != 0) return fail(c, SX_EINVAL, "scratch not 256-byte aligned");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  int rc = drain_events(c);
+  if (rc) return rc;
+  ensure_punit(c, dt);
+  const cudaStream_t st = c->stream;
+  const int32_t before = c->g.group == 2 ? 2 : 4;
+  // the state: every device buffer of the grid, and the host counters
+  SX_CUDA(c, cudaMemcpyAsync(scratch, c->ws_base, c->ws_used, cudaMemcpyDeviceToDevice, st));
+  const int64_t step0 = c->step;
+  std::memset(out, 0, sizeof(*out));
+  const int32_t cand[2] = {4, 2};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SX_CUDA(c, cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  double best = 0.0;
+  int32_t pick = before;
+  for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+    c->g.group = cand[i];
+    // one untimed step (first launch of the variant), then the timed ones
+    for (int32_t k = 0; k <= nsteps && ce == cudaSuccess; ++k) {
+      if (k == 1) ce = cudaEventRecord(e0, st);
+      if (ce == cudaSuccess)
+        ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, step0 + k, 0, dt, st);
+      if (ce == cudaSuccess)
+        ce = sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, st);
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess) {
+      out->candidates[i] = cand[i];
+      out->ms_per_step[i] = (double)ms / nsteps;
+      out->ncandidates = i + 1;
+      if (i == 0 || out->ms_per_step[i] < best) {
+        best = out->ms_per_step[i];
+        pick = cand[i];
+      }
+      ce = cudaMemcpyAsync(c->ws_base, scratch, c->ws_used, cudaMemcpyDeviceToDevice, st);
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  c->g.group = before;
+  if (ce != cudaSuccess) {
+    // put the state back in any case, then report
+    cudaMemcpyAsync(c->ws_base, scratch, c->ws_used, cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+    return cuda_fail(c, ce, "sx_autotune");
+  }
+  out->variant = pick;
+  return sx_set_variant(c, pick);
+}
+
 int sx_get_info(sx_ctx *c, sx_info *info) {
   if (!c || !info) return SX_EINVAL;
   std::memset(info, 0, sizeof(*info));
@@ -679,7 +764,7 @@ int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_
   b->copy_pending = true;
   for (int32_t k = 0; k < nsteps; ++k) {
     SX_BCUDA(b, sx::launch_rotation_batch(b->d_rot, n, b->stream));
-    SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.mw, b->d_args, b->d_prefix, n,
+    SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.group, b->d_args, b->d_prefix, n,
                                       b->h_prefix[n], b->d_queue, c0->cfg.nbins, b->device, b->stream));
   }
   SX_BCUDA(b, cudaEventRecord(b->ev, b->stream));

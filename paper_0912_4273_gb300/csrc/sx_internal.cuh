@@ -11,8 +11,6 @@ constexpr int kQ = 127;            // quantisation of unit vectors (int8)
 constexpr int kMaxBins = 128;
 constexpr int kMaxDeg = 64;        // largest non-sink degree the step kernel stages
 constexpr int kTile = 32;          // vertices per CTA in the step kernel (one chemistry warp)
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
 constexpr int kMaxSources = 4096;
 constexpr uint32_t kRotTag = 0x53583252u;  // Philox counter word 3 of the rotation draws
 constexpr int kRotMaxAttempts = 64;
@@ -199,6 +197,7 @@ struct DevGrid {
   uint32_t *M[2];       // nnz*mw masks, ping-pong
   double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
   int64_t nblocks;      // tiles of kTile vertices
+  int group;            // step kernel variant: vertices per warp (2 or 4; 0 = 4)
   StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
   unsigned long long *steps_done;  // device step counter (advanced by the rotation kernel)
   int *incoming;        // set by a grid update: the next step takes P[prev] as incoming photons
@@ -245,7 +244,7 @@ StepArgs make_step_args(DevGrid &g, double dt, double chem_frac, double chem_tol
 // Batched: one rotation CTA per grid, then one persistent launch over the
 // tiles of all grids (work queue).  All grids share nbins and precision.
 cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, cudaStream_t st);
-cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, const int64_t *d_prefix,
+cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int device, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);

@@ -391,8 +391,17 @@ struct Bud<float> {
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
 #endif
 
-constexpr int kGroup = kTile / kWarps;  // consecutive vertices a warp works on together
-constexpr int kGroupCap = 72;           // out-edges of a group staged at once in phase 3
+// A step kernel variant works on 32-vertex tiles with G consecutive vertices
+// per warp, so kTile / G warps per CTA: G = 4 (8 warps, 6 CTAs/SM) or G = 2
+// (16 warps, 3 CTAs/SM), both at 40 registers.
+template <int G>
+struct Shape {
+  static constexpr int kWarps = kTile / G;
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kMinBlocks = SX_STEP_MIN_BLOCKS * 8 / kWarps;
+  static constexpr int kCap = 18 * G;  // out-edges of a group staged at once in phase 3
+  static constexpr int kLanesPerVertex = 32 / G;
+};
 constexpr int kLcap = 64;               // packets listed at once in phase 1
 
 // One round of photon packets arriving at the vertices of a warp's group:
@@ -434,8 +443,12 @@ __device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
 //            in-edges.
 // Only bins that hold photons are touched: a bin without photons sets no mask
 // bit, so no reader looks at its stored value, and it is not written.
-template <typename T, int MW>
+template <typename T, int MW, int G>
 __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool reload) {
+  constexpr int kGroup = G;
+  constexpr int kWarps = Shape<G>::kWarps;
+  constexpr int kThreads = Shape<G>::kThreads;
+  constexpr int kGroupCap = Shape<G>::kCap;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *s_I = reinterpret_cast<T *>(smem_raw);  // [kTile][tile_stride(nbins)]
   __shared__ uint32_t s_qbq[kMaxBins];
@@ -454,8 +467,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
   constexpr int kScr1 = kLcap * 4 + kLcap * 2;
   constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
-  static_assert(kScr3 >= 96 * (int)sizeof(typename Bud<T>::type), "the budget terms of a warp fit in its scratch");
-  constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
+  constexpr int kScrB = 96 * (int)sizeof(typename Bud<T>::type);  // the budget terms of a warp
+  constexpr int kScr13 = kScr1 > kScr3 ? kScr1 : kScr3;
+  constexpr int kScr = ((kScr13 > kScrB ? kScr13 : kScrB) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -485,10 +499,17 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   const int64_t vg = v0 + g0;            // its grid index
   T *grow = s_I + (size_t)g0 * nbs;      // the group's rows
   uint32_t(*gocc)[MW] = s_occ + g0;      // and occupancy
-  // the group's rows are kGroup * nbs * sizeof(T) bytes, a multiple of 16
-  // (nbs odd, kGroup = 4), at a 16-byte aligned offset
-  for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 16; i += 32)
-    reinterpret_cast<uint4 *>(grow)[i] = make_uint4(0u, 0u, 0u, 0u);
+  // the group's rows, kGroup * nbs * sizeof(T) bytes at an offset that is a
+  // multiple of the same, are cleared with 16-byte stores when G sizeof(T)
+  // is a multiple of 16, else 8-byte ones (G even)
+  if constexpr (kGroup * sizeof(T) % 16 == 0) {
+    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 16; i += 32)
+      reinterpret_cast<uint4 *>(grow)[i] = make_uint4(0u, 0u, 0u, 0u);
+  } else {
+    static_assert(kGroup * sizeof(T) % 8 == 0, "rows cleared in 8-byte words");
+    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 8; i += 32)
+      reinterpret_cast<uint2 *>(grow)[i] = make_uint2(0u, 0u);
+  }
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
   // the tile's running budget (escaped, absorbed), read now so that the load
@@ -601,19 +622,20 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
       __syncwarp();
     }
     // N_in of the group's vertices in stored units (empty bins hold zero):
-    // eight lanes per vertex, each summing every eighth bin, then a
-    // reduction over the eight lanes
+    // L = 32 / G lanes per vertex, each summing every L-th bin, then a
+    // reduction over the L lanes
     __syncwarp();
     {
       using BT = typename Bud<T>::type;
-      const int g = lane >> 3, j = lane & 7;
+      constexpr int L = Shape<G>::kLanesPerVertex;
+      const int g = lane / L, j = lane % L;
       const T *row = grow + (size_t)g * nbs;
       BT sum{};
-      for (int b = j; b < nbins; b += 8) {
+      for (int b = j; b < nbins; b += L) {
         if constexpr (sizeof(T) == 8) sum = __dadd_rn(sum, row[b]); else sum = ff_add(sum, row[b]);
       }
 #pragma unroll
-      for (int o = 4; o > 0; o >>= 1) sum = Bud<T>::add(sum, Bud<T>::shfl_xor(sum, o));
+      for (int o = L / 2; o > 0; o >>= 1) sum = Bud<T>::add(sum, Bud<T>::shfl_xor(sum, o));
       if (j == 0) s_nin[g0 + g] = sum;
     }
   }
@@ -833,15 +855,15 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
 
 // One grid, one CTA per tile (the hardware hands tiles to SMs as they free up,
 // which balances tiles of unequal cost).
-template <typename T, int MW>
-__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS) k_step(const StepArgs a) {
-  step_tile<T, MW>(a, blockIdx.x, true);
+template <typename T, int MW, int G>
+__global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_step(const StepArgs a) {
+  step_tile<T, MW, G>(a, blockIdx.x, true);
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
 // queue; a tile is one grid's 32 consecutive vertices.
-template <typename T, int MW>
-__global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS)
+template <typename T, int MW, int G>
+__global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
     k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
                  unsigned long long *__restrict__ queue) {
   __shared__ long long s_item;
@@ -858,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, SX_STEP_MIN_BLOCKS)
       const int mid = (lo + hi + 1) >> 1;
       if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    step_tile<T, MW>(args[lo], t - prefix[lo], lo != cur_grid);
+    step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid);
     cur_grid = lo;
   }
 }
@@ -891,11 +913,11 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
   return a;
 }
 
-template <typename T, int MW>
+template <typename T, int MW, int G>
 static void configure_smem() {
   static const bool done = [] {  // once per instantiation (thread-safe initialisation)
-    cudaFuncSetAttribute(k_step<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_step_batch<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_step<T, MW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_step_batch<T, MW, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     return true;
   }();
   (void)done;
@@ -904,65 +926,77 @@ static void configure_smem() {
 // Mask words a step kernel works with for nbins bins.
 static int compute_words(int nbins) { return nbins <= 32 ? 1 : nbins <= 64 ? 2 : nbins <= 96 ? 3 : 4; }
 
-template <typename T, int MW>
-static cudaError_t launch_step_t(DevGrid &g, double dt, double fc, double tol, int max_sub,
-                                 cudaStream_t st) {
-  const StepArgs a = make_step_args(g, dt, fc, tol, max_sub);
-  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(g.nbins);
-  configure_smem<T, MW>();
-  if (g.nblocks <= 0) return cudaSuccess;
-  k_step<T, MW><<<(unsigned)g.nblocks, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
+// Calls f.template run<T, MW, G>() for the instantiation that serves
+// (precision, nbins, group); group is 2 or 4 vertices per warp (else 4).
+template <typename F>
+static cudaError_t dispatch_step(int precision, int nbins, int group, const F &f) {
+  const int w = compute_words(nbins);
+  const bool g2 = group == 2;
+#define SX_DISPATCH_W(T)                                                                 \
+  if (w == 1) return g2 ? f.template run<T, 1, 2>() : f.template run<T, 1, 4>();        \
+  if (w == 2) return g2 ? f.template run<T, 2, 2>() : f.template run<T, 2, 4>();        \
+  if (w == 3) return g2 ? f.template run<T, 3, 2>() : f.template run<T, 3, 4>();        \
+  return g2 ? f.template run<T, 4, 2>() : f.template run<T, 4, 4>();
+  if (precision == 0) {
+    SX_DISPATCH_W(double)
+  }
+  SX_DISPATCH_W(float)
+#undef SX_DISPATCH_W
 }
+
+struct StepLaunch {
+  const StepArgs &a;
+  int64_t ntiles;
+  int nbins;
+  cudaStream_t st;
+  template <typename T, int MW, int G>
+  cudaError_t run() const {
+    const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(nbins);
+    configure_smem<T, MW, G>();
+    k_step<T, MW, G><<<(unsigned)ntiles, Shape<G>::kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+};
 
 cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st) {
-  const int w = compute_words(g.nbins);
-  if (g.precision == 0) {
-    if (w == 1) return launch_step_t<double, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-    if (w == 2) return launch_step_t<double, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-    if (w == 3) return launch_step_t<double, 3>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-    return launch_step_t<double, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
+  if (g.nblocks <= 0) return cudaSuccess;
+  const StepArgs a = make_step_args(g, dt, chem_frac, chem_tol, chem_max_sub);
+  return dispatch_step(g.precision, g.nbins, g.group, StepLaunch{a, g.nblocks, g.nbins, st});
+}
+
+struct BatchLaunch {
+  const StepArgs *d_args;
+  const int64_t *d_prefix;
+  int ngrids;
+  int64_t total_tiles;
+  unsigned long long *d_queue;
+  int nbins, device;
+  cudaStream_t st;
+  template <typename T, int MW, int G>
+  cudaError_t run() const {
+    configure_smem<T, MW, G>();
+    int nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(nbins);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<T, MW, G>, Shape<G>::kThreads,
+                                                  smem);
+    int64_t ctas = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
+    if (ctas > total_tiles) ctas = total_tiles;
+    cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (ctas <= 0) return cudaSuccess;
+    k_step_batch<T, MW, G><<<(unsigned)ctas, Shape<G>::kThreads, smem, st>>>(d_args, d_prefix, ngrids,
+                                                                              d_queue);
+    return cudaGetLastError();
   }
-  if (w == 1) return launch_step_t<float, 1>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-  if (w == 2) return launch_step_t<float, 2>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-  if (w == 3) return launch_step_t<float, 3>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-  return launch_step_t<float, 4>(g, dt, chem_frac, chem_tol, chem_max_sub, st);
-}
+};
 
-template <typename T, int MW>
-static cudaError_t launch_batch_t(const StepArgs *d_args, const int64_t *d_prefix, int ngrids,
-                                  int64_t total, unsigned long long *d_queue, int nbins, int device,
-                                  cudaStream_t st) {
-  configure_smem<T, MW>();
-  int nsm = 0, per_sm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-  const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(nbins);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batch<T, MW>, kThreads, smem);
-  int64_t ctas = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
-  if (ctas > total) ctas = total;
-  cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
-  if (e != cudaSuccess) return e;
-  if (ctas <= 0) return cudaSuccess;
-  k_step_batch<T, MW><<<(unsigned)ctas, kThreads, smem, st>>>(d_args, d_prefix, ngrids, d_queue);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_step_batch(int precision, int mw, const StepArgs *d_args, const int64_t *d_prefix,
+cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int device, cudaStream_t st) {
-  (void)mw;  // the memory words follow from nbins
-  const int w = compute_words(nbins);
-  if (precision == 0) {
-    if (w == 1) return launch_batch_t<double, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-    if (w == 2) return launch_batch_t<double, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-    if (w == 3) return launch_batch_t<double, 3>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-    return launch_batch_t<double, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-  }
-  if (w == 1) return launch_batch_t<float, 1>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-  if (w == 2) return launch_batch_t<float, 2>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-  if (w == 3) return launch_batch_t<float, 3>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
-  return launch_batch_t<float, 4>(d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st);
+  return dispatch_step(precision, nbins, group,
+                       BatchLaunch{d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st});
 }
 
 // ----------------------------------------------------------------------------

@@ -47,6 +47,15 @@ class sx_budget(C.Structure):
                     in_flight=self.in_flight)
 
 
+SX_TUNE_MAX_CANDIDATES = 4
+
+
+class sx_tune_result(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("ncandidates", C.c_int32),
+                ("candidates", C.c_int32 * SX_TUNE_MAX_CANDIDATES),
+                ("ms_per_step", C.c_double * SX_TUNE_MAX_CANDIDATES)]
+
+
 class sx_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("step", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("kappa", C.c_double),
@@ -74,6 +83,10 @@ _SIGS = [
     ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
     ("sx_get_info", C.c_int, [C.c_void_p, _P(sx_info)]),
     ("sx_profile", C.c_int, [C.c_void_p, C.c_int]),
+    ("sx_set_variant", C.c_int, [C.c_void_p, C.c_int32]),
+    ("sx_get_variant", C.c_int, [C.c_void_p, _P(C.c_int32)]),
+    ("sx_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_size_t,
+                              _P(sx_tune_result)]),
     ("sx_grid_update_mark", C.c_int, [C.c_void_p, C.c_double, C.c_double, _P(C.c_int32),
                                       _P(C.c_int64)]),
     ("sx_grid_update_apply", C.c_int, [C.c_void_p, C.c_int64, _P(C.c_double), _P(C.c_int64),
@@ -191,6 +204,23 @@ def sx_get_info(ctx) -> sx_info:
 
 def sx_profile(ctx, enable: bool):
     _check(ctx, lib().sx_profile(ctx, 1 if enable else 0))
+
+
+def sx_set_variant(ctx, variant: int):
+    _check(ctx, lib().sx_set_variant(ctx, variant))
+
+
+def sx_get_variant(ctx) -> int:
+    v = C.c_int32()
+    _check(ctx, lib().sx_get_variant(ctx, C.byref(v)))
+    return v.value
+
+
+def sx_autotune(ctx, dt: float, nsteps: int, scratch_ptr: int, scratch_bytes: int) -> sx_tune_result:
+    r = sx_tune_result()
+    _check(ctx, lib().sx_autotune(ctx, dt, nsteps, C.c_void_p(scratch_ptr), scratch_bytes,
+                                  C.byref(r)))
+    return r
 
 
 def sx_grid_update_mark(ctx, y_thresh: float, min_spacing: float, n: int) -> np.ndarray:
@@ -423,6 +453,28 @@ class Solver:
 
     def profile(self, enable: bool = True):
         sx_profile(self.ctx, enable)
+
+    @property
+    def variant(self) -> int:
+        """Vertices per warp of the step kernel (2 or 4)."""
+        return sx_get_variant(self.ctx)
+
+    @variant.setter
+    def variant(self, v: int):
+        sx_set_variant(self.ctx, int(v))
+
+    def autotune(self, dt: float, nsteps: int = 4) -> dict:
+        """Time every step-kernel variant for nsteps steps from the current
+        state and keep the fastest; the state is saved in a scratch copy of
+        the workspace (allocated here for the call) and restored."""
+        scratch = self._torch.empty_like(self.workspace)
+        try:
+            r = sx_autotune(self.ctx, dt, nsteps, scratch.data_ptr(), scratch.numel())
+        finally:
+            del scratch
+        k = r.ncandidates
+        return dict(variant=r.variant, candidates=list(r.candidates[:k]),
+                    ms_per_step=list(r.ms_per_step[:k]))
 
     @property
     def info(self) -> dict:

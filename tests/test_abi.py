@@ -62,3 +62,15 @@ def test_argument_errors_without_gpu(libpath):
     with pytest.raises(S.SimplexError) as e:
         S.sx_create(cfg, I.fibonacci_bins(42))
     assert e.value.code == S.SX_EINVAL
+
+
+def test_variant_and_autotune_argument_errors(libpath):
+    """The launch-variant calls reject a missing context before touching a GPU."""
+    from paper_0912_4273_gb300 import simplex as S
+
+    L = S.lib()
+    assert L.sx_set_variant(None, 4) == S.SX_EINVAL
+    v = ctypes.c_int32()
+    assert L.sx_get_variant(None, ctypes.byref(v)) == S.SX_EINVAL
+    r = S.sx_tune_result()
+    assert L.sx_autotune(None, 1.0, 1, None, 0, ctypes.byref(r)) == S.SX_EINVAL

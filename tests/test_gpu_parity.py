@@ -46,11 +46,14 @@ def c0():
     return prob, bins, ref, snaps
 
 
+@pytest.mark.parametrize("variant", [4, 2])
 @pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
                                                  (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
-def test_c0_parity(c0, precision, ytol, btol):
+def test_c0_parity(c0, precision, ytol, btol, variant):
     prob, bins, ref, snaps = c0
     s = S.Solver(bins, precision=precision, seed=0, kappa=ref.kappa).load(prob)
+    s.variant = variant
+    assert s.variant == variant
     for k in range(4):
         s.step(DT, 50)
         y_ref, b_ref, ph_ref = snaps[k]
@@ -182,20 +185,23 @@ def test_invalid_grids_are_rejected():
     s.close()
 
 
-def test_batched_step_equals_single_grid_steps():
+@pytest.mark.parametrize("variant", [4, 2])
+def test_batched_step_equals_single_grid_steps(variant):
     """Grids stepped together in one persistent launch give bit-identical
     results to each grid stepped alone (every tile does the same arithmetic
-    whichever CTA takes it)."""
+    whichever CTA takes it), with the variant of the batch's first grid."""
     bins = I.fibonacci_bins(42)
     probs = [I.stromgren_problem(n, seed=s) for n, s in ((300, 1), (2048, 2), (5000, 3), (777, 4))]
     dts = [DT, 0.5 * DT, 2 * DT, DT]
     alone = []
     for p, dt in zip(probs, dts):
         s = S.Solver(bins, seed=7).load(p)
+        s.variant = variant
         s.step(dt, 23)
         alone.append((s.y, s.budget, s.photons()))
         s.close()
     sol = [S.Solver(bins, seed=7).load(p) for p in probs]
+    sol[0].variant = variant
     batch = S.Batch(max_grids=8)
     batch.step(sol, dts, 10)
     batch.step(sol, dts, 13)
@@ -287,3 +293,34 @@ def test_clumpy_medium_with_16_sources(precision, ytol, btol):
         assert budget_err(s.budget, ref.budget) <= btol
     assert s.info["nsources"] == 16
     s.close()
+
+
+def test_autotune_leaves_the_state_and_keeps_a_variant(c0):
+    """The autotuner times both step-kernel variants from the current state
+    and restores it exactly; stepping on equals stepping with the chosen
+    variant set by hand at the same point."""
+    prob, bins, ref, snaps = c0
+    s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa).load(prob)
+    s.step(DT, 50)
+    y, b, ph, st = s.y, s.budget, s.photons(), s.info["step"]
+    r = s.autotune(DT, 4)
+    assert r["variant"] in (2, 4) and sorted(r["candidates"]) == [2, 4]
+    assert all(ms > 0 for ms in r["ms_per_step"])
+    assert r["ms_per_step"][r["candidates"].index(r["variant"])] == min(r["ms_per_step"])
+    assert s.variant == r["variant"]
+    assert np.array_equal(s.y, y) and s.budget == b and np.array_equal(s.photons(), ph)
+    assert s.info["step"] == st
+    s.step(DT, 50)
+    u = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa).load(prob)
+    u.step(DT, 50)
+    u.variant = r["variant"]
+    u.step(DT, 50)
+    assert np.array_equal(s.y, u.y) and s.budget == u.budget
+    y_ref, b_ref, _ = snaps[1]
+    assert np.abs(s.y - y_ref).max() <= 1e-4
+    assert budget_err(s.budget, b_ref) <= 1e-5
+    with pytest.raises(S.SimplexError) as e:
+        s.variant = 3
+    assert e.value.code == S.SX_EINVAL
+    s.close()
+    u.close()
