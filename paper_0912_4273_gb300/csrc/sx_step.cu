@@ -402,7 +402,6 @@ struct Shape {
   static constexpr int kCap = 18 * G;  // out-edges of a group staged at once in phase 3
   static constexpr int kLanesPerVertex = 32 / G;
 };
-constexpr int kLcap = 64;               // packets listed at once in phase 1
 
 // One round of photon packets arriving at the vertices of a warp's group:
 // lane i adds `val` to bin `key & 127` of group vertex `key >> 7` (if `on`).
@@ -465,7 +464,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   __shared__ long long s_step;
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
-  constexpr int kScr1 = kLcap * 4 + kLcap * 2;
+  constexpr int kScr1 = 0;
   constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
   constexpr int kScrB = 96 * (int)sizeof(typename Bud<T>::type);  // the budget terms of a warp
   constexpr int kScr13 = kScr1 > kScr3 ? kScr1 : kScr3;
@@ -529,8 +528,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
 
   // ---------------- phase 1: gather, remap, sources ----------------
   {
-    int32_t *lsrc = reinterpret_cast<int32_t *>(s_scr[warp]);     // [kLcap] sender
-    uint16_t *lkey = reinterpret_cast<uint16_t *>(lsrc + kLcap);  // [kLcap] vertex << 7 | old bin
     if (s_incoming) {
       // after a grid update the photons in flight arrive as a field in the
       // previous buffer (the masks are all clear: no gather this step)
@@ -570,40 +567,42 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
         if (lane >= d) incl += t;
       }
       const int total = __shfl_sync(0xffffffffu, incl, 31);
-      // the packets as a list (sender, vertex, old bin) in (edge, bin) order,
-      // kLcap entries at a time
-      for (int p0 = 0; p0 < total; p0 += kLcap) {
-        int pos = incl - cnt - p0;
-        const bool all = total <= kLcap;
+      // The packets of the chunk in (edge, bin) order: lane j takes packet
+      // p + j, found without a list: its edge is the lowest lane whose
+      // inclusive count exceeds p + j (binary search over the lanes), its
+      // bin the r-th set bit of that edge's mask.
+      for (int p = 0; p < total; p += 32) {
+        const int j = p + lane;
+        const bool on = j < total;
+        int k = 0;
+#pragma unroll
+        for (int s2 = 16; s2 > 0; s2 >>= 1) {
+          const int ik = __shfl_sync(0xffffffffu, incl, k + s2 - 1);
+          if (ik <= j) k += s2;
+        }
+        k = min(k, 31);
+        const int ek = __shfl_sync(0xffffffffu, incl - cnt, k);  // packets before edge k
+        const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
+        const int gk = __shfl_sync(0xffffffffu, g, k);
+        int r = j - ek;  // rank of the packet among edge k's bins
+        int bo = 0;
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
-          uint32_t m = my_m[w];
-          while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1u;
-            if (all || (pos >= 0 && pos < kLcap)) {
-              lsrc[pos] = my_src;
-              lkey[pos] = (uint16_t)((g << 7) | (32 * w + i));
-            }
-            ++pos;
+          uint32_t m = __shfl_sync(0xffffffffu, my_m[w], k);
+          const int c = __popc(m);
+          if (r >= 0 && r < c) {
+            for (int t = 0; t < r; ++t) m &= m - 1u;
+            bo = 32 * w + __ffs(m) - 1;
           }
+          r -= c;
         }
-        __syncwarp();
-        const int nl = min(total - p0, kLcap);
-        for (int j0 = 0; j0 < nl; j0 += 32) {
-          const int j = j0 + lane;
-          const bool on = j < nl;
-          int key = 0;
-          T val = T(0);
-          if (on) {
-            const int kk = lkey[j];
-            const int bo = kk & 127;
-            val = Pp[(size_t)lsrc[j] * nbp + bo];
-            key = (kk & ~127) | s_fwd[bo];
-          }
-          add_round<T, MW>(grow, nbs, gocc, on, key, val, lt_mask);
+        int key = 0;
+        T val = T(0);
+        if (on) {
+          val = Pp[(size_t)src * nbp + bo];
+          key = (gk << 7) | s_fwd[bo];
         }
-        __syncwarp();
+        add_round<T, MW>(grow, nbs, gocc, on, key, val, lt_mask);
       }
     }
     // a source puts its share in every bin
@@ -742,16 +741,32 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
           for (int w = 0; w < MW; ++w) s_am[idx][w] = 0u;
         }
       }
-      // the (vertex, bin) pairs holding photons, vertex-major, bins ascending;
-      // sinks pass nothing on
-      int np = 0;
-      for (int g = ga; g < gb; ++g) {
-        if ((sinks >> g) & 1u) continue;
+      // the (vertex, bin) pairs holding photons, vertex-major, bins ascending
+      // (sinks pass nothing on): lane c takes mask word c % MW of vertex
+      // ga + c / MW, places its bits after those of the lower lanes
+      int np;
+      {
+        const int nw = (gb - ga) * MW;
+        uint32_t word = 0u;
+        int gq = 0, wq = 0;
+        if (lane < nw) {
+          gq = ga + lane / MW;
+          wq = lane % MW;
+          if (!((sinks >> gq) & 1u)) word = gocc[gq][wq];
+        }
+        const int cnt = __popc(word);
+        int incl = cnt;
 #pragma unroll
-        for (int w = 0; w < MW; ++w) {
-          const uint32_t occ = gocc[g][w];
-          if ((occ >> lane) & 1u) s_pair[np + __popc(occ & lt_mask)] = (uint16_t)((g << 7) | (32 * w + lane));
-          np += __popc(occ);
+        for (int d = 1; d < 32; d <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += t;
+        }
+        np = __shfl_sync(0xffffffffu, incl, 31);
+        int pos = incl - cnt;
+        while (word) {
+          const int i = __ffs(word) - 1;
+          word &= word - 1u;
+          s_pair[pos++] = (uint16_t)((gq << 7) | (32 * wq + i));
         }
       }
       __syncwarp();
