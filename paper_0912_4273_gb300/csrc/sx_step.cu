@@ -456,10 +456,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   __shared__ uint32_t s_occ[kTile][MW];
   __shared__ int32_t s_R[kWarps][kGroup + 1];  // row pointers of each warp's group
   // the chemistry's inputs: per-vertex constants and y (copied in while
-  // phase 1 runs), N_in (written by phase 1)
+  // phase 1 runs)
   __shared__ __align__(16) VConst s_vc[kTile];
   __shared__ __align__(16) double s_y[kTile];
-  __shared__ typename Bud<T>::type s_nin[kTile];
+
   __shared__ int s_incoming;
   __shared__ long long s_step;
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
@@ -620,23 +620,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
       if (lane < MW) gocc[g][lane] = word_bins(nbins, lane);
       __syncwarp();
     }
-    // N_in of the group's vertices in stored units (empty bins hold zero):
-    // L = 32 / G lanes per vertex, each summing every L-th bin, then a
-    // reduction over the L lanes
-    __syncwarp();
-    {
-      using BT = typename Bud<T>::type;
-      constexpr int L = Shape<G>::kLanesPerVertex;
-      const int g = lane / L, j = lane % L;
-      const T *row = grow + (size_t)g * nbs;
-      BT sum{};
-      for (int b = j; b < nbins; b += L) {
-        if constexpr (sizeof(T) == 8) sum = __dadd_rn(sum, row[b]); else sum = ff_add(sum, row[b]);
-      }
-#pragma unroll
-      for (int o = L / 2; o > 0; o >>= 1) sum = Bud<T>::add(sum, Bud<T>::shfl_xor(sum, o));
-      if (j == 0) s_nin[g0 + g] = sum;
-    }
   }
   __syncthreads();
 
@@ -654,8 +637,21 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
     int nsub = 0, capped = 0;
     if (v < a.n) {
       const VConst c = s_vc[vl];
+      // N_in in stored units: the occupied bins of the vertex, ascending
+      const T *row = s_I + (size_t)vl * nbs;
+      typename Bud<T>::type nin_acc{};
+#pragma unroll
+      for (int w = 0; w < MW; ++w) {
+        uint32_t m = s_occ[vl][w];
+        while (m) {
+          const int i = __ffs(m) - 1;
+          m &= m - 1u;
+          if constexpr (sizeof(T) == 8) nin_acc = __dadd_rn(nin_acc, row[32 * w + i]);
+          else nin_acc = ff_add(nin_acc, row[32 * w + i]);
+        }
+      }
       if constexpr (sizeof(T) == 8) {
-        const double nin = s_nin[vl];
+        const double nin = nin_acc;
         if (c.flags & 1) {
           bud_sink = nin;  // a sink passes nothing on
         } else {
@@ -670,7 +666,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
           bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
         }
       } else {
-        const FF nin = s_nin[vl];
+        const FF nin = nin_acc;
         if (c.flags & 1) {
           bud_sink_ff = nin;  // a sink passes nothing on
         } else {
