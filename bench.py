@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "110913ba5ce9b18ab1bfa807e4eb8dc4f165d702b5fb5709a7f5ad8c259e1294",
-               "bytes_per_launch": 1059.694e6 + 382.124e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "f4ee2fe984843965beed9b5afdfa15e6ccafee1ca5462ace38219c05c56c150d",
+               "bytes_per_launch": 1060.390e6 + 380.278e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
