@@ -443,7 +443,7 @@ __device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
 // Only bins that hold photons are touched: a bin without photons sets no mask
 // bit, so no reader looks at its stored value, and it is not written.
 template <typename T, int MW, int G>
-__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool reload) {
+__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool reload, bool more) {
   constexpr int kGroup = G;
   constexpr int kWarps = Shape<G>::kWarps;
   constexpr int kThreads = Shape<G>::kThreads;
@@ -628,6 +628,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   // (FP64 sums, or float-float in FP32 mode)
   double bud_abs = 0.0, bud_sink = 0.0;
   FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f};
+  unsigned diag_nsub = 0, diag_capped = 0;  // subcycle counters, summed after phase 3
   if (warp < kTile / 32) {
     cp_async_wait_all();
     __syncwarp();
@@ -696,16 +697,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
       }
     }
     s_f[vl] = f;
-    unsigned ns = (unsigned)nsub, nc = (unsigned)capped;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-      ns += __shfl_down_sync(0xffffffffu, ns, d);
-      nc += __shfl_down_sync(0xffffffffu, nc, d);
-    }
-    if (lane == 0) {
-      if (ns) atomicAdd(&a.diag[kDiagSubcycles], (unsigned long long)ns);
-      if (nc) atomicAdd(&a.diag[kDiagCapped], (unsigned long long)nc);
-    }
+    diag_nsub = (unsigned)nsub;
+    diag_capped = (unsigned)capped;
   }
   __syncthreads();
 
@@ -825,6 +818,18 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
       ga = gb;
     }
   }
+  if (warp < kTile / 32) {  // the chemistry lanes' subcycle counters
+    unsigned ns = diag_nsub, nc = diag_capped;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      ns += __shfl_down_sync(0xffffffffu, ns, d);
+      nc += __shfl_down_sync(0xffffffffu, nc, d);
+    }
+    if (lane == 0) {
+      if (ns) atomicAdd(&a.diag[kDiagSubcycles], (unsigned long long)ns);
+      if (nc) atomicAdd(&a.diag[kDiagCapped], (unsigned long long)nc);
+    }
+  }
   // ---------------- budget partials of the tile ----------------
   // every lane's terms go to its warp's scratch; then warp 0 sums the photons
   // in flight, warp 1 the escaped ones (and those passed to sinks), warp 2
@@ -861,14 +866,14 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
       }
     }
   }
-  __syncthreads();  // shared state is reused by the next tile of a persistent CTA
+  if (more) __syncthreads();  // shared state is reused by the next tile of a persistent CTA
 }
 
 // One grid, one CTA per tile (the hardware hands tiles to SMs as they free up,
 // which balances tiles of unequal cost).
 template <typename T, int MW, int G>
 __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_step(const StepArgs a) {
-  step_tile<T, MW, G>(a, blockIdx.x, true);
+  step_tile<T, MW, G>(a, blockIdx.x, true, false);
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
@@ -891,7 +896,7 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
       const int mid = (lo + hi + 1) >> 1;
       if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid);
+    step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid, true);
     cur_grid = lo;
   }
 }
