@@ -47,9 +47,10 @@ enum {
 
 enum {
     SX_FP64 = 0,           /* photons, transport and chemistry in FP64 */
-    SX_FP32_TRANSPORT = 1  /* photons and transport in FP32 (Kahan-compensated
-                              gathers); chemistry, neutral fraction and the
-                              photon budget in FP64 */
+    SX_FP32_TRANSPORT = 1  /* photons and transport in FP32 (sums in a fixed
+                              order); chemistry rates in FP32 with the neutral
+                              fraction accumulated in FP64; the photon budget
+                              in float-float and FP64 */
 };
 
 #define SX_MAX_BINS 128
@@ -136,8 +137,8 @@ int sx_add_source(sx_ctx *ctx, int32_t vertex, double photons_per_s);
 /* Queue nsteps radiative-transfer steps of dt_s seconds each (Sect. 4.6):
    per step, rotate the bins at random (Philox4x32-10, counter = step), move
    packets in flight to the closest bin of the new orientation, inject the
-   sources, update ionisation and absorb (FP64), route the transmitted photons
-   one edge further.  Errors: SX_EINVAL (dt <= 0, nsteps < 0), SX_ESTATE. */
+   sources, update ionisation and absorb, route the transmitted photons one
+   edge further.  Errors: SX_EINVAL (dt <= 0, nsteps < 0), SX_ESTATE. */
 int sx_step(sx_ctx *ctx, double dt_s, int32_t nsteps);
 
 /* Wait for the context's queued work. */
