@@ -877,7 +877,9 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_st
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
-// queue; a tile is one grid's 32 consecutive vertices.
+// queue, kBatchChunk consecutive tiles at a time; a tile is one grid's 32
+// consecutive vertices.
+constexpr int kBatchChunk = 8;
 template <typename T, int MW, int G>
 __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
     k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
@@ -886,18 +888,23 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
   const int64_t total = prefix[ngrids];
   int cur_grid = -1;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, 1ull);
+    // kBatchChunk consecutive tiles per grab: one atomic on the shared
+    // counter serves several tiles
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, (unsigned long long)kBatchChunk);
     __syncthreads();
-    const int64_t t = s_item;
+    const int64_t t0 = s_item;
     __syncthreads();
-    if (t >= total) break;
-    int lo = 0, hi = ngrids - 1;  // the grid whose tile range holds t
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    if (t0 >= total) break;
+    const int64_t t1 = t0 + kBatchChunk < total ? t0 + kBatchChunk : total;
+    for (int64_t t = t0; t < t1; ++t) {
+      int lo = 0, hi = ngrids - 1;  // the grid whose tile range holds t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid, true);
+      cur_grid = lo;
     }
-    step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid, true);
-    cur_grid = lo;
   }
 }
 
