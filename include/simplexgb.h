@@ -186,6 +186,33 @@ int sx_grid_update_apply(sx_ctx *ctx, int64_t n_new, const double *pos, const in
 int sx_profile(sx_ctx *ctx, int enable);
 
 /* ---------------------------------------------------------------------------
+ * Checkpoints (a system facility, no counterpart in the paper).  A
+ * checkpoint holds a loaded grid's tables and state -- positions, CSR,
+ * per-edge and per-vertex tables, neutral fractions, the photons in flight
+ * and their routing, budget, sources, step counters -- in one little-endian
+ * file; restoring it and stepping on gives bit-identical results to stepping
+ * on from the save.
+ * ------------------------------------------------------------------------- */
+
+/* Write the context's grid and state to path (overwritten).  Waits for the
+   stream.  Errors: SX_EINVAL (path not writable), SX_ESTATE (no grid, or a
+   grid update marked but not applied), SX_ECUDA. */
+int sx_save(sx_ctx *ctx, const char *path);
+
+/* Vertex and directed-edge counts of the grid in a checkpoint, to size the
+   workspace (sx_workspace_bytes).  Errors: SX_EINVAL (not a checkpoint). */
+int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz);
+
+/* Replace the context's grid and state by the checkpoint's, in the caller's
+   workspace (>= sx_workspace_bytes for the checkpoint's n and nnz, 256-byte
+   aligned).  The context must have the checkpoint's bins (directions) and
+   precision; the run parameters (seed, sigma, alpha_B, kappa, chemistry)
+   are the checkpoint's.  Errors: SX_EINVAL (not a checkpoint, other bins or
+   precision, truncated file), SX_ENOMEM (workspace too small), SX_ECUDA. */
+int sx_restore(sx_ctx *ctx, const char *path, void *d_workspace, int64_t workspace_bytes);
+
+/* ---------------------------------------------------------------------------
+ * Launch shape of the step kernel/* ---------------------------------------------------------------------------
  * Launch shape of the step kernel (a system choice, no counterpart in the
  * paper).  A step launch works on 32-vertex tiles; its variant is the number
  * of consecutive vertices one warp works on: 4 (8 warps per tile, the

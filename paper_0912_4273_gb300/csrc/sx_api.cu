@@ -512,6 +512,223 @@ int sx_read_neutral_fraction(sx_ctx *c, double *y_out) {
   return SX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints: the grid's tables and state as workspace regions, plus the
+// host state, in one little-endian file.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr char kCkptMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '1'};
+
+struct CkptHeader {
+  char magic[8];
+  int64_t n, nnz;
+  int32_t nbins, precision;
+  uint64_t seed;
+  double sigma, alpha_B, kappa_cfg, chem_frac, chem_tol;
+  int32_t chem_max_sub, nsrc;
+  int64_t step;
+  double emitted, punit;
+  int32_t punit_set, fresh_update;
+  double carry_abs, carry_esc, carry_fly;
+  int32_t group, max_degree;
+  uint64_t bytes_a, bytes_p, bytes_m, bytes_b, bytes_col;
+};
+
+struct File {
+  FILE *f = nullptr;
+  explicit File(const char *path, const char *mode) : f(std::fopen(path, mode)) {}
+  ~File() {
+    if (f) std::fclose(f);
+  }
+  bool write(const void *p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+  bool read(void *p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+};
+
+// The workspace regions a checkpoint holds, for a grid of this layout whose
+// next step is `step`: [offset, bytes] of the tables and y, the photons and
+// masks that step reads, the partials/tables/sources/counters, the sender
+// ids, kappa.
+constexpr int kCkptRegions = 6;
+struct CkptRegions {
+  size_t off[kCkptRegions], bytes[kCkptRegions];
+};
+CkptRegions ckpt_regions(const sx::Layout &L, int64_t n, int64_t nnz, int nbins, int precision,
+                         int64_t step) {
+  const int nbp = (nbins + 3) / 4 * 4;
+  const int mw = nbins <= 32 ? 1 : (nbins <= 64 ? 2 : 4);
+  const size_t tsz = precision == SX_FP64 ? sizeof(double) : sizeof(float);
+  const int next = (int)((step & 1) ^ 1);  // the buffers the next step reads
+  CkptRegions r;
+  r.off[0] = L.off_pos;
+  r.bytes[0] = L.off_P0 - L.off_pos;
+  r.off[1] = next ? L.off_P1 : L.off_P0;
+  r.bytes[1] = tsz * (size_t)nbp * (size_t)n;
+  r.off[2] = next ? L.off_M1 : L.off_M0;
+  r.bytes[2] = sizeof(uint32_t) * (size_t)mw * (size_t)nnz;
+  r.off[3] = L.off_partials;
+  r.bytes[3] = L.off_kpart - L.off_partials;
+  r.off[4] = L.off_s_col;
+  r.bytes[4] = sizeof(int32_t) * (size_t)nnz;
+  r.off[5] = L.off_kappa;
+  r.bytes[5] = sizeof(double);
+  return r;
+}
+}  // namespace
+
+int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz) {
+  if (!path || !n || !nnz) return SX_EINVAL;
+  File f(path, "rb");
+  CkptHeader h;
+  if (!f.f || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0) return SX_EINVAL;
+  *n = h.n;
+  *nnz = h.nnz;
+  return SX_OK;
+}
+
+int sx_save(sx_ctx *c, const char *path) {
+  if (!c) return SX_EINVAL;
+  if (!path) return fail(c, SX_EINVAL, "NULL path");
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (c->marked) return fail(c, SX_ESTATE, "a grid update is pending (mark without apply)");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  const sx::DevGrid &g = c->g;
+  const CkptRegions r = ckpt_regions(c->L, g.n, g.nnz, g.nbins, c->cfg.precision, c->step);
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  h.n = g.n;
+  h.nnz = g.nnz;
+  h.nbins = c->cfg.nbins;
+  h.precision = c->cfg.precision;
+  h.seed = c->cfg.seed;
+  h.sigma = c->cfg.sigma;
+  h.alpha_B = c->cfg.alpha_B;
+  h.kappa_cfg = c->cfg.kappa;
+  h.chem_frac = c->cfg.chem_frac;
+  h.chem_tol = c->cfg.chem_tol;
+  h.chem_max_sub = c->cfg.chem_max_sub;
+  h.nsrc = (int32_t)c->src_vertex.size();
+  h.step = c->step;
+  h.emitted = c->emitted;
+  h.punit = g.punit;
+  h.punit_set = c->punit_set ? 1 : 0;
+  h.fresh_update = c->fresh_update ? 1 : 0;
+  h.carry_abs = c->carry_abs;
+  h.carry_esc = c->carry_esc;
+  h.carry_fly = c->carry_fly;
+  h.group = g.group;
+  h.max_degree = c->max_degree;
+  h.bytes_a = r.bytes[0];
+  h.bytes_p = r.bytes[1];
+  h.bytes_m = r.bytes[2];
+  h.bytes_b = r.bytes[3];
+  h.bytes_col = r.bytes[4];
+  std::vector<char> buf;
+  File f(path, "wb");
+  if (!f.f) return fail(c, SX_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = f.write(&h, sizeof(h)) && f.write(c->bins.data(), sizeof(double) * c->bins.size()) &&
+            f.write(c->src_vertex.data(), sizeof(int32_t) * c->src_vertex.size()) &&
+            f.write(c->src_rate.data(), sizeof(double) * c->src_rate.size());
+  const char *base = static_cast<const char *>(c->ws_base);
+  for (int k = 0; k < kCkptRegions && ok; ++k) {
+    buf.resize(r.bytes[k]);
+    SX_CUDA(c, cudaMemcpyAsync(buf.data(), base + r.off[k], r.bytes[k], cudaMemcpyDeviceToHost, c->stream));
+    SX_CUDA(c, cudaStreamSynchronize(c->stream));
+    ok = f.write(buf.data(), r.bytes[k]);
+  }
+  if (!ok) return fail(c, SX_EINVAL, std::string("write to ") + path + " failed");
+  return SX_OK;
+}
+
+int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace_bytes) {
+  if (!c) return SX_EINVAL;
+  if (!path || !d_workspace) return fail(c, SX_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
+    return fail(c, SX_EINVAL, "workspace not 256-byte aligned");
+  File f(path, "rb");
+  CkptHeader h;
+  if (!f.f || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)
+    return fail(c, SX_EINVAL, std::string(path) + " is not a checkpoint");
+  if (h.nbins != c->cfg.nbins || h.precision != c->cfg.precision)
+    return fail(c, SX_EINVAL, "checkpoint bins or precision differ from the context's");
+  if (h.n < 1 || h.nnz < 0 || h.nsrc < 0 || h.nsrc > sx::kMaxSources)
+    return fail(c, SX_EINVAL, "corrupt checkpoint header");
+  std::vector<double> bins(3 * (size_t)h.nbins);
+  std::vector<int32_t> srcv(h.nsrc);
+  std::vector<double> srcr(h.nsrc);
+  if (!f.read(bins.data(), sizeof(double) * bins.size()) ||
+      !f.read(srcv.data(), sizeof(int32_t) * srcv.size()) ||
+      !f.read(srcr.data(), sizeof(double) * srcr.size()))
+    return fail(c, SX_EINVAL, "truncated checkpoint");
+  if (bins != c->bins) return fail(c, SX_EINVAL, "checkpoint bin directions differ from the context's");
+  const sx::Layout L = sx::make_layout(h.n, h.nnz, h.nbins, h.precision);
+  const size_t need = L.total + sizeof(double) * 3 * sx::kMaxBins + 256;
+  if (workspace_bytes < 0 || (size_t)workspace_bytes < need)
+    return fail(c, SX_ENOMEM, "workspace too small for the checkpoint's grid");
+  const CkptRegions r = ckpt_regions(L, h.n, h.nnz, h.nbins, h.precision, h.step);
+  if (r.bytes[0] != h.bytes_a || r.bytes[1] != h.bytes_p || r.bytes[2] != h.bytes_m ||
+      r.bytes[3] != h.bytes_b || r.bytes[4] != h.bytes_col)
+    return fail(c, SX_EINVAL, "checkpoint written by an incompatible layout");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  const cudaStream_t st = c->stream;
+  c->loaded = false;
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  char *base = static_cast<char *>(d_workspace);
+  // the buffers of the step that is not restored start clear
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_P0, 0, L.off_partials - L.off_P0, st));
+  std::vector<char> buf;
+  for (int k = 0; k < kCkptRegions; ++k) {
+    buf.resize(r.bytes[k]);
+    if (!f.read(buf.data(), r.bytes[k])) return fail(c, SX_EINVAL, "truncated checkpoint");
+    SX_CUDA(c, cudaMemcpyAsync(base + r.off[k], buf.data(), r.bytes[k], cudaMemcpyHostToDevice, st));
+    SX_CUDA(c, cudaStreamSynchronize(st));  // buf is reused
+  }
+  sx::DevGrid g{};
+  sx::bind_layout(g, d_workspace, L);
+  g.n = h.n;
+  g.nnz = h.nnz;
+  g.nbins = h.nbins;
+  g.nbp = (h.nbins + 3) / 4 * 4;
+  g.mw = h.nbins <= 32 ? 1 : (h.nbins <= 64 ? 2 : 4);
+  g.precision = h.precision;
+  g.punit = h.punit;
+  g.nsrc = h.nsrc;
+  g.group = h.group;
+  c->bins_dev = reinterpret_cast<double *>(base + L.total);
+  SX_CUDA(c, cudaMemcpyAsync(c->bins_dev, c->bins.data(), sizeof(double) * c->bins.size(),
+                             cudaMemcpyHostToDevice, st));
+  SX_CUDA(c, cudaStreamSynchronize(st));
+  c->g = g;
+  c->L = L;
+  c->ws_base = d_workspace;
+  c->ws_used = L.total + sizeof(double) * 3 * (size_t)h.nbins;
+  c->cfg.seed = h.seed;
+  c->cfg.sigma = h.sigma;
+  c->cfg.alpha_B = h.alpha_B;
+  c->cfg.kappa = h.kappa_cfg;
+  c->cfg.chem_frac = h.chem_frac;
+  c->cfg.chem_tol = h.chem_tol;
+  c->cfg.chem_max_sub = h.chem_max_sub;
+  c->step = h.step;
+  c->emitted = h.emitted;
+  c->punit_set = h.punit_set != 0;
+  c->fresh_update = h.fresh_update != 0;
+  c->carry_abs = h.carry_abs;
+  c->carry_esc = h.carry_esc;
+  c->carry_fly = h.carry_fly;
+  c->max_degree = h.max_degree;
+  c->marked = false;
+  c->removed.clear();
+  c->src_vertex = srcv;
+  c->src_rate = srcr;
+  c->src_slot.clear();
+  for (int32_t k = 0; k < h.nsrc; ++k) c->src_slot[srcv[k]] = k;
+  c->loaded = true;
+  return SX_OK;
+}
+
 int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");

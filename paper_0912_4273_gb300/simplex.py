@@ -83,6 +83,9 @@ _SIGS = [
     ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
     ("sx_get_info", C.c_int, [C.c_void_p, _P(sx_info)]),
     ("sx_profile", C.c_int, [C.c_void_p, C.c_int]),
+    ("sx_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("sx_checkpoint_info", C.c_int, [C.c_char_p, _P(C.c_int64), _P(C.c_int64)]),
+    ("sx_restore", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64]),
     ("sx_set_variant", C.c_int, [C.c_void_p, C.c_int32]),
     ("sx_get_variant", C.c_int, [C.c_void_p, _P(C.c_int32)]),
     ("sx_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_size_t,
@@ -204,6 +207,22 @@ def sx_get_info(ctx) -> sx_info:
 
 def sx_profile(ctx, enable: bool):
     _check(ctx, lib().sx_profile(ctx, 1 if enable else 0))
+
+
+def sx_save(ctx, path: str):
+    _check(ctx, lib().sx_save(ctx, os.fsencode(path)))
+
+
+def sx_checkpoint_info(path: str):
+    n, nnz = C.c_int64(), C.c_int64()
+    rc = lib().sx_checkpoint_info(os.fsencode(path), C.byref(n), C.byref(nnz))
+    if rc != SX_OK:
+        raise SimplexError(rc, f"{path} is not a checkpoint")
+    return n.value, nnz.value
+
+
+def sx_restore(ctx, path: str, ws_ptr: int, ws_bytes: int):
+    _check(ctx, lib().sx_restore(ctx, os.fsencode(path), C.c_void_p(ws_ptr), ws_bytes))
 
 
 def sx_set_variant(ctx, variant: int):
@@ -453,6 +472,21 @@ class Solver:
 
     def profile(self, enable: bool = True):
         sx_profile(self.ctx, enable)
+
+    def save(self, path: str):
+        """Write the grid and its state to a checkpoint file."""
+        sx_save(self.ctx, path)
+
+    def restore(self, path: str):
+        """Replace the grid and state by a checkpoint's (same bins and
+        precision); the workspace is allocated here for its size."""
+        n, nnz = sx_checkpoint_info(path)
+        nbytes = self.workspace_bytes(n, nnz)
+        ws = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        sx_restore(self.ctx, path, ws.data_ptr(), ws.numel())
+        self.workspace = ws
+        self.n = n
+        return self
 
     @property
     def variant(self) -> int:

@@ -74,3 +74,21 @@ def test_variant_and_autotune_argument_errors(libpath):
     assert L.sx_get_variant(None, ctypes.byref(v)) == S.SX_EINVAL
     r = S.sx_tune_result()
     assert L.sx_autotune(None, 1.0, 1, None, 0, ctypes.byref(r)) == S.SX_EINVAL
+
+
+def test_checkpoint_argument_errors(libpath, tmp_path):
+    """Checkpoint calls reject missing arguments and files that are not
+    checkpoints without touching a GPU."""
+    from paper_0912_4273_gb300 import simplex as S
+
+    L = S.lib()
+    assert L.sx_save(None, b"x") == S.SX_EINVAL
+    assert L.sx_restore(None, b"x", None, 0) == S.SX_EINVAL
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    bad = tmp_path / "bad.sxck"
+    bad.write_bytes(b"not a checkpoint")
+    assert L.sx_checkpoint_info(str(bad).encode(), ctypes.byref(n), ctypes.byref(nnz)) == S.SX_EINVAL
+    assert L.sx_checkpoint_info(str(tmp_path / "missing").encode(), ctypes.byref(n),
+                                ctypes.byref(nnz)) == S.SX_EINVAL
+    with pytest.raises(S.SimplexError):
+        S.sx_checkpoint_info(str(bad))
