@@ -101,8 +101,12 @@ void sx_config_default(sx_config *cfg);
 
 /* Create a context.  bin_dirs: nbins x 3 unit vectors (row-major, FP64) --
    the global direction bins of Sect. 2.2.3 before rotation.  They are copied.
-   Errors: SX_EINVAL (nbins out of range, zero vector, bad precision or
-   chemistry parameters), SX_ECUDA. */
+   NULL: the library's Fibonacci lattice, z_j = 1 - (2j + 1)/n,
+   phi_j = j pi (3 - sqrt 5), j = 0..n-1, in that order (the paper does not
+   give its construction); pass the directions explicitly where results must
+   match another program bit for bit (their cosines and sines come from the
+   host's math library).  Errors: SX_EINVAL (nbins out of range, not unit
+   vectors, bad precision or chemistry parameters), SX_ECUDA. */
 int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out);
 
 /* Device workspace needed for a grid of n vertices and nnz directed edges. */

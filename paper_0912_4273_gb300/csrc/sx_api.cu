@@ -1,6 +1,7 @@
 // sx_api.cu -- the extern "C" boundary declared in include/simplexgb.h.
 // Host code only marshals arguments, copies inputs and queues kernels; every
 // step of the transport path runs in the kernels of sx_setup.cu / sx_step.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -218,9 +219,24 @@ void sx_config_default(sx_config *cfg) {
 int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
   if (!out) return fail(nullptr, SX_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!cfg || !bin_dirs) return fail(nullptr, SX_EINVAL, "cfg or bin_dirs is NULL");
+  if (!cfg) return fail(nullptr, SX_EINVAL, "cfg is NULL");
   if (cfg->nbins < 1 || cfg->nbins > SX_MAX_BINS)
     return fail(nullptr, SX_EINVAL, "nbins must be in 1..128");
+  std::vector<double> fib;
+  if (!bin_dirs) {  // the Fibonacci lattice
+    const int nb = cfg->nbins;
+    fib.resize(3 * (size_t)nb);
+    const double golden = M_PI * (3.0 - std::sqrt(5.0));
+    for (int j = 0; j < nb; ++j) {
+      const double z = 1.0 - (2.0 * j + 1.0) / nb;
+      const double r = std::sqrt(std::max(0.0, 1.0 - z * z));
+      const double phi = j * golden;
+      double d[3] = {r * std::cos(phi), r * std::sin(phi), z};
+      const double l = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      for (int k = 0; k < 3; ++k) fib[3 * (size_t)j + k] = d[k] / l;
+    }
+    bin_dirs = fib.data();
+  }
   if (cfg->precision != SX_FP64 && cfg->precision != SX_FP32_TRANSPORT)
     return fail(nullptr, SX_EINVAL, "precision must be SX_FP64 or SX_FP32_TRANSPORT");
   if (!(cfg->chem_frac > 0.0 && cfg->chem_frac <= 1.0))

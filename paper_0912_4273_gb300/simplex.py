@@ -152,11 +152,16 @@ def sx_config_default() -> sx_config:
     return cfg
 
 
-def sx_create(cfg: sx_config, bin_dirs: np.ndarray):
+def sx_create(cfg: sx_config, bin_dirs):
+    """bin_dirs: nbins x 3 unit vectors, or None for the library's Fibonacci
+    lattice."""
+    ctx = C.c_void_p()
+    if bin_dirs is None:
+        _check(None, lib().sx_create(C.byref(cfg), None, C.byref(ctx)))
+        return ctx
     b = np.ascontiguousarray(bin_dirs, dtype=np.float64)
     if b.shape != (cfg.nbins, 3):
         raise ValueError("bin_dirs must be nbins x 3")
-    ctx = C.c_void_p()
     _check(None, lib().sx_create(C.byref(cfg), _ptr(b, C.c_double), C.byref(ctx)))
     return ctx
 
@@ -377,8 +382,10 @@ class Solver:
         import torch
 
         self._torch = torch
+        # an integer: that many bins on the library's Fibonacci lattice
+        nbins = int(bins) if np.isscalar(bins) else len(bins)
         cfg = sx_config_default()
-        cfg.nbins = len(bins)
+        cfg.nbins = nbins
         cfg.precision = precision
         cfg.seed = seed
         cfg.sigma = sigma
@@ -392,8 +399,8 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         cfg.stream = C.c_void_p(self.stream.cuda_stream)
         self.cfg = cfg
-        self.nbins = len(bins)
-        self.ctx = sx_create(cfg, bins)
+        self.nbins = nbins
+        self.ctx = sx_create(cfg, None if np.isscalar(bins) else bins)
         self.workspace = None
         self.n = 0
 

@@ -96,3 +96,16 @@ def test_restore_refuses_other_bins_and_non_checkpoints(tmp_path):
     assert e.value.code == S.SX_EINVAL
     s.close()
     other.close()
+
+
+def test_library_fibonacci_bins():
+    """NULL bin directions: the library's own Fibonacci lattice, which agrees
+    with the unordered lattice of the input generator (same formula)."""
+    prob = I.stromgren_problem(2000, seed=6)
+    a = S.Solver(42, precision=S.SX_FP64, seed=2).load(prob)
+    b = S.Solver(I.fibonacci_bins(42, ordered=False), precision=S.SX_FP64, seed=2).load(prob)
+    a.step(DT, 20)
+    b.step(DT, 20)
+    assert np.abs(a.y - b.y).max() <= 1e-9
+    a.close()
+    b.close()
