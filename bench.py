@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "f4ee2fe984843965beed9b5afdfa15e6ccafee1ca5462ace38219c05c56c150d",
-               "bytes_per_launch": 1060.390e6 + 380.278e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "48f53a0067d1f78e7dc09eb282b2dec889e4771bd77ad115b10f1b45c152eb52",
+               "bytes_per_launch": 1059.839e6 + 380.245e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
@@ -273,7 +273,8 @@ def run_ours(args, wl, rank, world, local_rank):
                      "algorithmic_bytes_per_launch": bytes_launch,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
         "clocks": clk,
-        "gpu_launches": 2 * args.steps,
+        # the step kernels and one rotation launch per block of steps
+        "gpu_launches": args.steps + -(-args.steps // S.SX_STEP_BLOCK),
         "e2e": e2e,
         "cpu_baseline": cpu,
         "budget_residual": (budget["emitted"] - budget["absorbed"] - budget["escaped"]

@@ -142,7 +142,11 @@ int sx_add_source(sx_ctx *ctx, int32_t vertex, double photons_per_s);
    per step, rotate the bins at random (Philox4x32-10, counter = step), move
    packets in flight to the closest bin of the new orientation, inject the
    sources, update ionisation and absorb, route the transmitted photons one
-   edge further.  Errors: SX_EINVAL (dt <= 0, nsteps < 0), SX_ESTATE. */
+   edge further.  The rotation tables of up to SX_STEP_BLOCK consecutive steps
+   are made by one kernel launch, so nsteps steps take nsteps step launches
+   and ceil(nsteps / SX_STEP_BLOCK) rotation launches.
+   Errors: SX_EINVAL (dt <= 0, nsteps < 0), SX_ESTATE. */
+#define SX_STEP_BLOCK 16
 int sx_step(sx_ctx *ctx, double dt_s, int32_t nsteps);
 
 /* Wait for the context's queued work. */

@@ -58,7 +58,8 @@ struct sx_ctx {
 };
 
 static thread_local std::string g_create_err;
-static constexpr int kGraphSteps = 16;
+static constexpr int kGraphSteps = sx::kRotAhead;  // one rotation launch per graph
+static_assert(sx::kRotAhead == SX_STEP_BLOCK, "the step block of the header");
 
 static int fail(sx_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg; else g_create_err = msg;
@@ -176,7 +177,7 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
                              cudaMemcpyHostToDevice, st));
   // tables
   SX_CUDA(c, sx::launch_setup(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
-  SX_CUDA(c, sx::launch_rotation(g, *bins_dev, c->cfg.seed, 0, 1, 1.0, st));
+  SX_CUDA(c, sx::launch_rotation(g, *bins_dev, c->cfg.seed, 1, 1, 1.0, st));
   SX_CUDA(c, sx::launch_kappa_and_consts(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
                                           y0 ? g.s_y0 : nullptr, st));
   unsigned long long diag[sx::kDiagCount];
@@ -469,11 +470,9 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
       cudaGraph_t gr = nullptr;
       SX_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t ce = cudaSuccess;
-      for (int k = 0; k < kGraphSteps && ce == cudaSuccess; ++k) {
-        ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, 0, 0, dt, c->stream);
-        if (ce == cudaSuccess)
-          ce = sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, c->stream);
-      }
+      ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, kGraphSteps, 0, dt, c->stream);
+      for (int k = 0; k < kGraphSteps && ce == cudaSuccess; ++k)
+        ce = sx::launch_step(c->g, k, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, c->stream);
       cudaError_t ee = cudaStreamEndCapture(c->stream, &gr);
       if (ce != cudaSuccess) return cuda_fail(c, ce, "graph capture");
       if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture");
@@ -492,22 +491,26 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
       c->step += c->graph_steps;
     }
   }
-  for (int32_t k = k0; k < nsteps; ++k) {
-    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, c->step, 0, dt, c->stream));
-    if (c->profiling) {
-      if (c->events_used == c->events.size()) {
-        cudaEvent_t a, b;
-        SX_CUDA(c, cudaEventCreate(&a));
-        SX_CUDA(c, cudaEventCreate(&b));
-        c->events.emplace_back(a, b);
+  // the rest: the tables of up to kRotAhead steps, then their step launches
+  for (int32_t k = k0; k < nsteps;) {
+    const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
+    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, m, 0, dt, c->stream));
+    for (int j = 0; j < m; ++j, ++k) {
+      if (c->profiling) {
+        if (c->events_used == c->events.size()) {
+          cudaEvent_t a, b;
+          SX_CUDA(c, cudaEventCreate(&a));
+          SX_CUDA(c, cudaEventCreate(&b));
+          c->events.emplace_back(a, b);
+        }
+        SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
       }
-      SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
+      SX_CUDA(c, sx::launch_step(c->g, j, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
+                                 c->stream));
+      if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
+      for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
+      c->step++;
     }
-    SX_CUDA(c, sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
-                               c->stream));
-    if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
-    for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
-    c->step++;
   }
   return SX_OK;
 }
@@ -839,7 +842,6 @@ int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scra
   const int32_t before = c->g.group == 2 ? 2 : 4;
   // the state: every device buffer of the grid, and the host counters
   SX_CUDA(c, cudaMemcpyAsync(scratch, c->ws_base, c->ws_used, cudaMemcpyDeviceToDevice, st));
-  const int64_t step0 = c->step;
   std::memset(out, 0, sizeof(*out));
   const int32_t cand[2] = {4, 2};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -852,10 +854,9 @@ int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scra
     // one untimed step (first launch of the variant), then the timed ones
     for (int32_t k = 0; k <= nsteps && ce == cudaSuccess; ++k) {
       if (k == 1) ce = cudaEventRecord(e0, st);
+      if (ce == cudaSuccess) ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, 1, 0, dt, st);
       if (ce == cudaSuccess)
-        ce = sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, step0 + k, 0, dt, st);
-      if (ce == cudaSuccess)
-        ce = sx::launch_step(c->g, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, st);
+        ce = sx::launch_step(c->g, 0, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub, st);
     }
     if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
@@ -995,10 +996,13 @@ int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_
   SX_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream));
   SX_BCUDA(b, cudaEventRecord(b->ev_copy, b->stream));
   b->copy_pending = true;
-  for (int32_t k = 0; k < nsteps; ++k) {
-    SX_BCUDA(b, sx::launch_rotation_batch(b->d_rot, n, b->stream));
-    SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.group, b->d_args, b->d_prefix, n,
-                                      b->h_prefix[n], b->d_queue, c0->cfg.nbins, b->device, b->stream));
+  for (int32_t k = 0; k < nsteps;) {  // the tables of up to kRotAhead steps, then their steps
+    const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
+    SX_BCUDA(b, sx::launch_rotation_batch(b->d_rot, n, m, b->stream));
+    for (int j = 0; j < m; ++j, ++k)
+      SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.group, b->d_args, b->d_prefix, n,
+                                        b->h_prefix[n], b->d_queue, c0->cfg.nbins, j, b->device,
+                                        b->stream));
   }
   SX_BCUDA(b, cudaEventRecord(b->ev, b->stream));
   for (int32_t i = 0; i < n; ++i) {

@@ -14,6 +14,11 @@ constexpr int kTile = 32;          // vertices per CTA in the step kernel (one c
 constexpr int kMaxSources = 4096;
 constexpr uint32_t kRotTag = 0x53583252u;  // Philox counter word 3 of the rotation draws
 constexpr int kRotMaxAttempts = 64;
+// Step tables are made kRotAhead steps at a time (one rotation launch for up
+// to kRotAhead step launches); the ring holds them, then the unrotated table.
+constexpr int kRotAhead = 16;
+constexpr int kTabUnrotated = kRotAhead;
+constexpr int kTabCount = kRotAhead + 1;
 
 // One directed Delaunay edge i -> col, stored in i's CSR row (16 bytes).
 struct __align__(16) Edge {
@@ -32,7 +37,8 @@ struct __align__(16) VConst {
   int32_t src;     // source slot or -1
 };
 
-// Written once per step by the rotation kernel, read by every CTA.
+// Written by the rotation kernel for every step, read by every CTA of that
+// step.
 struct StepTables {
   float4 qb[kMaxBins];            // quantised rotated bins (x, y, z), as exact floats
   uint32_t qbq[kMaxBins];         // the same as signed bytes (x, y, z, 0), for byte dot products
@@ -46,13 +52,13 @@ struct StepTables {
 };
 
 // Arguments of the rotation kernel for one grid.  The step index lives on the
-// device (*steps_done), so that launches of successive steps are identical and
-// can be captured in a CUDA graph.
+// device (*steps_done), so that launches of successive blocks of steps are
+// identical and can be captured in a CUDA graph.
 struct RotArgs {
   const double *bins;              // nbins x 3, unrotated
   uint64_t seed;
-  unsigned long long *steps_done;  // read, then advanced by one (unless unrotated)
-  StepTables *tab;
+  unsigned long long *steps_done;  // read, then advanced by the steps made (unless unrotated)
+  StepTables *tab;                 // the tables of the first step; the next ones follow
   int nbins;
   int unrotated;                   // 1: identity orientation (kappa), counter untouched
   int nsrc;
@@ -198,7 +204,7 @@ struct DevGrid {
   double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
   int64_t nblocks;      // tiles of kTile vertices
   int group;            // step kernel variant: vertices per warp (2 or 4; 0 = 4)
-  StepTables *tabs;     // [0] current step, [1] unrotated (kappa)
+  StepTables *tabs;     // [kTabCount]: the next steps' tables, then the unrotated one (kappa)
   unsigned long long *steps_done;  // device step counter (advanced by the rotation kernel)
   int *incoming;        // set by a grid update: the next step takes P[prev] as incoming photons
   double *src_rate;     // kMaxSources
@@ -235,18 +241,22 @@ cudaError_t launch_setup(DevGrid &g, const double *bins_dev, double sigma, doubl
 cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double sigma,
                                     double alpha_B, double kappa_cfg, const double *y0_dev,
                                     cudaStream_t st);
-cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t step,
+// Tables of the next `count` (1..kRotAhead) steps into tabs[0..count-1], or
+// the unrotated table (count 1).
+cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int count,
                             int unrotated, double dt, cudaStream_t st);
-cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
+// One step with the tables in tabs[slot].
+cudaError_t launch_step(DevGrid &g, int slot, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st);
 RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unrotated, double dt);
 StepArgs make_step_args(DevGrid &g, double dt, double chem_frac, double chem_tol, int chem_max_sub);
-// Batched: one rotation CTA per grid, then one persistent launch over the
-// tiles of all grids (work queue).  All grids share nbins and precision.
-cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, cudaStream_t st);
+// Batched: one rotation CTA per grid (tables of `count` steps), then one
+// persistent launch per step over the tiles of all grids (work queue), with
+// the tables in slot `slot` of each grid.  All grids share nbins and precision.
+cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, int count, cudaStream_t st);
 cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
-                              int nbins, int device, cudaStream_t st);
+                              int nbins, int slot, int device, cudaStream_t st);
 cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
 // dynamic grid update (sx_update.cu)

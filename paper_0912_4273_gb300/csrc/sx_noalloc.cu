@@ -50,7 +50,7 @@ constexpr size_t kOffEv = kOffEdges + up(sizeof(sx::Edge) * kNe);
 constexpr size_t kOffMeanLen = kOffEv + up(sizeof(float4) * kNe);
 constexpr size_t kOffBins = kOffMeanLen + up(sizeof(double) * kNv);
 constexpr size_t kOffTabs = kOffBins + up(sizeof(double) * 3 * sx::kMaxBins);
-constexpr size_t kOffKpart = kOffTabs + up(sizeof(sx::StepTables) * 2);
+constexpr size_t kOffKpart = kOffTabs + up(sizeof(sx::StepTables) * sx::kTabCount);
 constexpr size_t kOffKappa = kOffKpart + up(sizeof(double) * 2 * kKappaBlocks);
 constexpr size_t kOffDiag = kOffKappa + up(sizeof(double));
 constexpr size_t kOffSteps = kOffDiag + up(sizeof(unsigned long long) * sx::kDiagCount);
@@ -132,7 +132,7 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   NA_CUDA(cudaMemcpyAsync(g.s_flags, flags, n, cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemcpyAsync(bins_dev, bin_dirs, sizeof(double) * 3 * nbins, cudaMemcpyHostToDevice, st));
   NA_CUDA(sx::launch_setup(g, bins_dev, 0.0, 0.0, 0.0, st));
-  NA_CUDA(sx::launch_rotation(g, bins_dev, 0, 0, 1, 1.0, st));
+  NA_CUDA(sx::launch_rotation(g, bins_dev, 0, 1, 1, 1.0, st));
   NA_CUDA(sx::launch_kappa(g, bins_dev, st));
   unsigned long long diag[sx::kDiagCount];
   double kappa = 0.0;

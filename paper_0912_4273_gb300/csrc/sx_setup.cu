@@ -34,7 +34,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
   L.off_M0 = take(sizeof(uint32_t) * mw * nnz);
   L.off_M1 = take(sizeof(uint32_t) * mw * nnz);
   L.off_partials = take(sizeof(double) * 4 * L.nblocks);
-  L.off_tabs = take(sizeof(StepTables) * 2);
+  L.off_tabs = take(sizeof(StepTables) * kTabCount);
   L.off_src = take(sizeof(double) * kMaxSources);
   L.off_share = take(sizeof(double) * kMaxSources);
   L.off_share_f = take(sizeof(float) * kMaxSources);
@@ -334,7 +334,7 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
   const int T = 256;
   if (kappa_cfg <= 0.0) {
     k_kappa<<<(unsigned)g.nblocks_kappa, T, 0, st>>>(n, g.nbins, g.row_ptr, g.edges, g.s_ev,
-                                                     g.s_flags, g.tabs + 1, bins_dev,
+                                                     g.s_flags, g.tabs + kTabUnrotated, bins_dev,
                                                      g.kappa_part);
     k_kappa_final<<<1, T, 0, st>>>(g.nblocks_kappa, g.kappa_part, kappa_cfg, g.kappa_dev);
   } else {
@@ -346,11 +346,11 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
   return cudaGetLastError();
 }
 
-// kappa alone (k_kappa + k_kappa_final on the unrotated tables in g.tabs[1]).
+// kappa alone (k_kappa + k_kappa_final on the unrotated tables in g.tabs[kTabUnrotated]).
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st) {
   const int T = 256;
   k_kappa<<<(unsigned)g.nblocks_kappa, T, 0, st>>>(g.n, g.nbins, g.row_ptr, g.edges, g.s_ev,
-                                                   g.s_flags, g.tabs + 1, bins_dev, g.kappa_part);
+                                                   g.s_flags, g.tabs + kTabUnrotated, bins_dev, g.kappa_part);
   k_kappa_final<<<1, T, 0, st>>>(g.nblocks_kappa, g.kappa_part, 0.0, g.kappa_dev);
   return cudaGetLastError();
 }

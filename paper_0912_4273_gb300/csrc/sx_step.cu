@@ -4,19 +4,22 @@
 //               uniform quaternion), quantised rotated bins, and the map that
 //               moves packets in flight to the closest bin of the new
 //               orientation (Sect. 2.2.3).
-//  k_step<T,MW> one launch per step, pull formulation.  A CTA owns a tile of
-//               32 consecutive vertices:
-//     phase 1   warp per vertex, lane per in-edge: gather the packets routed
-//               to it in the previous step (per-edge bin masks), each moved to
-//               the closest bin of the new orientation and added in a fixed
-//               order (Kahan in FP32); add the sources (Sect. 4.3);
+//  k_step<T,MW,G> one launch per step, pull formulation.  A CTA owns a tile
+//               of 32 consecutive vertices, a warp a group of G (4 or 2)
+//               consecutive vertices whose edges are contiguous:
+//     phase 1   lanes over the group's in-edges: gather the packets routed to
+//               the group in the previous step (per-edge bin masks), each
+//               moved to the closest bin of the new orientation and added in
+//               a fixed order; add the sources (Sect. 4.3);
 //     phase 2   lane per vertex: N_in and the subcycled photoionisation /
-//               recombination in FP64 (Sect. 4.5), transmitted fraction f;
-//     phase 3   warp per vertex, lanes over (bin, edge): O = f I; associate
-//               every bin holding photons with the edge of largest quantised
-//               dot product; split O over the <= 3 most straightforward
-//               neighbours of that edge (store O / |S| once and one bin mask
-//               per outgoing edge); budget partials.
+//               recombination (Sect. 4.5), transmitted fraction f;
+//     phase 3   lanes over the group's occupied (vertex, bin) pairs: O = f I;
+//               associate every bin holding photons with the edge of largest
+//               quantised dot product; split O over the <= 3 most
+//               straightforward neighbours of that edge (store O / |S| once,
+//               one bin mask per outgoing edge); budget partials.
+//  k_step_batch the same tiles for several independent grids in one
+//               persistent launch (a shared work counter hands out tiles).
 //  k_budget     deterministic reduction of the per-CTA budget partials.
 //  k_inflight   photons in flight towards every vertex (readout).
 #include <limits.h>
@@ -71,83 +74,101 @@ __device__ void rotate_quantise(const double R[9], const double *d, int q[3]) {
   }
 }
 
-__device__ void rotation_body(const RotArgs &r) {
-  __shared__ double sR[9], sRp[9];
-  __shared__ int s_att;
-  __shared__ long long s_step;
-  __shared__ int s_qn[kMaxBins][3], s_qo[kMaxBins][3];
-  __shared__ int s_map[kMaxBins];
+constexpr int kRotThreads = 256;
+
+// Tables of `count` consecutive steps s0 .. s0+count-1 (s0 = the device step
+// counter) in one CTA.  Row k of s_R / s_q holds the orientation of step
+// s0-1+k and the bins quantised under it, so that row k is the previous
+// orientation of the step in row k+1 (at step 0 row 0 repeats step 0, which
+// remaps nothing).
+__device__ void rotation_body(const RotArgs &r, int count) {
+  __shared__ double s_R[kRotAhead + 1][9];
+  __shared__ int s_att[kRotAhead + 1];
+  __shared__ long long s_step0;
+  __shared__ int s_inc;
+  __shared__ int4 s_q[kRotAhead + 1][kMaxBins];
   const int t = threadIdx.x;
   const int nbins = r.nbins;
   if (t == 0) {
-    int att = 0, attp = 0;
-    long long step = 0;
-    if (r.unrotated) {
-      for (int i = 0; i < 9; ++i) sR[i] = sRp[i] = (i % 4 == 0) ? 1.0 : 0.0;
-    } else {
-      step = (long long)*r.steps_done;
-      *r.steps_done = (unsigned long long)(step + 1);
-      rotation_matrix(r.seed, step, sR, &att);
-      if (step > 0) rotation_matrix(r.seed, step - 1, sRp, &attp);
-      else
-        for (int i = 0; i < 9; ++i) sRp[i] = sR[i];
+    long long s0 = 0;
+    int inc = 0;
+    if (!r.unrotated) {
+      s0 = (long long)*r.steps_done;
+      *r.steps_done = (unsigned long long)(s0 + count);
+      if (r.incoming) {  // a grid update hands its photons to the first of these steps
+        inc = *r.incoming;
+        *r.incoming = 0;
+      }
     }
-    s_att = att;
-    s_step = step;
+    s_step0 = s0;
+    s_inc = inc;
   }
-  // photons each source puts in every bin this step, in stored units:
+  __syncthreads();
+  const long long s0 = s_step0;
+  if (t <= count) {  // one thread per orientation
+    if (r.unrotated) {
+      for (int i = 0; i < 9; ++i) s_R[t][i] = (i % 4 == 0) ? 1.0 : 0.0;
+      s_att[t] = 0;
+    } else {
+      rotation_matrix(r.seed, (t == 0 && s0 == 0) ? 0 : s0 - 1 + t, s_R[t], &s_att[t]);
+    }
+  }
+  // photons each source puts in every bin per step, in stored units:
   // ((rate dt) / n) / unit, the unit being a power of two
   for (int k = t; k < r.nsrc; k += blockDim.x) {
     r.share[k] = __dmul_rn(__ddiv_rn(__dmul_rn(r.src_rate[k], r.dt), (double)nbins), r.inv_punit);
     r.share_f[k] = (float)r.share[k];
   }
   __syncthreads();
-  StepTables *out = r.tab;
-  for (int b = t; b < nbins; b += blockDim.x) {
+  for (int i = t; i < (count + 1) * nbins; i += blockDim.x) {
+    const int k = i / nbins, b = i - k * nbins;
     int q[3];
-    rotate_quantise(sR, r.bins + 3 * b, q);
-    s_qn[b][0] = q[0]; s_qn[b][1] = q[1]; s_qn[b][2] = q[2];
-    out->qb[b] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
-    out->qbq[b] = (uint32_t)(q[0] & 0xFF) | ((uint32_t)(q[1] & 0xFF) << 8) | ((uint32_t)(q[2] & 0xFF) << 16);
-    rotate_quantise(sRp, r.bins + 3 * b, q);
-    s_qo[b][0] = q[0]; s_qo[b][1] = q[1]; s_qo[b][2] = q[2];
+    rotate_quantise(s_R[k], r.bins + 3 * b, q);
+    s_q[k][b] = make_int4(q[0], q[1], q[2], 0);
+    if (k > 0) {
+      StepTables *out = r.tab + (k - 1);
+      out->qb[b] = make_float4((float)q[0], (float)q[1], (float)q[2], 0.f);
+      out->qbq[b] = (uint32_t)(q[0] & 0xFF) | ((uint32_t)(q[1] & 0xFF) << 8) | ((uint32_t)(q[2] & 0xFF) << 16);
+    }
   }
   __syncthreads();
-  // closest new bin of every old bin (ties -> lowest index)
-  for (int b = t; b < nbins; b += blockDim.x) {
-    int best = 0, bestd = 0;
-    for (int b2 = 0; b2 < nbins; ++b2) {
-      const int d = s_qn[b2][0] * s_qo[b][0] + s_qn[b2][1] * s_qo[b][1] + s_qn[b2][2] * s_qo[b][2];
-      if (b2 == 0 || d > bestd) {
-        best = b2;
-        bestd = d;
+  // for every step, the closest bin of its orientation to every bin of the
+  // previous one (ties -> lowest index); packets of an old bin move there.
+  // Nothing moves at step 0 or in the unrotated table.
+  for (int i = t; i < count * kMaxBins; i += blockDim.x) {
+    const int k = i / kMaxBins, b = i - k * kMaxBins;
+    int best = b;
+    if (!r.unrotated && s0 + k > 0 && b < nbins) {
+      const int4 o = s_q[k][b];
+      int bestd = 0;
+      for (int b2 = 0; b2 < nbins; ++b2) {
+        const int4 nq = s_q[k + 1][b2];
+        const int d = nq.x * o.x + nq.y * o.y + nq.z * o.z;
+        if (b2 == 0 || d > bestd) {
+          best = b2;
+          bestd = d;
+        }
       }
     }
-    s_map[b] = best;
+    r.tab[k].fwd[b] = (unsigned char)best;
   }
-  __syncthreads();
-  // packets of an old bin move to its closest new bin; nothing moves at step 0
-  const bool remap = !r.unrotated && s_step > 0;
-  for (int b = t; b < kMaxBins; b += blockDim.x)
-    out->fwd[b] = (unsigned char)((remap && b < nbins) ? s_map[b] : b);
-  if (t == 0) {
-    out->attempts = s_att;
-    out->step = s_step;
-    out->remap = remap ? 1 : 0;
-    int inc = 0;
-    if (!r.unrotated && r.incoming) {
-      inc = *r.incoming;
-      *r.incoming = 0;
-    }
-    out->incoming = inc;
+  if (t < count) {
+    StepTables *out = r.tab + t;
+    out->attempts = s_att[t + 1];
+    out->step = s0 + t;
+    out->remap = (!r.unrotated && s0 + t > 0) ? 1 : 0;
+    out->incoming = t == 0 ? s_inc : 0;
   }
 }
 
-__global__ void __launch_bounds__(128) k_rotation(const RotArgs r) { rotation_body(r); }
+__global__ void __launch_bounds__(kRotThreads) k_rotation(const RotArgs r, int count) {
+  rotation_body(r, count);
+}
 
 // one CTA per grid of a batch
-__global__ void __launch_bounds__(128) k_rotation_batch(const RotArgs *__restrict__ ra) {
-  rotation_body(ra[blockIdx.x]);
+__global__ void __launch_bounds__(kRotThreads) k_rotation_batch(const RotArgs *__restrict__ ra,
+                                                                int count) {
+  rotation_body(ra[blockIdx.x], count);
 }
 
 RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unrotated, double dt) {
@@ -155,7 +176,7 @@ RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unr
   r.bins = bins_dev;
   r.seed = seed;
   r.steps_done = g.steps_done;
-  r.tab = g.tabs + (unrotated ? 1 : 0);
+  r.tab = g.tabs + (unrotated ? kTabUnrotated : 0);
   r.nbins = g.nbins;
   r.unrotated = unrotated;
   r.nsrc = unrotated ? 0 : g.nsrc;
@@ -168,15 +189,18 @@ RotArgs make_rot_args(DevGrid &g, const double *bins_dev, uint64_t seed, int unr
   return r;
 }
 
-cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int64_t /*step*/,
+cudaError_t launch_rotation(DevGrid &g, const double *bins_dev, uint64_t seed, int count,
                             int unrotated, double dt, cudaStream_t st) {
-  k_rotation<<<1, 128, 0, st>>>(make_rot_args(g, bins_dev, seed, unrotated, dt));
+  if (unrotated) count = 1;
+  if (count < 1 || count > kRotAhead) return cudaErrorInvalidValue;
+  k_rotation<<<1, kRotThreads, 0, st>>>(make_rot_args(g, bins_dev, seed, unrotated, dt), count);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, cudaStream_t st) {
+cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, int count, cudaStream_t st) {
   if (ngrids <= 0) return cudaSuccess;
-  k_rotation_batch<<<ngrids, 128, 0, st>>>(d_rot);
+  if (count < 1 || count > kRotAhead) return cudaErrorInvalidValue;
+  k_rotation_batch<<<ngrids, kRotThreads, 0, st>>>(d_rot, count);
   return cudaGetLastError();
 }
 
@@ -329,22 +353,6 @@ __device__ __forceinline__ void store_mask(uint32_t *__restrict__ M, int64_t e, 
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void acc_add(T &acc, T &c, T x);
-template <>
-__device__ __forceinline__ void acc_add<double>(double &acc, double &, double x) {
-  acc = __dadd_rn(acc, x);  // FP64: plain sum in the fixed edge order
-}
-template <>
-__device__ __forceinline__ void acc_add<float>(float &acc, float &c, float x) {
-  // Kahan-compensated FP32 sum
-  const float yv = __fsub_rn(x, c);
-  const float t = __fadd_rn(acc, yv);
-  c = __fsub_rn(__fsub_rn(t, acc), yv);
-  acc = t;
-}
-
-
 // Row stride (elements) of the shared photon tile: odd, so that a lane per
 // vertex walking its own row touches 32 distinct banks.
 __host__ __device__ __forceinline__ int tile_stride(int nbins) { return nbins | 1; }
@@ -443,7 +451,8 @@ __device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
 // Only bins that hold photons are touched: a bin without photons sets no mask
 // bit, so no reader looks at its stored value, and it is not written.
 template <typename T, int MW, int G>
-__device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool reload, bool more) {
+__device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *__restrict__ tab, int64_t tile,
+                                          bool reload, bool more) {
   constexpr int kGroup = G;
   constexpr int kWarps = Shape<G>::kWarps;
   constexpr int kThreads = Shape<G>::kThreads;
@@ -476,12 +485,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
   const uint32_t lt_mask = (1u << lane) - 1u;
   if (reload) {  // this step's tables (a CTA keeps them from tile to tile of one grid)
     for (int b = tid; b < kMaxBins; b += kThreads) {
-      s_qbq[b] = a.tab->qbq[b];
-      s_fwd[b] = a.tab->fwd[b];
+      s_qbq[b] = tab->qbq[b];
+      s_fwd[b] = tab->fwd[b];
     }
     if (tid == 0) {
-      s_step = a.tab->step;
-      s_incoming = a.tab->incoming;
+      s_step = tab->step;
+      s_incoming = tab->incoming;
     }
   }
   const int64_t v0 = tile * kTile;
@@ -873,7 +882,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, int64_t tile, bool 
 // which balances tiles of unequal cost).
 template <typename T, int MW, int G>
 __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_step(const StepArgs a) {
-  step_tile<T, MW, G>(a, blockIdx.x, true, false);
+  step_tile<T, MW, G>(a, a.tab, blockIdx.x, true, false);
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
@@ -883,7 +892,7 @@ constexpr int kBatchChunk = 8;
 template <typename T, int MW, int G>
 __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
     k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
-                 unsigned long long *__restrict__ queue) {
+                 unsigned long long *__restrict__ queue, int slot) {
   __shared__ long long s_item;
   const int64_t total = prefix[ngrids];
   int cur_grid = -1;
@@ -902,7 +911,7 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
         const int mid = (lo + hi + 1) >> 1;
         if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
       }
-      step_tile<T, MW, G>(args[lo], t - prefix[lo], lo != cur_grid, true);
+      step_tile<T, MW, G>(args[lo], args[lo].tab + slot, t - prefix[lo], lo != cur_grid, true);
       cur_grid = lo;
     }
   }
@@ -981,10 +990,12 @@ struct StepLaunch {
   }
 };
 
-cudaError_t launch_step(DevGrid &g, double dt, double chem_frac, double chem_tol,
+cudaError_t launch_step(DevGrid &g, int slot, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st) {
   if (g.nblocks <= 0) return cudaSuccess;
-  const StepArgs a = make_step_args(g, dt, chem_frac, chem_tol, chem_max_sub);
+  if (slot < 0 || slot >= kRotAhead) return cudaErrorInvalidValue;
+  StepArgs a = make_step_args(g, dt, chem_frac, chem_tol, chem_max_sub);
+  a.tab = g.tabs + slot;
   return dispatch_step(g.precision, g.nbins, g.group, StepLaunch{a, g.nblocks, g.nbins, st});
 }
 
@@ -994,7 +1005,7 @@ struct BatchLaunch {
   int ngrids;
   int64_t total_tiles;
   unsigned long long *d_queue;
-  int nbins, device;
+  int nbins, slot, device;
   cudaStream_t st;
   template <typename T, int MW, int G>
   cudaError_t run() const {
@@ -1010,16 +1021,17 @@ struct BatchLaunch {
     if (e != cudaSuccess) return e;
     if (ctas <= 0) return cudaSuccess;
     k_step_batch<T, MW, G><<<(unsigned)ctas, Shape<G>::kThreads, smem, st>>>(d_args, d_prefix, ngrids,
-                                                                              d_queue);
+                                                                              d_queue, slot);
     return cudaGetLastError();
   }
 };
 
 cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
-                              int nbins, int device, cudaStream_t st) {
+                              int nbins, int slot, int device, cudaStream_t st) {
+  if (slot < 0 || slot >= kRotAhead) return cudaErrorInvalidValue;
   return dispatch_step(precision, nbins, group,
-                       BatchLaunch{d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, device, st});
+                       BatchLaunch{d_args, d_prefix, ngrids, total_tiles, d_queue, nbins, slot, device, st});
 }
 
 // ----------------------------------------------------------------------------

@@ -23,6 +23,7 @@ SX_FP64, SX_FP32_TRANSPORT = 0, 1
 SX_MAX_BINS = 128
 SX_MAX_DEGREE = 64
 SX_FLAG_SINK = 1
+SX_STEP_BLOCK = 16  # steps whose rotation tables one launch makes
 
 
 class SimplexError(RuntimeError):

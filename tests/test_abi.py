@@ -45,6 +45,17 @@ def test_binding_covers_every_declared_symbol():
         assert hasattr(S, n)
 
 
+def test_binding_constants_match_the_header():
+    from paper_0912_4273_gb300 import simplex as S
+
+    txt = open(os.path.join(ROOT, "include", "simplexgb.h")).read()
+    defs = dict(re.findall(r"^#define\s+(SX_[A-Z_0-9]+)\s+(-?\d+)\b", txt, flags=re.M))
+    assert "SX_STEP_BLOCK" in defs and "SX_MAX_BINS" in defs
+    for name, val in defs.items():
+        if hasattr(S, name):
+            assert getattr(S, name) == int(val), name
+
+
 def test_argument_errors_without_gpu(libpath):
     from paper_0912_4273_gb300 import inputs as I
     from paper_0912_4273_gb300 import simplex as S

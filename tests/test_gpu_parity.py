@@ -92,8 +92,12 @@ def test_bin_counts(nbins):
 def test_deterministic_and_chunk_invariant(c0):
     prob, bins, ref, _ = c0
     out = []
-    for chunks in ((60,), (20, 40), (1,) * 60):
+    # blocks of rotation tables (SX_STEP_BLOCK steps per rotation launch)
+    # split anywhere give the same steps; so do the timed launches
+    for chunks, prof in (((60,), False), ((20, 40), False), ((1,) * 60, False),
+                         ((17, 33, 10), True)):
         s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0).load(prob)
+        s.profile(prof)
         for c in chunks:
             s.step(DT, c)
         out.append((s.y, s.budget))
@@ -222,7 +226,8 @@ def test_batched_step_equals_single_grid_steps(variant):
 
 def test_graph_replay_on_a_stream_matches_direct_launches(c0):
     """On a non-default stream sx_step replays a captured CUDA graph of 16
-    steps; results are bit-identical to single-step launches."""
+    steps (one rotation launch for all 16, then their step launches); results
+    are bit-identical to single-step launches."""
     prob, bins, ref, _ = c0
     st = torch.cuda.Stream()
     out = []
