@@ -6,10 +6,15 @@ count, a time step and a number of steps.  The server
   * admits requests in arrival order while their device workspace (the HBM
     footprint reported by sx_workspace_bytes) fits in the memory budget, and
     keeps every admitted grid's state resident on the device;
-  * advances all admitted grids that share (bins, precision) together, a
-    chunk of steps at a time, with one batched persistent launch per step
+  * advances admitted grids that share (bins, precision) together, a chunk
+    of steps at a time, with one batched persistent launch per step
     (sx_batch_step); requests join and leave between chunks, so work of
     requests that arrived at different times overlaps on the device;
+  * picks the grids of each chunk by least remaining work (steps left x
+    vertices) until their vertices fill the device (``fill_vertices``): small
+    grids share a launch, while a grid that fills the device alone is not
+    slowed down by the others, which wait resident (shortest remaining work
+    first keeps the median latency low);
   * loads newly admitted grids on their own stream while the others step;
   * reads a finished request's neutral fraction and photon budget, releases
     its workspace and records its latency (finish - arrival).
@@ -115,17 +120,24 @@ class GpuBackend:
         self.batches.clear()
 
 
+# Vertices that keep the step kernel busy: about four waves of its resident
+# 32-vertex tiles (152 SMs x 6 CTAs) on a GB300.
+DEFAULT_FILL_VERTICES = 1 << 17
+
+
 class Server:
     """Continuous batching of SimpleX2 solves under an HBM budget."""
 
     def __init__(self, backend, hbm_budget: int, chunk_steps: int = 8, max_grids: int = 256,
-                 clock: Callable[[], float] = time.perf_counter, first_fit: bool = True):
+                 clock: Callable[[], float] = time.perf_counter, first_fit: bool = True,
+                 fill_vertices: Optional[int] = DEFAULT_FILL_VERTICES):
         self.backend = backend
         self.budget = int(hbm_budget)
         self.chunk = int(chunk_steps)
         self.max_grids = int(max_grids)
         self.clock = clock
         self.first_fit = first_fit
+        self.fill = None if fill_vertices is None else int(fill_vertices)
         self.pending: collections.deque = collections.deque()
         self.active: Dict[tuple, List[list]] = collections.defaultdict(list)  # key -> [[req, solver, done, bytes]]
         self.used = 0
@@ -203,17 +215,34 @@ class Server:
                 break  # strict arrival order: later requests wait behind this one
             i += 1
 
+    def _select(self, lst: List[list]) -> List[list]:
+        """The grids of one key to advance in this chunk: least remaining
+        work first, packed while their vertices stay within the fill target
+        (at least one grid); every grid when there is no target."""
+        if self.fill is None:
+            return list(lst)
+        order = sorted(lst, key=lambda ent: ((ent[0].steps - ent[2]) * ent[0].problem.n,
+                                             ent[0].arrival, ent[0].rid))
+        picked, nv = [], 0
+        for ent in order:
+            if picked and nv + ent[0].problem.n > self.fill:
+                continue
+            picked.append(ent)
+            nv += ent[0].problem.n
+        return picked
+
     def _tick(self):
         for key in list(self.active.keys()):
             lst = self.active[key]
             if not lst:
                 continue
-            n = min(self.chunk, min(ent[0].steps - ent[2] for ent in lst))
+            sel = self._select(lst)
+            n = min(self.chunk, min(ent[0].steps - ent[2] for ent in sel))
             if n > 0:
-                self.backend.step(key, [ent[1] for ent in lst], [ent[0].dt for ent in lst], n)
-                for ent in lst:
+                self.backend.step(key, [ent[1] for ent in sel], [ent[0].dt for ent in sel], n)
+                for ent in sel:
                     ent[2] += n
-            done = [ent for ent in lst if ent[2] >= ent[0].steps]
+            done = [ent for ent in sel if ent[2] >= ent[0].steps]
             for ent in done:
                 lst.remove(ent)
                 req = ent[0]

@@ -29,11 +29,15 @@ def _requests():
     return out
 
 
-def test_served_results_equal_solving_alone():
+@pytest.mark.parametrize("fill", [SV.DEFAULT_FILL_VERTICES, 4000])
+def test_served_results_equal_solving_alone(fill):
+    """With the default fill target every resident grid of a key shares each
+    chunk; with 4000 vertices the chunks take subsets (least remaining work
+    first), so grids pause and resume between chunks."""
     reqs = _requests()
     be = SV.GpuBackend()
     sizes = [be.footprint(r) for r in reqs]
-    srv = SV.Server(be, hbm_budget=int(2.5 * max(sizes)), chunk_steps=5)
+    srv = SV.Server(be, hbm_budget=int(2.5 * max(sizes)), chunk_steps=5, fill_vertices=fill)
     done = srv.run(reqs)
     be.close()
     assert all(r.status == "done" for r in done)

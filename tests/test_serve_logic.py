@@ -1,5 +1,6 @@
 """Host-side logic of the serving loop, on the CPU with a fake backend:
-admission by HBM footprint, continuous batching by (bins, precision),
+admission by HBM footprint, continuous batching by (bins, precision), the
+choice of grids per chunk (least remaining work within a fill target),
 rejection, load failures, cancellation."""
 import numpy as np
 import pytest
@@ -86,6 +87,27 @@ def test_continuous_batching_joins_running_requests():
     srv.run([req(0, 100, 40), req(1, 100, 8, arrival=0.005)])
     together = [rids for _, rids, _ in be.steps if len(rids) == 2]
     assert together, "the later request must join the running batch"
+
+
+def test_least_remaining_work_first_within_the_fill_target():
+    be = FakeBackend()
+    srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock(), fill_vertices=1000)
+    out = srv.run([req(0, 1000, 40), req(1, 100, 8, arrival=0.005), req(2, 300, 12, arrival=0.005)])
+    by = {r.rid: r for r in out}
+    assert all(r.status == "done" and r.y[0] == r.steps for r in out)
+    # the small requests pass the large one, which fills the device alone
+    assert by[1].t_done < by[0].t_done and by[2].t_done < by[0].t_done
+    for _, rids, _ in be.steps:
+        assert 0 not in rids or rids == [0]
+    # the two small ones share launches (400 vertices within the target),
+    # the one with less remaining work first
+    shared = [rids for _, rids, _ in be.steps if len(rids) == 2]
+    assert shared and all(rids == [1, 2] for rids in shared)
+    # without a target every resident grid advances in every chunk
+    be = FakeBackend()
+    srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock(), fill_vertices=None)
+    srv.run([req(0, 1000, 40), req(1, 100, 8, arrival=0.005)])
+    assert any(sorted(rids) == [0, 1] for _, rids, _ in be.steps)
 
 
 def test_rejection_failure_and_cancellation():
