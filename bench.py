@@ -489,21 +489,25 @@ def run_served(args):
         dt = 4.0 / (I.ALPHA_B * nH) / steps
         reqs.append(SV.Request(rid=rid, problem=prob, bins=I.fibonacci_bins(nb), steps=steps,
                                dt=dt, seed=rid, arrival=t))
-    be = SV.GpuBackend()
     free, total = torch.cuda.mem_get_info()
-    srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk)
-    srv.run(reqs)
-    be.close()
-    st_b = srv.stats()
-    res_b = {r.rid: r.y for r in reqs}
-    for r in reqs:
-        r.y = None
+    stats, results = {}, {}
+    # continuous batching with the default fill target, then with every
+    # resident grid in every chunk
+    for name, fill in (("continuous_batching", SV.DEFAULT_FILL_VERTICES),
+                       ("continuous_batching_every_grid", None)):
+        be = SV.GpuBackend()
+        srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk, fill_vertices=fill)
+        srv.run(reqs)
+        be.close()
+        stats[name] = dict(srv.stats(), fill_vertices=fill)
+        results[name] = {r.rid: r.y for r in reqs}
+        for r in reqs:
+            r.y = None
     st_p = SV.serve_one_at_a_time(reqs)
-    same = all(np.array_equal(res_b[r.rid], r.y) for r in reqs)
+    same = all(np.array_equal(res[r.rid], r.y) for res in results.values() for r in reqs)
     print(json.dumps({"mode": "served", "requests": len(reqs), "rate_per_s": args.rate,
                       "n_range": [1e4, args.serve_nmax], "pool_geometries": len(pool_sizes),
-                      "continuous_batching": st_b, "one_at_a_time": st_p,
-                      "identical_results": same}), flush=True)
+                      **stats, "one_at_a_time": st_p, "identical_results": same}), flush=True)
 
 
 def run_clumpy(args):
