@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "48f53a0067d1f78e7dc09eb282b2dec889e4771bd77ad115b10f1b45c152eb52",
-               "bytes_per_launch": 1059.839e6 + 380.245e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "cfd4c69426837bcd53bfa0981ffa986f59eeaf327633aa6831fa9f975148e123",
+               "bytes_per_launch": 1060.374e6 + 380.685e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------

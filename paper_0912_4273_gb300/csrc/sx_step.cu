@@ -886,25 +886,25 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_st
 }
 
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
-// queue, kBatchChunk consecutive tiles at a time; a tile is one grid's 32
-// consecutive vertices.
+// queue, `grab` (1..kBatchChunk) consecutive tiles at a time; a tile is one
+// grid's 32 consecutive vertices.
 constexpr int kBatchChunk = 8;
 template <typename T, int MW, int G>
 __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
     k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
-                 unsigned long long *__restrict__ queue, int slot) {
+                 unsigned long long *__restrict__ queue, int slot, int grab) {
   __shared__ long long s_item;
   const int64_t total = prefix[ngrids];
   int cur_grid = -1;
   for (;;) {
-    // kBatchChunk consecutive tiles per grab: one atomic on the shared
-    // counter serves several tiles
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, (unsigned long long)kBatchChunk);
+    // several consecutive tiles per grab: one atomic on the shared counter
+    // serves them all
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(queue, (unsigned long long)grab);
     __syncthreads();
     const int64_t t0 = s_item;
     __syncthreads();
     if (t0 >= total) break;
-    const int64_t t1 = t0 + kBatchChunk < total ? t0 + kBatchChunk : total;
+    const int64_t t1 = t0 + grab < total ? t0 + grab : total;
     for (int64_t t = t0; t < t1; ++t) {
       int lo = 0, hi = ngrids - 1;  // the grid whose tile range holds t
       while (lo < hi) {
@@ -1017,11 +1017,16 @@ struct BatchLaunch {
                                                   smem);
     int64_t ctas = (int64_t)nsm * (per_sm > 0 ? per_sm : 1);
     if (ctas > total_tiles) ctas = total_tiles;
+    // tiles per grab: up to kBatchChunk while every CTA still gets about
+    // eight grabs, so that a small batch does not end on a few CTAs' long
+    // last grabs
+    const int64_t per = ctas > 0 ? total_tiles / (ctas * 8) : 1;
+    const int grab = per < 1 ? 1 : (per > kBatchChunk ? kBatchChunk : (int)per);
     cudaError_t e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     if (ctas <= 0) return cudaSuccess;
     k_step_batch<T, MW, G><<<(unsigned)ctas, Shape<G>::kThreads, smem, st>>>(d_args, d_prefix, ngrids,
-                                                                              d_queue, slot);
+                                                                              d_queue, slot, grab);
     return cudaGetLastError();
   }
 };

@@ -189,6 +189,28 @@ def test_invalid_grids_are_rejected():
     s.close()
 
 
+def test_batched_large_batch_takes_several_tiles_per_grab():
+    """A batch whose tiles outnumber the persistent CTAs many times over
+    (4 grids of 2^17 interior vertices: about 17k tiles, so several tiles per
+    grab of the work queue) still matches each grid stepped alone."""
+    bins = I.fibonacci_bins(42)
+    probs = [I.cached(I.stromgren_problem, 1 << 17, seed=s) for s in (11, 12, 13, 14)]
+    alone = []
+    for p in probs:
+        s = S.Solver(bins, seed=5).load(p)
+        s.step(DT, 20)
+        alone.append((s.y, s.budget))
+        s.close()
+    sol = [S.Solver(bins, seed=5).load(p) for p in probs]
+    batch = S.Batch(max_grids=4)
+    batch.step(sol, [DT] * 4, 20)
+    for s, (y, b) in zip(sol, alone):
+        assert np.array_equal(s.y, y)
+        assert s.budget == b
+        s.close()
+    batch.close()
+
+
 @pytest.mark.parametrize("variant", [4, 2])
 def test_batched_step_equals_single_grid_steps(variant):
     """Grids stepped together in one persistent launch give bit-identical
