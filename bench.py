@@ -499,7 +499,7 @@ def run_served(args):
         srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk, fill_vertices=fill)
         srv.run(reqs)
         be.close()
-        stats[name] = dict(srv.stats(), fill_vertices=fill)
+        stats[name] = dict(srv.stats(), fill_vertices=fill, max_wait_s=srv.max_wait)
         results[name] = {r.rid: r.y for r in reqs}
         for r in reqs:
             r.y = None

@@ -14,7 +14,9 @@ count, a time step and a number of steps.  The server
     vertices) until their vertices fill the device (``fill_vertices``): small
     grids share a launch, while a grid that fills the device alone is not
     slowed down by the others, which wait resident (shortest remaining work
-    first keeps the median latency low);
+    first keeps the median latency low); requests that have waited longer
+    than ``max_wait_s`` since arrival go first, oldest first, so that large
+    ones are not held back indefinitely;
   * loads newly admitted grids on their own stream while the others step;
   * reads a finished request's neutral fraction and photon budget, releases
     its workspace and records its latency (finish - arrival).
@@ -123,6 +125,8 @@ class GpuBackend:
 # Vertices that keep the step kernel busy: about four waves of its resident
 # 32-vertex tiles (152 SMs x 6 CTAs) on a GB300.
 DEFAULT_FILL_VERTICES = 1 << 17
+# Waiting time after which a request goes ahead of shorter ones.
+DEFAULT_MAX_WAIT_S = 0.5
 
 
 class Server:
@@ -130,7 +134,8 @@ class Server:
 
     def __init__(self, backend, hbm_budget: int, chunk_steps: int = 8, max_grids: int = 256,
                  clock: Callable[[], float] = time.perf_counter, first_fit: bool = True,
-                 fill_vertices: Optional[int] = DEFAULT_FILL_VERTICES):
+                 fill_vertices: Optional[int] = DEFAULT_FILL_VERTICES,
+                 max_wait_s: Optional[float] = DEFAULT_MAX_WAIT_S):
         self.backend = backend
         self.budget = int(hbm_budget)
         self.chunk = int(chunk_steps)
@@ -138,6 +143,7 @@ class Server:
         self.clock = clock
         self.first_fit = first_fit
         self.fill = None if fill_vertices is None else int(fill_vertices)
+        self.max_wait = None if max_wait_s is None else float(max_wait_s)
         self.pending: collections.deque = collections.deque()
         self.active: Dict[tuple, List[list]] = collections.defaultdict(list)  # key -> [[req, solver, done, bytes]]
         self.used = 0
@@ -216,13 +222,21 @@ class Server:
             i += 1
 
     def _select(self, lst: List[list]) -> List[list]:
-        """The grids of one key to advance in this chunk: least remaining
-        work first, packed while their vertices stay within the fill target
-        (at least one grid); every grid when there is no target."""
+        """The grids of one key to advance in this chunk: requests past the
+        maximum wait first (oldest first), then least remaining work, packed
+        while their vertices stay within the fill target (at least one grid);
+        every grid when there is no target."""
         if self.fill is None:
             return list(lst)
-        order = sorted(lst, key=lambda ent: ((ent[0].steps - ent[2]) * ent[0].problem.n,
-                                             ent[0].arrival, ent[0].rid))
+        now = self.now()
+
+        def priority(ent):
+            req = ent[0]
+            if self.max_wait is not None and now - req.arrival > self.max_wait:
+                return (0, req.arrival, req.rid)
+            return (1, (req.steps - ent[2]) * req.problem.n, req.arrival, req.rid)
+
+        order = sorted(lst, key=priority)
         picked, nv = [], 0
         for ent in order:
             if picked and nv + ent[0].problem.n > self.fill:

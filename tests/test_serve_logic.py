@@ -110,6 +110,24 @@ def test_least_remaining_work_first_within_the_fill_target():
     assert any(sorted(rids) == [0, 1] for _, rids, _ in be.steps)
 
 
+def test_a_request_past_the_maximum_wait_goes_first():
+    # request 1 has less remaining work, but once both have waited longer
+    # than max_wait the older one (request 0, lower id at equal arrival) leads
+    def run(max_wait):
+        be = FakeBackend()
+        srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock(), fill_vertices=1000,
+                        max_wait_s=max_wait)
+        out = srv.run([req(0, 1000, 40), req(1, 900, 8)])
+        assert all(r.status == "done" and r.y[0] == r.steps for r in out)
+        assert all(len(rids) == 1 for _, rids, _ in be.steps)  # 1900 > 1000: never together
+        return {r.rid: r.t_done for r in out}
+
+    t = run(None)
+    assert t[1] < t[0]
+    t = run(0.002)
+    assert t[0] < t[1]
+
+
 def test_rejection_failure_and_cancellation():
     be = FakeBackend(fail_rids={1})
     srv = SV.Server(be, hbm_budget=100 * 1000, clock=Clock())
