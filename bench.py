@@ -493,10 +493,13 @@ def run_served(args):
     stats, results = {}, {}
     # continuous batching with the default fill target, then with every
     # resident grid in every chunk
+    max_wait = SV.DEFAULT_MAX_WAIT_S if args.max_wait is None else (
+        None if args.max_wait < 0 else args.max_wait)
     for name, fill in (("continuous_batching", SV.DEFAULT_FILL_VERTICES),
                        ("continuous_batching_every_grid", None)):
         be = SV.GpuBackend()
-        srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk, fill_vertices=fill)
+        srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk, fill_vertices=fill,
+                        max_wait_s=max_wait)
         srv.run(reqs)
         be.close()
         stats[name] = dict(srv.stats(), fill_vertices=fill, max_wait_s=srv.max_wait)
@@ -515,13 +518,15 @@ def run_clumpy(args):
     84 bins, FP32 transport, dt = 0.5 Myr) with the dynamic grid update of
     Sect. 2.1.4 every --update-every steps: vertices with y < 1e-3 whose mean
     edge is shorter than the mesh cell are removed (independent set), the
-    survivors re-triangulated on the host and the state carried over.
-    Reports the step kernel's throughput (per-launch CUDA events) and the
-    cost of each update: marking on the device, re-triangulation on the host
-    (scipy Qhull), loading the new grid with the hand-over on the device."""
+    cavities of the removed vertices re-triangulated on the host and the state
+    carried over.  Reports the step kernel's throughput (per-launch CUDA
+    events) and the cost of each update: marking on the device, local
+    re-triangulation on the host (scipy Qhull per cavity), loading the new
+    grid with the hand-over on the device."""
     import torch
 
     from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import remesh as R
     from paper_0912_4273_gb300 import simplex as S
 
     n = args.clumpy_n
@@ -547,7 +552,7 @@ def run_clumpy(args):
         t0 = time.perf_counter()
         rem = s.mark_removal(1e-3, min_spacing)
         t1 = time.perf_counter()
-        p2, o2n = I.survivor_problem(prob, rem)
+        p2, o2n = R.remove_vertices(prob, rem)
         t2 = time.perf_counter()
         s.apply_update(p2, o2n)
         s.sync()
@@ -592,6 +597,8 @@ def main(argv=None):
     ap.add_argument("--serve-nmax", type=float, default=4e5)
     ap.add_argument("--serve-steps-max", type=int, default=400)
     ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--max-wait", type=float, default=None,
+                    help="served: seconds after which a request goes first (< 0: never)")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args(argv)
     if args.mode == "batched":

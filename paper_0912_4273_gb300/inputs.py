@@ -152,6 +152,7 @@ class Problem:
     src_rate: np.ndarray   # float64 [nsrc], photons / s
     box: float             # cm, side of the interior cube [0, box]^3
     meta: dict
+    simplices: np.ndarray | None = None  # int32 [ntet, 4], the Delaunay tetrahedra
 
     @property
     def n(self) -> int:
@@ -211,7 +212,8 @@ def stromgren_problem(n_interior: int = 8192, box_kpc: float = 13.2, nH: float =
                    src_vertex=np.array([inv[0]], dtype=np.int32),
                    src_rate=np.array([rate], dtype=np.float64), box=L,
                    meta=dict(kind="stromgren", n_interior=n_interior, box_kpc=box_kpc, nH=nH,
-                             rate=rate, seed=seed, corner_source=corner_source))
+                             rate=rate, seed=seed, corner_source=corner_source),
+                   simplices=g.simplices)
 
 
 def cached(recipe, *args, cache_dir: str | None = None, **kw) -> Problem:
@@ -232,13 +234,15 @@ def cached(recipe, *args, cache_dir: str | None = None, **kw) -> Problem:
         return Problem(pos=z["pos"], row_ptr=z["row_ptr"], col=z["col"], nH=z["nH"],
                        volume=z["volume"], flags=z["flags"], src_vertex=z["src_vertex"],
                        src_rate=z["src_rate"], box=float(z["box"]),
-                       meta=json.loads(str(z["meta"])))
+                       meta=json.loads(str(z["meta"])),
+                       simplices=z["simplices"] if "simplices" in z.files else None)
     p = recipe(*args, **kw)
     os.makedirs(cache_dir, exist_ok=True)
     tmp = path + f".tmp{os.getpid()}.npz"
+    extra = {} if p.simplices is None else {"simplices": p.simplices}
     np.savez(tmp, pos=p.pos, row_ptr=p.row_ptr, col=p.col, nH=p.nH, volume=p.volume,
              flags=p.flags, src_vertex=p.src_vertex, src_rate=p.src_rate, box=p.box,
-             meta=json.dumps(p.meta))
+             meta=json.dumps(p.meta), **extra)
     os.replace(tmp, path)
     return p
 
@@ -302,7 +306,8 @@ def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13
     return Problem(pos=allp, row_ptr=g.row_ptr, col=g.col, nH=nh[order], volume=g.volume,
                    flags=flags[order], src_vertex=inv[:nsrc].astype(np.int32), src_rate=rates,
                    box=L, meta=dict(kind="clumpy", n_points=n_points, mesh=mesh, box_kpc=box_kpc,
-                                    nbar=nbar, sigma_ln=sigma_ln, nsrc=nsrc, seed=seed))
+                                    nbar=nbar, sigma_ln=sigma_ln, nsrc=nsrc, seed=seed),
+                   simplices=g.simplices)
 
 
 def survivor_problem(problem: Problem, removed) -> tuple:
@@ -320,7 +325,8 @@ def survivor_problem(problem: Problem, removed) -> tuple:
     p = Problem(pos=pts, row_ptr=g.row_ptr, col=g.col, nH=problem.nH[keep].copy(),
                 volume=g.volume, flags=problem.flags[keep].copy(),
                 src_vertex=new_of_old[problem.src_vertex].astype(np.int32),
-                src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta))
+                src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta),
+                simplices=g.simplices)
     return p, keep.astype(np.int32)
 
 
@@ -336,4 +342,4 @@ def point_process_problem(points: np.ndarray, nH, sink_mask=None, sources=()) ->
     sr = np.array([r for _, r in sources], dtype=np.float64)
     return Problem(pos=pts, row_ptr=g.row_ptr, col=g.col, nH=nh, volume=g.volume, flags=flags,
                    src_vertex=sv, src_rate=sr, box=float(np.ptp(pts, axis=0).max()),
-                   meta=dict(kind="points"))
+                   meta=dict(kind="points"), simplices=g.simplices)

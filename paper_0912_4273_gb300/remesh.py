@@ -1,0 +1,140 @@
+"""Vertex removal from a Delaunay tetrahedralisation by local re-triangulation:
+the host step of the dynamic grid update (Sect. 2.1.4).
+
+Removing a vertex v leaves a cavity, the union of the tetrahedra around v.
+Every tetrahedron outside the cavity keeps its empty circumsphere, so it stays
+in the Delaunay tetrahedralisation of the remaining points, and so do the
+faces on the cavity's boundary.  The tetrahedra that fill the cavity have
+their vertices among v's neighbours and empty circumspheres, so (for points in
+general position) they are exactly the tetrahedra of the Delaunay
+tetrahedralisation of v's neighbours whose interiors lie in the cavity.
+Vertices removed together form an independent set (no two adjacent), so no
+tetrahedron holds two of them, the cavities have disjoint interiors and each
+is filled on its own.
+
+The paper's QHull cannot delete points and rebuilds the whole grid after a
+removal; here only the cavities are re-triangulated (QHull on each vertex's
+neighbours) and the graph, the cell volumes and the tetrahedra are patched.
+Each cavity's new tetrahedra must fill its volume; a vertex on the convex
+hull (whose removal changes the hull) fails that check, and the grid is then
+rebuilt from scratch.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs as I
+
+
+def _in_any_tet(p: np.ndarray, tets: np.ndarray, eps: float = 1e-9) -> np.ndarray:
+    """Whether each point p[k] (K x 3) lies in one of the tetrahedra
+    (S x 4 x 3), by barycentric coordinates."""
+    a = tets[:, 0]
+    m = np.stack([tets[:, 1] - a, tets[:, 2] - a, tets[:, 3] - a], axis=-1)  # S x 3 x 3
+    minv = np.linalg.inv(m)
+    lam = np.einsum("sij,ksj->ksi", minv, p[:, None, :] - a[None, :, :])     # K x S x 3
+    ok = (lam >= -eps).all(axis=-1) & (lam.sum(axis=-1) <= 1.0 + eps)
+    return ok.any(axis=1)
+
+
+def _fill_cavity(pos: np.ndarray, v: int, star: np.ndarray):
+    """Tetrahedra (old vertex ids) that fill the cavity of v, whose star is
+    `star` (tetrahedra holding v), or None if they do not fill it."""
+    from scipy.spatial import Delaunay
+
+    link = np.unique(star[star != v])
+    if len(link) < 4:
+        return None
+    origin = pos[v]
+    p = pos[link] - origin  # coordinates relative to v: better conditioned
+    try:
+        cand = Delaunay(p).simplices
+    except Exception:  # QHull refuses (e.g. a flat neighbourhood)
+        return None
+    inside = _in_any_tet(p[cand].mean(axis=1), pos[star] - origin)
+    new = link[cand[inside]]
+    v_old = I.tet_volumes(pos, star).sum()
+    v_new = I.tet_volumes(pos, new).sum()
+    if not abs(v_new - v_old) <= 1e-9 * v_old:
+        return None
+    return new
+
+
+def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True) -> tuple:
+    """The grid without the `removed` vertices (an independent set of the
+    graph): survivors in their old order, their Delaunay graph, cell volumes
+    (1/4 of the incident tetrahedra), media, flags, sources and tetrahedra.
+    Returns (problem, old_of_new), as a full rebuild of the survivors would.
+
+    Needs the grid's tetrahedra (``problem.simplices``); a grid without them,
+    or a cavity that cannot be filled locally, is rebuilt by QHull (or, with
+    ``allow_rebuild=False``, raises RuntimeError)."""
+
+    def rebuild(why):
+        if not allow_rebuild:
+            raise RuntimeError(why)
+        return I.survivor_problem(problem, np.flatnonzero(rem))
+
+    n = problem.n
+    rem = np.zeros(n, dtype=bool)
+    rem[np.asarray(removed, dtype=np.int64)] = True
+    if problem.simplices is None:
+        return rebuild("the grid has no tetrahedra")
+    if np.any(rem[problem.src_vertex]):
+        raise ValueError("sources are never removed")
+    simp = np.asarray(problem.simplices)
+    hit = rem[simp]
+    cnt = hit.sum(axis=1)
+    if np.any(cnt > 1):
+        raise ValueError("removed vertices must not be adjacent")
+    star_ids = np.flatnonzero(cnt == 1)
+    st = simp[star_ids].astype(np.int64)
+    owner = st[hit[star_ids]]
+    order = np.argsort(owner, kind="stable")
+    st, owner = st[order], owner[order]
+    cuts = np.flatnonzero(np.diff(owner)) + 1
+    pos = problem.pos
+    new_tets = []
+    for grp, v in zip(np.split(st, cuts), owner[np.r_[0, cuts]] if len(owner) else []):
+        t = _fill_cavity(pos, int(v), grp)
+        if t is None:
+            return rebuild(f"the cavity of vertex {int(v)} cannot be filled locally")
+        new_tets.append(t)
+    new = np.concatenate(new_tets) if new_tets else np.zeros((0, 4), dtype=np.int64)
+
+    # the graph: old edges without the removed vertices, plus the cavity
+    # tetrahedra's edges not already present (keys src * n + dst, sorted)
+    deg = np.diff(problem.row_ptr)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = problem.col.astype(np.int64)
+    keep_e = ~(rem[src] | rem[dst])
+    key = src[keep_e] * n + dst[keep_e]
+    pairs = np.concatenate([new[:, [a, b]] for a, b in
+                            ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
+    add = np.unique(np.concatenate([pairs[:, 0] * n + pairs[:, 1], pairs[:, 1] * n + pairs[:, 0]]))
+    at = np.searchsorted(key, add)
+    present = (at < len(key)) & (key[np.minimum(at, len(key) - 1)] == add)
+    key = np.insert(key, at[~present], add[~present])
+
+    keep = np.flatnonzero(~rem)
+    new_of_old = np.full(n, -1, dtype=np.int64)
+    new_of_old[keep] = np.arange(len(keep))
+    n2 = len(keep)
+    src2 = new_of_old[key // n]
+    col2 = new_of_old[key % n].astype(np.int32)
+    row_ptr2 = np.zeros(n2 + 1, dtype=np.int64)
+    np.cumsum(np.bincount(src2, minlength=n2), out=row_ptr2[1:])
+
+    # cell volumes: the cavity's old tetrahedra leave their vertices, the new
+    # ones join theirs, a quarter each
+    vol = problem.volume.astype(np.float64).copy()
+    np.add.at(vol, st.ravel(), -np.repeat(I.tet_volumes(pos, st) * 0.25, 4))
+    np.add.at(vol, new.ravel(), np.repeat(I.tet_volumes(pos, new) * 0.25, 4))
+
+    simp2 = np.concatenate([simp[cnt == 0].astype(np.int64), new])
+    p = I.Problem(pos=np.ascontiguousarray(pos[keep]), row_ptr=row_ptr2, col=col2,
+                  nH=problem.nH[keep].copy(), volume=vol[keep], flags=problem.flags[keep].copy(),
+                  src_vertex=new_of_old[problem.src_vertex].astype(np.int32),
+                  src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta),
+                  simplices=new_of_old[simp2].astype(np.int32))
+    return p, keep.astype(np.int32)

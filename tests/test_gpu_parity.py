@@ -18,6 +18,7 @@ import pytest
 
 import oracle as O
 from paper_0912_4273_gb300 import inputs as I
+from paper_0912_4273_gb300 import remesh as R
 
 pytestmark = pytest.mark.gpu
 
@@ -286,9 +287,13 @@ def test_dynamic_update_parity(precision, ytol, btol):
     rem_gpu = s.mark_removal(1e-2, spacing)
     assert len(rem) > 10
     assert np.array_equal(rem, rem_gpu)
+    # the oracle takes a full QHull rebuild of the survivors, the device the
+    # local re-triangulation of the cavities: the same grid
     p2, o2n = I.survivor_problem(prob, rem)
     ref2 = ref.rebuild(rem, p2, o2n, params=O.Params(nbins=42, seed=11, kappa=kappa))
-    s.apply_update(p2, o2n)
+    p2l, o2nl = R.remove_vertices(prob, rem, allow_rebuild=False)
+    assert np.array_equal(o2nl, o2n) and np.array_equal(p2l.col, p2.col)
+    s.apply_update(p2l, o2nl)
     assert s.info["step"] == 80 and s.n == p2.n
     assert budget_err(s.budget, ref2.budget) <= btol
     assert np.abs(s.photons() - ref2.I.sum(axis=1)).max() <= btol * ref2.budget["emitted"]
