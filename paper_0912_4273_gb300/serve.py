@@ -126,7 +126,7 @@ class GpuBackend:
 # 32-vertex tiles (152 SMs x 6 CTAs) on a GB300.
 DEFAULT_FILL_VERTICES = 1 << 17
 # Waiting time after which a request goes ahead of shorter ones.
-DEFAULT_MAX_WAIT_S = 0.5
+DEFAULT_MAX_WAIT_S = 1.0
 
 
 class Server:
