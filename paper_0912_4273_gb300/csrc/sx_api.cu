@@ -199,6 +199,18 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   return SX_OK;
 }
 
+// The scale and carries that turn the tiles' sums into the reported budget.
+static sx::BudgetScale budget_scale(const sx_ctx *c) {
+  sx::BudgetScale sc;
+  sc.emitted = c->emitted;
+  sc.punit = c->g.punit;
+  sc.carry_abs = c->carry_abs;
+  sc.carry_esc = c->carry_esc;
+  sc.carry_fly = c->carry_fly;
+  sc.fly_mode = c->fresh_update ? 1 : (c->step > 0 ? 2 : 0);
+  return sc;
+}
+
 extern "C" {
 
 void sx_config_default(sx_config *cfg) {
@@ -362,7 +374,7 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
                                   reinterpret_cast<int32_t *>(go.s_out), go.P[freeb], st));
   // budget so far
   double tmp[3] = {0, 0, 0};
-  SX_CUDA(c, sx::launch_budget(go, st));
+  SX_CUDA(c, sx::launch_budget(go, budget_scale(c), st));
   SX_CUDA(c, cudaMemcpyAsync(tmp, go.budget_dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
   SX_CUDA(c, cudaStreamSynchronize(st));
   // the new grid
@@ -451,6 +463,42 @@ int sx_add_source(sx_ctx *c, int32_t vertex, double rate) {
   return SX_OK;
 }
 
+}  // extern "C"
+
+// Steps with direct launches, the rotation tables of up to kRotAhead steps
+// at a time; with `budgets`, after every step the budget is reduced and copied
+// to budgets[k] without waiting.
+static int step_direct(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets) {
+  for (int32_t k = 0; k < nsteps;) {
+    const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
+    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, m, 0, dt, c->stream));
+    for (int j = 0; j < m; ++j, ++k) {
+      if (c->profiling) {
+        if (c->events_used == c->events.size()) {
+          cudaEvent_t a, b;
+          SX_CUDA(c, cudaEventCreate(&a));
+          SX_CUDA(c, cudaEventCreate(&b));
+          c->events.emplace_back(a, b);
+        }
+        SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
+      }
+      SX_CUDA(c, sx::launch_step(c->g, j, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
+                                 c->stream));
+      if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
+      for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
+      c->step++;
+      if (budgets) {
+        SX_CUDA(c, sx::launch_budget(c->g, budget_scale(c), c->stream));
+        SX_CUDA(c, cudaMemcpyAsync(budgets + k, c->g.budget_dev + 4, sizeof(sx_budget),
+                                   cudaMemcpyDeviceToHost, c->stream));
+      }
+    }
+  }
+  return SX_OK;
+}
+
+extern "C" {
+
 int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
@@ -492,27 +540,18 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
     }
   }
   // the rest: the tables of up to kRotAhead steps, then their step launches
-  for (int32_t k = k0; k < nsteps;) {
-    const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
-    SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, m, 0, dt, c->stream));
-    for (int j = 0; j < m; ++j, ++k) {
-      if (c->profiling) {
-        if (c->events_used == c->events.size()) {
-          cudaEvent_t a, b;
-          SX_CUDA(c, cudaEventCreate(&a));
-          SX_CUDA(c, cudaEventCreate(&b));
-          c->events.emplace_back(a, b);
-        }
-        SX_CUDA(c, cudaEventRecord(c->events[c->events_used].first, c->stream));
-      }
-      SX_CUDA(c, sx::launch_step(c->g, j, dt, c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
-                                 c->stream));
-      if (c->profiling) SX_CUDA(c, cudaEventRecord(c->events[c->events_used++].second, c->stream));
-      for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
-      c->step++;
-    }
-  }
-  return SX_OK;
+  return step_direct(c, dt, nsteps - k0, nullptr);
+}
+
+int sx_step_budgets(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
+  if (nsteps > 0 && !budgets) return fail(c, SX_EINVAL, "budgets is NULL");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  ensure_punit(c, dt);
+  if (nsteps > 0) c->fresh_update = false;
+  return step_direct(c, dt, nsteps, budgets);
 }
 
 int sx_sync(sx_ctx *c) {
@@ -752,15 +791,10 @@ int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
-  if (b) {
-    double tmp[4] = {0, 0, 0, 0};
-    SX_CUDA(c, sx::launch_budget(c->g, c->stream));
-    SX_CUDA(c, cudaMemcpyAsync(tmp, c->g.budget_dev, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+  if (b) {  // the same device arithmetic as the reads of sx_step_budgets
+    SX_CUDA(c, sx::launch_budget(c->g, budget_scale(c), c->stream));
+    SX_CUDA(c, cudaMemcpyAsync(b, c->g.budget_dev + 4, sizeof(sx_budget), cudaMemcpyDeviceToHost, c->stream));
     SX_CUDA(c, cudaStreamSynchronize(c->stream));
-    b->emitted = c->emitted;
-    b->absorbed = tmp[0] * c->g.punit + c->carry_abs;
-    b->escaped = tmp[1] * c->g.punit + c->carry_esc;
-    b->in_flight = c->fresh_update ? c->carry_fly : (c->step > 0 ? tmp[2] * c->g.punit : 0.0);
   }
   if (per_vertex) {
     if (c->fresh_update) {

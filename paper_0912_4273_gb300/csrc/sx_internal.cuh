@@ -215,7 +215,7 @@ struct DevGrid {
   double *kappa_part;   // nblocks_kappa*2
   int64_t nblocks_kappa;
   double *kappa_dev;    // 1
-  double *budget_dev;   // 4
+  double *budget_dev;   // 8: the sums, then the reported budget (k_budget)
   // load-time scratch
   int64_t *s_row_ptr;
   int32_t *s_col;       // nnz neighbour ids as loaded; kept: the step kernel reads the senders here
@@ -257,7 +257,14 @@ cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, int count, c
 cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int slot, int device, cudaStream_t st);
-cudaError_t launch_budget(DevGrid &g, cudaStream_t st);
+// The budget as reported: sums x punit plus the carries of earlier grids;
+// the photons in flight are 0 before the first step (fly_mode 0), the carry
+// right after a grid update (1), else the sum (2).
+struct BudgetScale {
+  double emitted, punit, carry_abs, carry_esc, carry_fly;
+  int fly_mode;
+};
+cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st);
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
 // dynamic grid update (sx_update.cu)
 cudaError_t launch_mark(DevGrid &g, double y_thresh, double min_spacing, uint8_t *cand,

@@ -43,7 +43,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
   L.off_diag = take(sizeof(unsigned long long) * kDiagCount);
   L.off_kpart = take(sizeof(double) * 2 * L.nblocks_kappa);
   L.off_kappa = take(sizeof(double));
-  L.off_budget = take(sizeof(double) * 4);
+  L.off_budget = take(sizeof(double) * 8);
   L.off_s_row_ptr = take(sizeof(int64_t) * (n + 1));
   L.off_s_col = take(sizeof(int32_t) * nnz);
   L.off_s_nH = take(sizeof(double) * n);

@@ -1042,7 +1042,11 @@ cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, 
 // ----------------------------------------------------------------------------
 // Budget: sum of the per-CTA partials in a fixed order.
 // ----------------------------------------------------------------------------
-__global__ void k_budget(int64_t nb, const double *__restrict__ part, double *__restrict__ out) {
+// out[0..2]: the sums of the tiles' partials (absorbed, escaped, in flight,
+// in stored units); out[4..7]: the budget as the C ABI reports it
+// (emitted, absorbed, escaped, in flight in photons, carries included).
+__global__ void k_budget(int64_t nb, const double *__restrict__ part, double *__restrict__ out,
+                         BudgetScale sc) {
   __shared__ double s[3][256];
   double a0 = 0.0, a1 = 0.0, a2 = 0.0;
   for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
@@ -1063,11 +1067,15 @@ __global__ void k_budget(int64_t nb, const double *__restrict__ part, double *__
     out[0] = s[0][0];
     out[1] = s[1][0];
     out[2] = s[2][0];
+    out[4] = sc.emitted;
+    out[5] = __dadd_rn(__dmul_rn(s[0][0], sc.punit), sc.carry_abs);
+    out[6] = __dadd_rn(__dmul_rn(s[1][0], sc.punit), sc.carry_esc);
+    out[7] = sc.fly_mode == 2 ? __dmul_rn(s[2][0], sc.punit) : (sc.fly_mode == 1 ? sc.carry_fly : 0.0);
   }
 }
 
-cudaError_t launch_budget(DevGrid &g, cudaStream_t st) {
-  k_budget<<<1, 256, 0, st>>>(g.nblocks, g.partials, g.budget_dev);
+cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st) {
+  k_budget<<<1, 256, 0, st>>>(g.nblocks, g.partials, g.budget_dev, sc);
   return cudaGetLastError();
 }
 

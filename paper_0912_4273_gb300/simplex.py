@@ -79,6 +79,7 @@ _SIGS = [
                                _P(C.c_double), C.c_void_p, C.c_int64]),
     ("sx_add_source", C.c_int, [C.c_void_p, C.c_int32, C.c_double]),
     ("sx_step", C.c_int, [C.c_void_p, C.c_double, C.c_int32]),
+    ("sx_step_budgets", C.c_int, [C.c_void_p, C.c_double, C.c_int32, _P(sx_budget)]),
     ("sx_sync", C.c_int, [C.c_void_p]),
     ("sx_read_neutral_fraction", C.c_int, [C.c_void_p, _P(C.c_double)]),
     ("sx_read_photons", C.c_int, [C.c_void_p, _P(C.c_double), _P(sx_budget)]),
@@ -188,6 +189,15 @@ def sx_add_source(ctx, vertex: int, photons_per_s: float):
 
 def sx_step(ctx, dt_s: float, nsteps: int):
     _check(ctx, lib().sx_step(ctx, float(dt_s), int(nsteps)))
+
+
+def sx_step_budgets(ctx, dt_s: float, nsteps: int, budgets: np.ndarray):
+    """budgets: float64 array of nsteps x 4 (emitted, absorbed, escaped, in
+    flight), filled once the stream has reached the steps (sx_sync)."""
+    if budgets.dtype != np.float64 or budgets.shape != (nsteps, 4) or not budgets.flags.c_contiguous:
+        raise ValueError("budgets must be a C-contiguous float64 array of nsteps x 4")
+    _check(ctx, lib().sx_step_budgets(ctx, float(dt_s), int(nsteps),
+                                      budgets.ctypes.data_as(C.POINTER(sx_budget))))
 
 
 def sx_sync(ctx):
@@ -438,6 +448,16 @@ class Solver:
 
     def step(self, dt: float, nsteps: int = 1):
         sx_step(self.ctx, dt, nsteps)
+
+    def step_budgets(self, dt: float, nsteps: int, out: np.ndarray = None) -> np.ndarray:
+        """Steps, each followed by a queued read of the photon budget into row
+        k of `out` (nsteps x 4 float64: emitted, absorbed, escaped, in
+        flight; page-locked memory keeps the copies asynchronous).  The rows
+        are filled once the stream reaches them (``sync``)."""
+        if out is None:
+            out = np.empty((nsteps, 4), dtype=np.float64)
+        sx_step_budgets(self.ctx, dt, nsteps, out)
+        return out
 
     def sync(self):
         sx_sync(self.ctx)

@@ -76,7 +76,8 @@ def test_argument_errors_without_gpu(libpath):
 
 
 def test_variant_and_autotune_argument_errors(libpath):
-    """The launch-variant calls reject a missing context before touching a GPU."""
+    """The launch-variant, autotune and budget-stepping calls reject a missing
+    context before touching a GPU."""
     from paper_0912_4273_gb300 import simplex as S
 
     L = S.lib()
@@ -85,6 +86,7 @@ def test_variant_and_autotune_argument_errors(libpath):
     assert L.sx_get_variant(None, ctypes.byref(v)) == S.SX_EINVAL
     r = S.sx_tune_result()
     assert L.sx_autotune(None, 1.0, 1, None, 0, ctypes.byref(r)) == S.SX_EINVAL
+    assert L.sx_step_budgets(None, 1.0, 1, None) == S.SX_EINVAL
 
 
 def test_checkpoint_argument_errors(libpath, tmp_path):

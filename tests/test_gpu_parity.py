@@ -108,6 +108,30 @@ def test_deterministic_and_chunk_invariant(c0):
         assert b == out[0][1]
 
 
+def test_step_budgets_match_synchronous_reads(c0):
+    """sx_step_budgets queues a budget read behind every step: the rows equal
+    the budgets read synchronously after single steps, and the state equals
+    sx_step's."""
+    prob, bins, _, _ = c0
+    a = S.Solver(bins, seed=0).load(prob)
+    rows = []
+    for _ in range(20):
+        a.step(DT, 1)
+        b = a.budget
+        rows.append([b["emitted"], b["absorbed"], b["escaped"], b["in_flight"]])
+    c = S.Solver(bins, seed=0).load(prob)
+    out = torch.zeros((20, 4), dtype=torch.float64).pin_memory().numpy()
+    c.step_budgets(DT, 20, out)
+    c.sync()
+    assert np.array_equal(np.array(rows), out)
+    assert np.array_equal(a.y, c.y)
+    assert a.budget == c.budget
+    with pytest.raises(ValueError):
+        c.step_budgets(DT, 3, np.zeros((2, 4)))
+    a.close()
+    c.close()
+
+
 def test_transparent_medium_conserves_photons():
     p = np.random.default_rng(4).random((6000, 3))
     sink = np.any((p < 0.05) | (p > 0.95), axis=1)
