@@ -84,6 +84,8 @@ def lib():
             L.ox_mark_removal.restype = i64
             L.ox_hand_over.argtypes = [C.c_void_p, i64, P(i32), P(d)]
             L.ox_set_step.argtypes = [C.c_void_p, i64]
+            L.ox_get_inflight.argtypes = [C.c_void_p, P(d)]
+            L.ox_get_ballistic.argtypes = [C.c_void_p, P(u8), P(i64), P(u8)]
             L.ox_set_budget.argtypes = [C.c_void_p, P(d)]
             L.dl_triangulate.argtypes = [i64, P(d), P(P(i32))]
             L.dl_triangulate.restype = i64
@@ -169,16 +171,20 @@ class Params:
     chem_frac: float = 0.5
     chem_tol: float = 1e-5
     chem_max_sub: int = 1000
+    transport: int = 0          # 0 direction conserving, 1 ballistic, 2 combined
+    tau_switch: float = 1.0     # combined: ballistic where y tau_max >= tau_switch (Sect. 5.1.3)
 
 
 class _CParams(C.Structure):
     _fields_ = [("nbins", C.c_int), ("seed", C.c_uint64), ("sigma", C.c_double),
                 ("alpha_B", C.c_double), ("kappa", C.c_double), ("chem_frac", C.c_double),
-                ("chem_tol", C.c_double), ("chem_max_sub", C.c_int)]
+                ("chem_tol", C.c_double), ("chem_max_sub", C.c_int), ("transport", C.c_int),
+                ("tau_switch", C.c_double)]
 
 
 class OracleSim:
-    """FP64 SimpleX2 DCT simulation of one grid on the CPU."""
+    """FP64 SimpleX2 simulation of one grid on the CPU: direction-conserving,
+    ballistic or combined transport (``Params.transport``)."""
 
     def __init__(self, problem, params: Params, bins: np.ndarray, y0=None):
         L = lib()
@@ -197,7 +203,8 @@ class OracleSim:
         assert self._keep["bins"].shape == (params.nbins, 3)
         k = self._keep
         cp = _CParams(params.nbins, params.seed, params.sigma, params.alpha_B, params.kappa,
-                      params.chem_frac, params.chem_tol, params.chem_max_sub)
+                      params.chem_frac, params.chem_tol, params.chem_max_sub, params.transport,
+                      params.tau_switch)
         y0p = None
         if y0 is not None:
             k["y0"] = np.ascontiguousarray(y0, dtype=np.float64)
@@ -239,6 +246,24 @@ class OracleSim:
     def I(self, v):
         a = np.ascontiguousarray(v, dtype=np.float64)
         lib().ox_set_I(self.h, _p(a, C.c_double))
+
+    def photons(self) -> np.ndarray:
+        """Photons in flight towards every vertex (any transport)."""
+        out = np.zeros(self.n)
+        lib().ox_get_inflight(self.h, _p(out, C.c_double))
+        return out
+
+    def ballistic(self):
+        """(stb nnz x 4, twin nnz, thick n) of ballistic or combined transport:
+        the ballistic straight sets, the reverse-edge index and the modes of
+        the last step."""
+        nnz = int(self._keep["rp"][-1])
+        stb = np.zeros((max(nnz, 1), 4), dtype=np.uint8)
+        twin = np.zeros(max(nnz, 1), dtype=np.int64)
+        thick = np.zeros(self.n, dtype=np.uint8)
+        lib().ox_get_ballistic(self.h, _p(stb, C.c_uint8), _p(twin, C.c_int64),
+                               _p(thick, C.c_uint8))
+        return stb[:nnz], twin[:nnz], thick
 
     @property
     def budget(self) -> dict:
@@ -284,6 +309,8 @@ class OracleSim:
         """The state after the dynamic update on the re-triangulated survivors:
         photons of removed vertices handed over, neutral fractions, step count,
         budget and sources carried to the new grid (a new OracleSim)."""
+        if self.p.transport != 0:
+            raise NotImplementedError("the dynamic update carries bins: direction conserving only")
         removed = np.ascontiguousarray(removed, dtype=np.int32)
         I = np.ascontiguousarray(self.I)
         lib().ox_hand_over(self.h, len(removed), _p(removed, C.c_int32), _p(I, C.c_double))

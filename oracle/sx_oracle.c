@@ -20,6 +20,13 @@
  *                conserving; once equilibrium is reached the last subcycle's
  *                values are kept for the rest of the step.
  *   Sect. 4.6    photons move one Delaunay edge per radiative-transfer step.
+ *   Sect. 2.2.2  ballistic transport: photons that came in along an edge go
+ *                on, in d = 3 equal parts, to the most straightforward
+ *                neighbours with respect to that incoming direction (none
+ *                beyond 90 deg); a source sends to all its neighbours.
+ *   Sect. 2.2.4  combined transport: ballistic where the optical depth is
+ *                high, direction conserving where it is low; photons change
+ *                representation (bins <-> edges) on arrival.
  *
  * Readings of points the paper leaves open (all listed in the design notes):
  *   - association: bin b of vertex i goes with the edge k maximising the dot
@@ -36,7 +43,15 @@
  *     over interior vertices and unrotated bins; dL_i = kappa * mean edge length;
  *   - subcycle length h = min(t_left, f_c / (Gamma + R)); equilibrium when
  *     |dy| <= tol * y after a subcycle; cap max_sub subcycles;
- *   - sinks (boundary shell) absorb everything into "escaped".
+ *   - sinks (boundary shell) absorb everything into "escaped";
+ *   - ballistic straight set of the in-edge from u: the <= 3 slots k with the
+ *     largest positive quantised dot q_ik . (-q_iu), ties -> lowest slot;
+ *   - combined: a vertex is ballistic in a step when y tau_max >= tau_switch
+ *     with y its neutral fraction at the start of the step; it keeps its
+ *     photons per in-edge (bins arriving along an edge summed into it), a
+ *     direction-conserving vertex keeps bins (a packet arriving along an edge
+ *     goes to the bin closest to the direction it travelled);
+ *   - a ballistic source sends its photons in equal parts along all edges.
  *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
  * (-ffp-contract=off keeps every a*b+c a separate multiply and add so that the
@@ -317,6 +332,72 @@ double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, d
 }
 
 /* ------------------------------------------------------------------------ */
+/* Ballistic transport (Sect. 2.2.2): photons that came in along edge u -> i */
+/* go on in p = d = 3 equal parts to the most straightforward neighbours of  */
+/* i with respect to the direction they travelled (the edge i -> u           */
+/* reversed); neighbours beyond 90 degrees are left out.                     */
+/*   stb[e]: for the in-edge of slot j of vertex i, the <= 3 slots k with    */
+/*   the largest positive quantised dot q_ik . (-q_ij), ties -> lowest slot; */
+/*   twin[e]: the index of edge i -> k in k's row (rows ascending).          */
+/* ------------------------------------------------------------------------ */
+void ox_ballistic_tables(int64_t n, const int64_t *row_ptr, const int32_t *col,
+                         const int32_t *qedge, uint8_t *stb /* nnz*4 */, int64_t *twin /* nnz */) {
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
+        for (int64_t e = r0; e < r1; ++e) {
+            int32_t back[3] = {-qedge[3 * e], -qedge[3 * e + 1], -qedge[3 * e + 2]};
+            int64_t best[OX_MAX_STRAIGHT];
+            int slot[OX_MAX_STRAIGHT];
+            int cnt = 0;
+            for (int64_t e2 = r0; e2 < r1; ++e2) {
+                int64_t d = idot(back, qedge + 3 * e2);
+                if (d <= 0) continue;
+                /* keep the first three in (dot descending, slot ascending) order */
+                int at = cnt;
+                while (at > 0 && d > best[at - 1]) at--;
+                if (at >= OX_MAX_STRAIGHT) continue;
+                int last = cnt < OX_MAX_STRAIGHT ? cnt : OX_MAX_STRAIGHT - 1;
+                for (int m = last; m > at; --m) {
+                    best[m] = best[m - 1];
+                    slot[m] = slot[m - 1];
+                }
+                best[at] = d;
+                slot[at] = (int)(e2 - r0);
+                if (cnt < OX_MAX_STRAIGHT) cnt++;
+            }
+            for (int m = 0; m < OX_MAX_STRAIGHT; ++m) stb[4 * e + m] = (m < cnt) ? (uint8_t)slot[m] : 0xFF;
+            stb[4 * e + 3] = (uint8_t)cnt;
+            int64_t k = col[e], lo = row_ptr[k], hi = row_ptr[k + 1] - 1, t = -1;
+            while (lo <= hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (col[mid] == (int32_t)i) {
+                    t = mid;
+                    break;
+                }
+                if (col[mid] < (int32_t)i) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            twin[e] = t;
+        }
+    }
+}
+
+/* The bin whose rotated direction is closest to direction dir:
+   argmax_b q_b . dir, ties -> lowest b. */
+static int closest_bin(const int32_t *qb, int nbins, const int32_t *dir) {
+    int best = 0;
+    int64_t bestd = idot(qb, dir);
+    for (int b = 1; b < nbins; ++b) {
+        int64_t d = idot(qb + 3 * b, dir);
+        if (d > bestd) {
+            best = b;
+            bestd = d;
+        }
+    }
+    return best;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Simulation state                                                          */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -342,6 +423,16 @@ typedef struct {
     double kappa, fc, tol;
     int max_sub;
     int64_t total_sub, total_capped;
+    /* ballistic and combined transport (Sect. 2.2.2, 2.2.4) */
+    int transport;
+    double tau_switch;
+    uint8_t *stb;           /* nnz*4: ballistic straight set of every in-edge */
+    int64_t *twin;          /* nnz: index of edge i->k in k's row */
+    double *Pb, *Pbn;       /* nnz*nbins: bin packets arrived along each in-edge */
+    double *Pe, *Pen;       /* nnz: edge packets arrived along each in-edge */
+    double *Ev;             /* nnz: a thick vertex's photons per in-edge */
+    double *S;              /* n: a thick source's photons of this step */
+    uint8_t *thick;         /* n: the vertex's mode in the current step */
 } ox_sim;
 
 typedef struct {
@@ -349,6 +440,8 @@ typedef struct {
     uint64_t seed;
     double sigma, alpha_B, kappa, chem_frac, chem_tol;
     int chem_max_sub;
+    int transport;      /* 0 direction conserving, 1 ballistic, 2 combined */
+    double tau_switch;  /* combined: ballistic where y tau_max >= tau_switch */
 } ox_params;
 
 ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_t *row_ptr,
@@ -391,6 +484,21 @@ ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_
     s->fc = p->chem_frac;
     s->tol = p->chem_tol;
     s->max_sub = p->chem_max_sub;
+    s->transport = p->transport;
+    s->tau_switch = p->tau_switch;
+    if (s->transport != 0) {
+        size_t m = nnz ? (size_t)nnz : 1;
+        s->stb = (uint8_t *)malloc(4 * m);
+        s->twin = (int64_t *)malloc(sizeof(int64_t) * m);
+        ox_ballistic_tables(n, s->row_ptr, s->col, s->qedge, s->stb, s->twin);
+        s->Pb = (double *)calloc(m * (size_t)p->nbins, sizeof(double));
+        s->Pbn = (double *)calloc(m * (size_t)p->nbins, sizeof(double));
+        s->Pe = (double *)calloc(m, sizeof(double));
+        s->Pen = (double *)calloc(m, sizeof(double));
+        s->Ev = (double *)calloc(m, sizeof(double));
+        s->S = (double *)calloc((size_t)n + 1, sizeof(double));
+        s->thick = (uint8_t *)calloc((size_t)n + 1, 1);
+    }
     return s;
 }
 
@@ -399,6 +507,8 @@ void ox_destroy(ox_sim *s) {
     free(s->row_ptr); free(s->col); free(s->flags); free(s->bins); free(s->qedge);
     free(s->straight); free(s->mean_len); free(s->A); free(s->tau_max); free(s->R0);
     free(s->y); free(s->I); free(s->Inew); free(s->src_v); free(s->src_rate);
+    free(s->stb); free(s->twin); free(s->Pb); free(s->Pbn); free(s->Pe); free(s->Pen);
+    free(s->Ev); free(s->S); free(s->thick);
     free(s);
 }
 
@@ -494,8 +604,196 @@ static void ox_one_step(ox_sim *s, double dt) {
     free(qb);
 }
 
+/* One step of ballistic or combined transport (Sect. 2.2.2, 2.2.4).
+   A vertex is thick (ballistic) in a step when its optical depth y tau_max
+   reaches tau_switch (always, in ballistic transport), else thin (direction
+   conserving); sinks keep bins.  Photons arrive along in-edges and are kept
+   as the receiver's mode keeps them: a thin vertex in direction bins (bin
+   packets go to the closest bin of this step's orientation, edge packets to
+   the bin closest to the direction they travelled), a thick vertex per
+   in-edge.  A thin vertex sends its bins as in ox_one_step; a thick vertex
+   sends the photons of each in-edge to that edge's ballistic straight set,
+   and a thick source its own photons to all neighbours in equal parts
+   (Sect. 2.2.1). */
+static void ox_one_step_ballistic(ox_sim *s, double dt) {
+    const int nb = s->nbins;
+    const int64_t n = s->n;
+    const int64_t nnz = s->row_ptr[n];
+    double R[9];
+    ox_rotation(s->seed, s->step, R);
+    int32_t *qb = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nb);
+    int32_t *map = (int32_t *)malloc(sizeof(int32_t) * (size_t)nb);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)nb);
+    ox_rotated_bins(R, nb, s->bins, qb);
+    if (s->step > 0) {
+        double Rp[9];
+        ox_rotation(s->seed, s->step - 1, Rp);
+        int32_t *qp = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nb);
+        ox_rotated_bins(Rp, nb, s->bins, qp);
+        ox_bin_map(nb, qp, qb, map);
+        free(qp);
+    } else {
+        for (int b = 0; b < nb; ++b) map[b] = b;
+    }
+
+    /* the mode of every vertex in this step */
+    for (int64_t i = 0; i < n; ++i)
+        s->thick[i] = !(s->flags[i] & 1) &&
+                      (s->transport == 1 || s->y[i] * s->tau_max[i] >= s->tau_switch);
+
+    /* arrivals */
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r0 = s->row_ptr[i], r1 = s->row_ptr[i + 1];
+        double *Ii = s->I + (size_t)i * nb;
+        for (int b = 0; b < nb; ++b) Ii[b] = 0.0;
+        s->S[i] = 0.0;
+        if (!s->thick[i]) {
+            for (int b = 0; b < nb; ++b) tmp[b] = 0.0;
+            for (int64_t e = r0; e < r1; ++e)
+                for (int b = 0; b < nb; ++b) tmp[b] += s->Pb[(size_t)e * nb + b];
+            for (int b = 0; b < nb; ++b) Ii[map[b]] += tmp[b];
+            for (int64_t e = r0; e < r1; ++e) {
+                if (s->Pe[e] == 0.0) continue;
+                int32_t dir[3] = {-s->qedge[3 * e], -s->qedge[3 * e + 1], -s->qedge[3 * e + 2]};
+                Ii[closest_bin(qb, nb, dir)] += s->Pe[e];
+            }
+        } else {
+            for (int64_t e = r0; e < r1; ++e) {
+                double a = 0.0;
+                for (int b = 0; b < nb; ++b) a += s->Pb[(size_t)e * nb + b];
+                s->Ev[e] = a + s->Pe[e];
+            }
+        }
+    }
+
+    /* sources: in bins at a thin vertex, the vertex's own photons at a thick one */
+    for (int k = 0; k < s->nsrc; ++k) {
+        int64_t v = s->src_v[k];
+        double Nstep = s->src_rate[k] * dt;
+        s->budget[0] += Nstep;
+        if (s->thick[v]) {
+            s->S[v] += Nstep;
+        } else {
+            double share = Nstep / nb;
+            double *Iv = s->I + (size_t)v * nb;
+            for (int b = 0; b < nb; ++b) Iv[b] += share;
+        }
+    }
+
+    /* interaction and transport */
+    memset(s->Pbn, 0, sizeof(double) * (size_t)(nnz ? nnz : 1) * nb);
+    memset(s->Pen, 0, sizeof(double) * (size_t)(nnz ? nnz : 1));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r0 = s->row_ptr[i], r1 = s->row_ptr[i + 1];
+        const double *Ii = s->I + (size_t)i * nb;
+        double N_in = 0.0;
+        if (s->thick[i]) {
+            for (int64_t e = r0; e < r1; ++e) N_in += s->Ev[e];
+            N_in += s->S[i];
+        } else {
+            for (int b = 0; b < nb; ++b) N_in += Ii[b];
+        }
+        if (s->flags[i] & 1) {
+            s->budget[2] += N_in;
+            continue;
+        }
+        int nsub = 0, capped = 0;
+        double f = ox_chem(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
+                           s->max_sub, &nsub, &capped);
+        s->total_sub += nsub;
+        s->total_capped += capped;
+        double out_sum = 0.0;
+        if (!s->thick[i]) {
+            for (int b = 0; b < nb; ++b) {
+                double O = Ii[b] * f;
+                out_sum += O;
+                if (r1 == r0) {
+                    s->budget[2] += O;
+                    continue;
+                }
+                int k = associate(qb + 3 * b, s->qedge, r0, r1);
+                const uint8_t *st = s->straight + 4 * (r0 + k);
+                int cnt = st[3];
+                if (cnt == 0) {
+                    s->budget[2] += O;
+                    continue;
+                }
+                double w = O / cnt;
+                for (int m = 0; m < cnt; ++m) s->Pbn[(size_t)s->twin[r0 + st[m]] * nb + b] += w;
+            }
+        } else {
+            for (int64_t e = r0; e < r1; ++e) {
+                double O = s->Ev[e] * f;
+                out_sum += O;
+                const uint8_t *st = s->stb + 4 * e;
+                int cnt = st[3];
+                if (cnt == 0) {
+                    s->budget[2] += O;
+                    continue;
+                }
+                double w = O / cnt;
+                for (int m = 0; m < cnt; ++m) s->Pen[s->twin[r0 + st[m]]] += w;
+            }
+            if (s->S[i] != 0.0) {
+                double O = s->S[i] * f;
+                out_sum += O;
+                if (r1 == r0) {
+                    s->budget[2] += O;
+                } else {
+                    double w = O / (double)(r1 - r0);
+                    for (int64_t e = r0; e < r1; ++e) s->Pen[s->twin[e]] += w;
+                }
+            }
+        }
+        s->budget[1] += N_in - out_sum;
+    }
+    double *t = s->Pb;
+    s->Pb = s->Pbn;
+    s->Pbn = t;
+    t = s->Pe;
+    s->Pe = s->Pen;
+    s->Pen = t;
+    double inflight = 0.0;
+    for (size_t e = 0; e < (size_t)nnz * nb; ++e) inflight += s->Pb[e];
+    for (int64_t e = 0; e < nnz; ++e) inflight += s->Pe[e];
+    s->budget[3] = inflight;
+    s->step++;
+    free(qb);
+    free(map);
+    free(tmp);
+}
+
 void ox_step(ox_sim *s, double dt, int nsteps) {
-    for (int k = 0; k < nsteps; ++k) ox_one_step(s, dt);
+    for (int k = 0; k < nsteps; ++k) {
+        if (s->transport == 0) ox_one_step(s, dt);
+        else ox_one_step_ballistic(s, dt);
+    }
+}
+
+/* Photons in flight towards every vertex (the packets on its in-edges). */
+void ox_get_inflight(const ox_sim *s, double *out) {
+    const int nb = s->nbins;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double a = 0.0;
+        if (s->transport == 0) {
+            for (int b = 0; b < nb; ++b) a += s->I[(size_t)i * nb + b];
+        } else {
+            for (int64_t e = s->row_ptr[i]; e < s->row_ptr[i + 1]; ++e) {
+                for (int b = 0; b < nb; ++b) a += s->Pb[(size_t)e * nb + b];
+                a += s->Pe[e];
+            }
+        }
+        out[i] = a;
+    }
+}
+
+/* The ballistic tables and the modes of the last step (1 = thick). */
+void ox_get_ballistic(const ox_sim *s, uint8_t *stb, int64_t *twin, uint8_t *thick) {
+    int64_t nnz = s->row_ptr[s->n];
+    if (s->transport == 0) return;
+    memcpy(stb, s->stb, 4 * (size_t)nnz);
+    memcpy(twin, s->twin, sizeof(int64_t) * (size_t)nnz);
+    memcpy(thick, s->thick, (size_t)s->n);
 }
 
 void ox_get_y(const ox_sim *s, double *out) { memcpy(out, s->y, sizeof(double) * (size_t)s->n); }
