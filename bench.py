@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "cfd4c69426837bcd53bfa0981ffa986f59eeaf327633aa6831fa9f975148e123",
-               "bytes_per_launch": 1060.374e6 + 380.685e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "9408d42827a5df8b65a791e3803c7dc76b8885b1667185ae34cc6e3dc397fe04",
+               "bytes_per_launch": 1060.425e6 + 381.117e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
