@@ -176,6 +176,14 @@ def algorithmic_bytes_per_vertex(nbins: int, fp64: bool, mean_degree: float) -> 
     return 2 * nbins * w + 16 + 4 * mean_degree + 16
 
 
+def ballistic_bytes_per_vertex(mean_degree: float) -> float:
+    """Bytes one vertex-step of ballistic transport must move: per edge, the
+    FP32 packet on the in-edge read and the one on the out-edge written, the
+    sender id and the packed straight set; y read and written and the
+    constants (16 bytes each)."""
+    return (4 + 4 + 4 + 4) * mean_degree + 16 + 16
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -514,6 +522,57 @@ def run_served(args):
                       **stats, "one_at_a_time": st_p, "identical_results": same}), flush=True)
 
 
+def run_transport(args):
+    """Direction-conserving, ballistic and combined transport (tau_switch = 1,
+    Sect. 5.1.3) on the C1 grid (Test 1, 2^20 interior vertices, 84 bins,
+    FP32 transport, dt = 0.5 Myr): the step kernel's mean time over the same
+    --steps after --warmup steps from a neutral start, timed with per-launch
+    CUDA events.  Sect. 3.3 of the paper compares the three the same way."""
+    import torch
+
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    wl = WORKLOADS["c1"]
+    prob = make_problem(wl, wl["seed"])
+    bins = I.fibonacci_bins(wl["nbins"])
+    dt = wl["dt_myr"] * I.MYR_S
+    n_int = int(prob.interior.sum())
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    rows = {}
+    for name, tp in (("direction_conserving", S.SX_TRANSPORT_DCT),
+                     ("ballistic", S.SX_TRANSPORT_BALLISTIC),
+                     ("combined_tau1", S.SX_TRANSPORT_COMBINED)):
+        s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=wl["seed"], transport=tp,
+                     tau_switch=1.0).load(prob)
+        s.step(dt, args.warmup)
+        s.sync()
+        s.profile(True)
+        s.step(dt, args.steps)
+        info = s.info
+        ms = info["step_kernel_ms"] / max(info["step_kernel_launches"], 1)
+        b = s.budget
+        y = s.y
+        s.close()
+        mean_deg = prob.nnz / prob.n
+        if tp == S.SX_TRANSPORT_DCT:
+            per_v = algorithmic_bytes_per_vertex(wl["nbins"], False, mean_deg)
+        else:  # an edge packet read and written, sender id and straight set per edge; y, constants
+            per_v = ballistic_bytes_per_vertex(mean_deg)
+        gbs = per_v * prob.n / (ms * 1e-3) / 1e9
+        rows[name] = {"step_kernel_ms": ms,
+                      "vertex_steps_per_s": n_int / (ms * 1e-3),
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                   "frac": gbs / peak, "algorithmic_bytes_per_vertex": per_v},
+                      "ionised_fraction": float(np.mean(y[prob.interior] < 0.5)),
+                      "budget_residual": (b["emitted"] - b["absorbed"] - b["escaped"]
+                                          - b["in_flight"]) / b["emitted"]}
+        torch.cuda.synchronize()
+    print(json.dumps({"mode": "transport", "workload": wl["name"], "steps": args.steps,
+                      "warmup": args.warmup, **rows}), flush=True)
+
+
 def run_clumpy(args):
     """The clumpy medium (2^22 points by default, lognormal density on a 128^3
     mesh, 16 sources, 84 bins, FP32 transport, dt = 0.5 Myr) with the dynamic
@@ -588,7 +647,8 @@ def main(argv=None):
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy"], default="step")
+    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport"],
+                    default="step")
     ap.add_argument("--clumpy-n", type=int, default=1 << 22)
     ap.add_argument("--clumpy-steps", type=int, default=200)
     ap.add_argument("--update-every", type=int, default=50)
@@ -612,6 +672,9 @@ def main(argv=None):
         return
     if args.mode == "clumpy":
         run_clumpy(args)
+        return
+    if args.mode == "transport":
+        run_transport(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -53,6 +53,32 @@ enum {
                               in float-float and FP64 */
 };
 
+/* Transport of the photons that a vertex passes on (Sect. 2.2):
+     SX_TRANSPORT_DCT        direction conserving (Sect. 2.2.3): photons in n
+                             global direction bins, rotated every step;
+     SX_TRANSPORT_BALLISTIC  ballistic (Sect. 2.2.2): photons kept per
+                             incoming edge and sent on, in 3 equal parts, to
+                             the most straightforward neighbours with respect
+                             to that edge (none beyond 90 degrees); a source
+                             sends to all its neighbours;
+     SX_TRANSPORT_COMBINED   combined (Sect. 2.2.4): a vertex is ballistic in a
+                             step when its optical depth y tau_max (y its
+                             neutral fraction at the start of the step) is at
+                             least tau_switch, else direction conserving;
+                             photons arriving at a direction-conserving vertex
+                             along an edge go to the bin closest to the
+                             direction they travelled, bins arriving at a
+                             ballistic vertex along an edge are summed into
+                             that edge.
+   Ballistic and combined transport support sx_step, sx_step_budgets and the
+   readouts; the dynamic grid update, checkpoints, batches and the autotuner
+   take direction-conserving contexts only (SX_EINVAL otherwise). */
+enum {
+    SX_TRANSPORT_DCT = 0,
+    SX_TRANSPORT_BALLISTIC = 1,
+    SX_TRANSPORT_COMBINED = 2
+};
+
 #define SX_MAX_BINS 128
 #define SX_MAX_DEGREE 64      /* per non-sink vertex */
 #define SX_MAX_SOURCES 4096
@@ -72,6 +98,9 @@ typedef struct {
     int32_t chem_max_sub;   /* subcycle cap per step (>= 1) */
     int32_t device;         /* CUDA device ordinal */
     void *stream;           /* cudaStream_t, or NULL */
+    int32_t transport;      /* SX_TRANSPORT_DCT (default), _BALLISTIC or _COMBINED */
+    double tau_switch;      /* combined: ballistic where y tau_max >= tau_switch (default 1,
+                               Sect. 5.1.3) */
 } sx_config;
 
 typedef struct {

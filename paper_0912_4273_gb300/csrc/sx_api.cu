@@ -60,6 +60,9 @@ struct sx_ctx {
 static thread_local std::string g_create_err;
 static constexpr int kGraphSteps = sx::kRotAhead;  // one rotation launch per graph
 static_assert(sx::kRotAhead == SX_STEP_BLOCK, "the step block of the header");
+static_assert(sx::kTransportDct == SX_TRANSPORT_DCT && sx::kTransportBallistic == SX_TRANSPORT_BALLISTIC &&
+                  sx::kTransportCombined == SX_TRANSPORT_COMBINED,
+              "transport values of the header");
 
 static int fail(sx_ctx *c, int code, const std::string &msg) {
   if (c) c->err = msg; else g_create_err = msg;
@@ -137,7 +140,7 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   if (nnz >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "nnz must be < 2^31");
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
     return fail(c, SX_EINVAL, "workspace must be 256-byte aligned");
-  const sx::Layout Lw = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision);
+  const sx::Layout Lw = sx::make_layout(n, nnz, c->cfg.nbins, c->cfg.precision, c->cfg.transport);
   const int64_t need = (int64_t)(Lw.total + sizeof(double) * 3 * sx::kMaxBins + 256);
   if (workspace_bytes < need)
     return fail(c, SX_ENOMEM, "workspace too small: need " + std::to_string(need) + " bytes");
@@ -153,6 +156,8 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
   g.precision = c->cfg.precision;
   g.punit = 1.0;
+  g.transport = c->cfg.transport;
+  g.tau_switch = c->cfg.tau_switch;
   *bins_dev = reinterpret_cast<double *>(static_cast<char *>(d_workspace) + L.total);
   c->ws_base = d_workspace;
   c->ws_used = L.total + sizeof(double) * 3 * (size_t)c->cfg.nbins;
@@ -177,6 +182,10 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
                              cudaMemcpyHostToDevice, st));
   // tables
   SX_CUDA(c, sx::launch_setup(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
+  if (g.stb) {  // ballistic and combined transport: no packets yet, every vertex thin so far
+    SX_CUDA(c, cudaMemsetAsync(base + L.off_B0, 0, L.off_stb - L.off_B0, st));
+    SX_CUDA(c, sx::launch_ballistic_tables(g, st));
+  }
   SX_CUDA(c, sx::launch_rotation(g, *bins_dev, c->cfg.seed, 1, 1, 1.0, st));
   SX_CUDA(c, sx::launch_kappa_and_consts(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
                                           y0 ? g.s_y0 : nullptr, st));
@@ -211,6 +220,13 @@ static sx::BudgetScale budget_scale(const sx_ctx *c) {
   return sc;
 }
 
+// Entry points that handle direction-conserving transport only.
+static int dct_only(sx_ctx *c, const char *what) {
+  if (c->cfg.transport != SX_TRANSPORT_DCT)
+    return fail(c, SX_EINVAL, std::string(what) + " takes direction-conserving transport only");
+  return SX_OK;
+}
+
 extern "C" {
 
 void sx_config_default(sx_config *cfg) {
@@ -227,6 +243,8 @@ void sx_config_default(sx_config *cfg) {
   cfg->chem_max_sub = 1000;
   cfg->device = 0;
   cfg->stream = nullptr;
+  cfg->transport = SX_TRANSPORT_DCT;
+  cfg->tau_switch = 1.0;
 }
 
 int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
@@ -258,6 +276,10 @@ int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
     return fail(nullptr, SX_EINVAL, "chem_tol must be >= 0 and chem_max_sub >= 1");
   if (!(cfg->sigma >= 0.0) || !(cfg->alpha_B >= 0.0))
     return fail(nullptr, SX_EINVAL, "sigma and alpha_B must be >= 0");
+  if (cfg->transport != SX_TRANSPORT_DCT && cfg->transport != SX_TRANSPORT_BALLISTIC &&
+      cfg->transport != SX_TRANSPORT_COMBINED)
+    return fail(nullptr, SX_EINVAL, "transport must be SX_TRANSPORT_DCT, _BALLISTIC or _COMBINED");
+  if (std::isnan(cfg->tau_switch)) return fail(nullptr, SX_EINVAL, "tau_switch is NaN");
   for (int b = 0; b < cfg->nbins; ++b) {
     const double *d = bin_dirs + 3 * b;
     const double l2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -277,7 +299,7 @@ int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
 
 int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes) {
   if (!ctx || !bytes || n < 1 || nnz < 0) return fail(const_cast<sx_ctx *>(ctx), SX_EINVAL, "bad arguments");
-  const sx::Layout L = sx::make_layout(n, nnz, ctx->cfg.nbins, ctx->cfg.precision);
+  const sx::Layout L = sx::make_layout(n, nnz, ctx->cfg.nbins, ctx->cfg.precision, ctx->cfg.transport);
   *bytes = (int64_t)(L.total + sizeof(double) * 3 * sx::kMaxBins + 256);
   return SX_OK;
 }
@@ -312,6 +334,7 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
 int sx_grid_update_mark(sx_ctx *c, double y_thresh, double min_spacing, int32_t *removed,
                         int64_t *n_removed) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "the dynamic grid update")) return rc;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!removed || !n_removed) return fail(c, SX_EINVAL, "NULL argument");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
@@ -341,6 +364,7 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
                          const uint8_t *flags, const int32_t *old_of_new, void *d_workspace,
                          int64_t workspace_bytes) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "the dynamic grid update")) return rc;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!c->marked || c->mark_step != c->step)
     return fail(c, SX_ESTATE, "sx_grid_update_mark must come right before sx_grid_update_apply");
@@ -645,6 +669,7 @@ int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz) {
 
 int sx_save(sx_ctx *c, const char *path) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "a checkpoint")) return rc;
   if (!path) return fail(c, SX_EINVAL, "NULL path");
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (c->marked) return fail(c, SX_ESTATE, "a grid update is pending (mark without apply)");
@@ -699,6 +724,7 @@ int sx_save(sx_ctx *c, const char *path) {
 
 int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace_bytes) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "a checkpoint")) return rc;
   if (!path || !d_workspace) return fail(c, SX_EINVAL, "NULL argument");
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
     return fail(c, SX_EINVAL, "workspace not 256-byte aligned");
@@ -844,6 +870,7 @@ int sx_profile(sx_ctx *c, int enable) {
 
 int sx_set_variant(sx_ctx *c, int32_t variant) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "a launch variant")) return rc;
   if (variant != 2 && variant != 4) return fail(c, SX_EINVAL, "variant must be 2 or 4 vertices per warp");
   if (c->g.group != variant && c->graph) {  // a captured graph holds the old kernel
     cudaGraphExecDestroy(c->graph);
@@ -862,6 +889,7 @@ int sx_get_variant(sx_ctx *c, int32_t *variant) {
 int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scratch_bytes,
                 sx_tune_result *out) {
   if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "the autotuner")) return rc;
   if (!out || !scratch) return fail(c, SX_EINVAL, "NULL argument");
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1 || nsteps > 1000)
@@ -1002,6 +1030,8 @@ int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_
     const sx_ctx *c = ctxs[i];
     if (!c) return bfail(b, SX_EINVAL, "NULL context");
     if (!c->loaded) return bfail(b, SX_ESTATE, "context without grid");
+    if (c->cfg.transport != SX_TRANSPORT_DCT)
+      return bfail(b, SX_EINVAL, "a batch takes direction-conserving transport only");
     if (c->cfg.nbins != c0->cfg.nbins || c->cfg.precision != c0->cfg.precision ||
         c->cfg.device != b->device)
       return bfail(b, SX_EINVAL, "contexts differ in nbins, precision or device");

@@ -10,6 +10,8 @@ namespace sx {
 constexpr int kQ = 127;            // quantisation of unit vectors (int8)
 constexpr int kMaxBins = 128;
 constexpr int kMaxDeg = 64;        // largest non-sink degree the step kernel stages
+// transports (the values of SX_TRANSPORT_*)
+enum Transport { kTransportDct = 0, kTransportBallistic = 1, kTransportCombined = 2 };
 constexpr int kTile = 32;          // vertices per CTA in the step kernel (one chemistry warp)
 constexpr int kMaxSources = 4096;
 constexpr uint32_t kRotTag = 0x53583252u;  // Philox counter word 3 of the rotation draws
@@ -90,6 +92,16 @@ struct StepArgs {
   const float *src_share_f;
   double *partials;
   unsigned long long *diag;
+  // ballistic and combined transport (unused in direction-conserving transport)
+  void *B[2];              // edge packets at the receivers' in-edges, ping-pong by step parity
+  uint8_t *mode[2];        // 1 where the vertex sent ballistically, ping-pong by step parity
+  const uint32_t *stb;     // ballistic straight set of every in-edge
+  const uint16_t *bpos;    // per out-slot: start (low byte) and length of its in-edge list
+  const uint8_t *binv;     // the in-edge lists, 3 bytes per edge of a row
+  const double *src_rate;  // photons/s of each source slot
+  double src_scale;        // dt / punit: a source's photons of the step in stored units
+  int transport;
+  double tau_switch;
 };
 
 enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagCount = 8 };
@@ -223,17 +235,25 @@ struct DevGrid {
   uint8_t *s_flags;
   float4 *s_ev;         // nnz: edge vector (x, y, z) and length (w), FP32
   double *s_out;        // n doubles for readouts
+  // ballistic and combined transport (null in direction-conserving transport)
+  int transport;        // Transport
+  double tau_switch;    // combined: ballistic where y tau_max >= tau_switch
+  void *B[2];           // nnz edge packets (T) at the receivers' in-edges, ping-pong
+  uint8_t *mode[2];     // n: 1 where the vertex sent ballistically, ping-pong
+  uint32_t *stb;        // nnz: ballistic straight set of each in-edge (3 slot bytes, count)
+  uint16_t *bpos;       // nnz: per out-slot, where its in-edge list starts (low byte) and its length
+  uint8_t *binv;        // 3 nnz: the in-edges whose set holds each out-slot, ascending
 };
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
       off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
-      total;
+      off_B0, off_B1, off_mode0, off_mode1, off_stb, off_bpos, off_binv, total;
   int64_t nblocks, nblocks_kappa;
 };
 
-Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision);
+Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transport = 0);
 void bind_layout(DevGrid &g, void *base, const Layout &L);
 
 cudaError_t launch_setup(DevGrid &g, const double *bins_dev, double sigma, double alpha_B,
@@ -281,5 +301,7 @@ cudaError_t launch_row_totals(int precision, int64_t n, int nbins, int nbp, cons
 cudaError_t launch_sum_rows(int precision, int64_t n, int nbins, int nbp, const void *I,
                             double *part, int nblk, cudaStream_t st);
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
+// ballistic straight sets of every in-edge (after the edge tables)
+cudaError_t launch_ballistic_tables(DevGrid &g, cudaStream_t st);
 
 }  // namespace sx

@@ -10,7 +10,7 @@ namespace sx {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
+Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transport) {
   Layout L{};
   const int nbp = (nbins + 3) / 4 * 4;
   const int mw = nbins <= 32 ? 1 : (nbins <= 64 ? 2 : 4);
@@ -52,6 +52,15 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision) {
   L.off_s_flags = take(n);
   L.off_s_ev = take(sizeof(float4) * nnz);
   L.off_s_out = take(sizeof(double) * n);
+  if (transport != 0) {  // ballistic and combined transport: edge packets, modes, straight sets
+    L.off_B0 = take(tsz * nnz);
+    L.off_B1 = take(tsz * nnz);
+    L.off_mode0 = take(n);
+    L.off_mode1 = take(n);
+    L.off_stb = take(sizeof(uint32_t) * nnz);
+    L.off_bpos = take(sizeof(uint16_t) * nnz);
+    L.off_binv = take(3 * (size_t)nnz);
+  }
   L.total = o;
   return L;
 }
@@ -89,6 +98,88 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.s_flags = reinterpret_cast<uint8_t *>(b + L.off_s_flags);
   g.s_ev = reinterpret_cast<float4 *>(b + L.off_s_ev);
   g.s_out = reinterpret_cast<double *>(b + L.off_s_out);
+  if (L.off_stb) {
+    g.B[0] = b + L.off_B0;
+    g.B[1] = b + L.off_B1;
+    g.mode[0] = reinterpret_cast<uint8_t *>(b + L.off_mode0);
+    g.mode[1] = reinterpret_cast<uint8_t *>(b + L.off_mode1);
+    g.stb = reinterpret_cast<uint32_t *>(b + L.off_stb);
+    g.bpos = reinterpret_cast<uint16_t *>(b + L.off_bpos);
+    g.binv = reinterpret_cast<uint8_t *>(b + L.off_binv);
+  } else {
+    g.B[0] = g.B[1] = nullptr;
+    g.mode[0] = g.mode[1] = nullptr;
+    g.stb = nullptr;
+    g.bpos = nullptr;
+    g.binv = nullptr;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Ballistic straight sets (Sect. 2.2.2): photons that came in along the edge
+// from neighbour j (travelling along -q_ij) go on to the <= 3 slots k with
+// the largest positive quantised dot q_ik . (-q_ij), ties -> lowest slot.
+// Packed as slot bytes (x, y, z) and the count in the top byte.  Rows longer
+// than 255 slots (sinks', which never send) get no set.
+// ----------------------------------------------------------------------------
+//   The inverse: for out-slot k of vertex i, the in-edges j whose set holds k,
+//   ascending, as bytes at binv[3 r0 + off] (r0 the row start, 3 bytes per
+//   edge of the row) with bpos[r0 + k] = off | count << 8.
+__global__ void k_ballistic_tables(int64_t n, const int32_t *__restrict__ rp, const Edge *__restrict__ edges,
+                                   uint32_t *__restrict__ stb, uint16_t *__restrict__ bpos,
+                                   uint8_t *__restrict__ binv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t r0 = rp[i], r1 = rp[i + 1];
+  for (int32_t e = r0; e < r1; ++e) {
+    const char4 qe = edges[e].q;
+    int best[3];
+    int slot[3];
+    int cnt = 0;
+    if (r1 - r0 <= 255) {
+      for (int32_t e2 = r0; e2 < r1; ++e2) {
+        const char4 q2 = edges[e2].q;
+        const int d = -((int)qe.x * q2.x + (int)qe.y * q2.y + (int)qe.z * q2.z);
+        if (d <= 0) continue;
+        int at = cnt;
+        while (at > 0 && d > best[at - 1]) at--;
+        if (at >= 3) continue;
+        const int last = cnt < 3 ? cnt : 2;
+        for (int m = last; m > at; --m) {
+          best[m] = best[m - 1];
+          slot[m] = slot[m - 1];
+        }
+        best[at] = d;
+        slot[at] = (int)(e2 - r0);
+        if (cnt < 3) cnt++;
+      }
+    }
+    uint32_t w = (uint32_t)cnt << 24;
+    for (int m = 0; m < 3; ++m) w |= (uint32_t)(m < cnt ? slot[m] : 0xFF) << (8 * m);
+    stb[e] = w;
+  }
+  int off = 0;
+  for (int32_t k = 0; k < r1 - r0; ++k) {
+    int c = 0;
+    if (r1 - r0 <= kMaxDeg) {  // 3 kMaxDeg < 256: the start fits its byte (longer rows are sinks')
+      for (int32_t j = 0; j < r1 - r0; ++j) {
+        const uint32_t w = stb[r0 + j];
+        const int cnt = (int)(w >> 24);
+        bool hit = false;
+        for (int m = 0; m < cnt; ++m) hit |= (int)((w >> (8 * m)) & 0xFFu) == k;
+        if (hit) binv[3 * (int64_t)r0 + off + c++] = (uint8_t)j;
+      }
+    }
+    bpos[r0 + k] = (uint16_t)(off | (c << 8));
+    off += c;
+  }
+}
+
+cudaError_t launch_ballistic_tables(DevGrid &g, cudaStream_t st) {
+  if (!g.stb || g.n <= 0) return cudaSuccess;
+  k_ballistic_tables<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(g.n, g.row_ptr, g.edges, g.stb,
+                                                                     g.bpos, g.binv);
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

@@ -27,6 +27,7 @@
 #include <algorithm>
 
 #include "sx_internal.cuh"
+#include "sx_step_common.cuh"  // chemistry, mask words, budget sums, packet rounds
 
 namespace sx {
 
@@ -204,238 +205,6 @@ cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, int count, c
   return cudaGetLastError();
 }
 
-// ----------------------------------------------------------------------------
-// Chemistry of one cell over one step (Sect. 4.5): explicit subcycles at
-// constant flux F = N_in / dt; each subcycle absorbs F h (1 - e^-tau) photons
-// (one ionisation each) and transmits F h e^-tau; its length is
-// h = min(t_left, f_c / (Gamma + R)) with Gamma + R = ion / y + alpha_B n_e;
-// equilibrium (|dy| <= tol y) keeps the last subcycle's rates for the rest of
-// the step.  FP64.  One expm1 and one division per subcycle: e^-tau is
-// 1 + expm1(-tau) (its absolute error, 1e-16 of N_in, is what matters for the
-// transmitted photons), and f_c / (Gamma + R) = f_c y / (ion + R0 x y).
-// Returns the transmitted fraction f = (1/dt) sum e^-tau_k h_k.
-// ----------------------------------------------------------------------------
-__device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt, double invA,
-                            double tau_max, double R0, double fc, double tol, int max_sub,
-                            int &nsub, int &capped) {
-  double y = y_io;
-  nsub = 0;
-  capped = 0;
-  if (invA == 0.0) return 1.0;  // no atoms: transparent, nothing to ionise
-  const double F = __dmul_rn(N_in, inv_dt);
-  double t_left = dt;
-  double trans_int = 0.0;
-  while (t_left > 0.0) {
-    const double em = expm1(-__dmul_rn(tau_max, y));
-    const double ab = -em;                   // absorbed fraction
-    const double tr = __dadd_rn(1.0, em);    // transmitted fraction
-    const double ion = __dmul_rn(__dmul_rn(F, ab), invA);  // photoionisations per atom per s
-    const double x = __dsub_rn(1.0, y);
-    const double r0x = __dmul_rn(R0, x);
-    const double rec = __dmul_rn(r0x, x);    // recombinations per atom per s
-    double h = t_left;
-    if (y > 0.0) {
-      const double den = __dadd_rn(ion, __dmul_rn(r0x, y));
-      if (den > 0.0) {
-        const double hc = __ddiv_rn(__dmul_rn(fc, y), den);
-        if (hc < h) h = hc;
-      }
-    } else {
-      const double rate = __dadd_rn(__dmul_rn(__dmul_rn(F, tau_max), invA), r0x);
-      if (rate > 0.0) {
-        const double hc = __ddiv_rn(fc, rate);
-        if (hc < h) h = hc;
-      }
-    }
-    const double y_new = __dadd_rn(y, __dmul_rn(__dsub_rn(rec, ion), h));
-    trans_int = __dadd_rn(trans_int, __dmul_rn(tr, h));
-    t_left = (h == t_left) ? 0.0 : __dsub_rn(t_left, h);
-    nsub++;
-    const bool eq = fabs(__dsub_rn(y_new, y)) <= __dmul_rn(tol, y_new);
-    y = y_new;
-    if (t_left > 0.0 && (eq || nsub >= max_sub)) {
-      if (!eq) capped = 1;
-      trans_int = __dadd_rn(trans_int, __dmul_rn(tr, t_left));
-      t_left = 0.0;
-    }
-  }
-  y_io = y;
-  return __dmul_rn(trans_int, inv_dt);
-}
-
-// ----------------------------------------------------------------------------
-// The same subcycles for FP32 transport: rates, subcycle lengths and the
-// exponentials in FP32 (the photon field is FP32 already), the neutral
-// fraction accumulated in FP64, from float copies of y and x = 1 - y that
-// follow the FP32 increments.  The transmitted and the absorbed time
-// integrals are summed apart, each accurate where it is small, and the
-// returned f is taken from the smaller: e^-tau in thick cells, 1 - absorbed
-// in thin ones; *absf is the absorbed fraction, f + absf = 1 up to rounding.
-// Fa = F / A, photoionisations per atom per second at full absorption.
-// ----------------------------------------------------------------------------
-__device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau, float R0, float fc,
-                             float tol, int max_sub, int &nsub, int &capped, float &absf) {
-  double y = y_io;
-  float yf = (float)y, xf = (float)(1.0 - y);
-  nsub = 0;
-  capped = 0;
-  float t_left = dt, trans = 0.f, absd = 0.f;
-  while (t_left > 0.f) {
-    const float ty = tau * yf;
-    const float ab = -expm1f(-ty);  // absorbed fraction
-    const float tr = expf(-ty);     // transmitted fraction
-    const float ion = Fa * ab;
-    const float r0x = R0 * xf;
-    const float rec = r0x * xf;
-    float h = t_left;
-    if (yf > 0.f) {
-      const float den = ion + r0x * yf;
-      if (den > 0.f && fc * yf < den * t_left) h = __fdividef(fc * yf, den);
-    } else {
-      const float rate = Fa * tau + r0x;
-      if (rate > 0.f && fc < rate * t_left) h = __fdividef(fc, rate);
-    }
-    const float dy = (rec - ion) * h;
-    y += (double)dy;
-    yf += dy;
-    xf -= dy;
-    trans += tr * h;
-    absd += ab * h;
-    t_left = (h == t_left) ? 0.f : t_left - h;
-    nsub++;
-    const bool eq = fabsf(dy) <= tol * yf;
-    if (t_left > 0.f && (eq || nsub >= max_sub)) {
-      if (!eq) capped = 1;
-      trans += tr * t_left;
-      absd += ab * t_left;
-      t_left = 0.f;
-    }
-  }
-  y_io = y;
-  const float inv_dt = 1.f / dt;
-  const float fa = absd * inv_dt, ft = trans * inv_dt;
-  if (fa < ft) {
-    absf = fa;
-    return 1.f - fa;
-  }
-  absf = 1.f - ft;
-  return ft;
-}
-
-// ----------------------------------------------------------------------------
-// Mask words of one edge: bin b is bit b % 32 of word b / 32.  Memory holds
-// 1, 2 or 4 words per edge; 65..96 bins are handled as 3 words in registers
-// and kept at the 16-byte stride of 4 (the fourth word is zero).
-// ----------------------------------------------------------------------------
-template <int MW>
-__device__ __forceinline__ void load_mask(const uint32_t *__restrict__ M, int64_t e, uint32_t m[MW]) {
-  if constexpr (MW == 1) {
-    m[0] = __ldg(M + e);
-  } else if constexpr (MW == 2) {
-    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(M) + e);
-    m[0] = v.x; m[1] = v.y;
-  } else {
-    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(M) + e);
-    m[0] = v.x; m[1] = v.y; m[2] = v.z;
-    if constexpr (MW == 4) m[3] = v.w;
-  }
-}
-template <int MW>
-__device__ __forceinline__ void store_mask(uint32_t *__restrict__ M, int64_t e, const uint32_t m[MW]) {
-  if constexpr (MW == 1) {
-    M[e] = m[0];
-  } else if constexpr (MW == 2) {
-    reinterpret_cast<uint2 *>(M)[e] = make_uint2(m[0], m[1]);
-  } else if constexpr (MW == 3) {
-    reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], 0u);  // 16-byte stride
-  } else {
-    reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], m[3]);
-  }
-}
-
-// Row stride (elements) of the shared photon tile: odd, so that a lane per
-// vertex walking its own row touches 32 distinct banks.
-__host__ __device__ __forceinline__ int tile_stride(int nbins) { return nbins | 1; }
-
-// Per-lane budget accumulator: FP64 sum, or float-float in FP32 mode (the
-// FP64 pipe is narrow, so FP32-mode tiles combine their partial sums in
-// float-float and convert once).
-template <typename T>
-struct Acc;
-template <>
-struct Acc<double> {
-  double v = 0.0;
-  __device__ void add(double x) { v = __dadd_rn(v, x); }
-};
-template <>
-struct Acc<float> {
-  FF v{0.f, 0.f};
-  __device__ void add(float x) { v = ff_add(v, x); }
-};
-
-// A budget term of one lane (the type of Acc<T>::v) and its sums.
-template <typename T>
-struct Bud;
-template <>
-struct Bud<double> {
-  using type = double;
-  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
-  __device__ static double warp_sum(double v) { return warp_sum_d(v); }
-  __device__ static double to_double(double v) { return v; }
-  __device__ static double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-};
-template <>
-struct Bud<float> {
-  using type = FF;
-  __device__ static FF add(FF a, FF b) { return ff_add(a, b); }
-  __device__ static FF warp_sum(FF v) { return ff_warp_sum(v); }
-  __device__ static double to_double(FF v) { return ff_to_double(v); }
-  __device__ static FF shfl_xor(FF v, int o) {
-    return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-  }
-};
-
-#ifndef SX_STEP_MIN_BLOCKS
-#define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
-#endif
-
-// A step kernel variant works on 32-vertex tiles with G consecutive vertices
-// per warp, so kTile / G warps per CTA: G = 4 (8 warps, 6 CTAs/SM) or G = 2
-// (16 warps, 3 CTAs/SM), both at 40 registers.
-template <int G>
-struct Shape {
-  static constexpr int kWarps = kTile / G;
-  static constexpr int kThreads = 32 * kWarps;
-  static constexpr int kMinBlocks = SX_STEP_MIN_BLOCKS * 8 / kWarps;
-  static constexpr int kCap = 18 * G;  // out-edges of a group staged at once in phase 3
-  static constexpr int kLanesPerVertex = 32 / G;
-};
-
-// One round of photon packets arriving at the vertices of a warp's group:
-// lane i adds `val` to bin `key & 127` of group vertex `key >> 7` (if `on`).
-// Lanes of equal key add in lane order, one rank at a time, so every bin
-// sums its packets in list order.  The rows start at zero.
-template <typename T, int MW>
-__device__ __forceinline__ void add_round(T *grow, int nbs, uint32_t (*gocc)[MW], bool on,
-                                          int key, T val, uint32_t lt_mask) {
-  const int k = on ? key : (1 << 12) + (int)(threadIdx.x & 31);  // idle lanes: unique keys
-  const uint32_t grp = __match_any_sync(0xffffffffu, k);
-  const unsigned rank = __popc(grp & lt_mask);
-  const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
-  T *dst = grow + (k >> 7) * nbs + (k & 127);
-  for (unsigned r = 0; r <= maxr; ++r) {
-    if (on && rank == r) *dst += val;
-    __syncwarp();
-  }
-  if (on) atomicOr(&gocc[k >> 7][(k & 127) >> 5], 1u << (k & 31));
-}
-
-// Bins 0..nbins-1 that fall in mask word w.
-__device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
-  const int n = nbins - 32 * w;
-  return n >= 32 ? 0xffffffffu : (n <= 0 ? 0u : ((1u << n) - 1u));
-}
-
 // One tile of kTile consecutive vertices; warp w owns the group of kGroup
 // vertices kGroup w .. kGroup w + kGroup - 1 in phases 1 and 3, whose edges
 // are one contiguous range of the CSR arrays.
@@ -450,7 +219,13 @@ __device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
 //            in-edges.
 // Only bins that hold photons are touched: a bin without photons sets no mask
 // bit, so no reader looks at its stored value, and it is not written.
-template <typename T, int MW, int G>
+// With BAL (ballistic and combined transport) a vertex of the tile is thick
+// (ballistic) or thin (direction conserving) in the step: a thick vertex keeps
+// its photons per in-edge (the bins arriving along an edge summed into it)
+// and sends each in-edge's photons to that edge's ballistic straight set; a
+// thin vertex is handled as without BAL, and turns photons arriving along an
+// edge from a thick sender into the bin closest to their direction.
+template <typename T, int MW, int G, bool BAL = false>
 __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *__restrict__ tab, int64_t tile,
                                           bool reload, bool more) {
   constexpr int kGroup = G;
@@ -471,6 +246,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
 
   __shared__ int s_incoming;
   __shared__ long long s_step;
+  // BAL: thick vertices' photons per in-edge and their sources' photons of
+  // the step, and every tile vertex's mode (one element each without BAL)
+  __shared__ T s_E[BAL ? kTile : 1][BAL ? kMaxDeg : 1];
+  __shared__ T s_S[BAL ? kTile : 1];
+  __shared__ unsigned char s_thick[BAL ? kTile : 1];
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
   constexpr int kScr1 = 0;
@@ -520,6 +300,18 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   }
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
+  if constexpr (BAL) {  // the group's modes: thick where y tau_max reaches tau_switch
+    if (lane < kGroup) {
+      bool thick = false;
+      if (vg + lane < a.n) {
+        const VConst c = a.vc[vg + lane];
+        thick = !(c.flags & 1) && (a.transport == kTransportBallistic ||
+                                   __dmul_rn(a.y[vg + lane], c.tau_max) >= a.tau_switch);
+      }
+      s_thick[g0 + lane] = thick ? 1 : 0;
+      s_S[g0 + lane] = T(0);
+    }
+  }
   // the tile's running budget (escaped, absorbed), read now so that the load
   // overlaps the tile, by the lanes that write it back
   double run_part = 0.0;
@@ -562,9 +354,32 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       uint32_t my_m[MW];
 #pragma unroll
       for (int w = 0; w < MW; ++w) my_m[w] = 0u;
+      T edge_val = T(0);  // BAL: a packet that a thick sender routed along this edge
       if (e < R[kGroup]) {
         my_src = a.col[e];
-        load_mask<MW>(M_prev, (int64_t)e, my_m);
+        if constexpr (BAL) {
+          if (a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
+          else load_mask<MW>(M_prev, (int64_t)e, my_m);
+          if (s_thick[g0 + g]) {
+            // a thick receiver keeps the edge's photons together: the
+            // sender's bins ascending, then the edge packet
+            T acc = T(0);
+#pragma unroll
+            for (int w = 0; w < MW; ++w) {
+              uint32_t m = my_m[w];
+              while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1u;
+                acc += Pp[(size_t)my_src * nbp + 32 * w + i];
+              }
+              my_m[w] = 0u;
+            }
+            s_E[g0 + g][e - R[g]] = acc + edge_val;
+            edge_val = T(0);
+          }
+        } else {
+          load_mask<MW>(M_prev, (int64_t)e, my_m);
+        }
       }
       int cnt = 0;
 #pragma unroll
@@ -613,8 +428,31 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         }
         add_round<T, MW>(grow, nbs, gocc, on, key, val, lt_mask);
       }
+      if constexpr (BAL) {
+        // packets from thick senders at thin receivers: into the bin closest
+        // to the direction they travelled (the edge to the sender reversed),
+        // ties -> lowest bin
+        const bool on = edge_val != T(0);
+        int key = 0;
+        if (on) {
+          const char4 q = a.edges[e].q;
+          const int nq = (int)(unsigned char)(-q.x) | ((int)(unsigned char)(-q.y) << 8) |
+                         ((int)(unsigned char)(-q.z) << 16);
+          int best = 0, bestd = __dp4a((int)s_qbq[0], nq, 0);
+          for (int b = 1; b < nbins; ++b) {
+            const int d = __dp4a((int)s_qbq[b], nq, 0);
+            if (d > bestd) {
+              best = b;
+              bestd = d;
+            }
+          }
+          key = (g << 7) | best;
+        }
+        add_round<T, MW>(grow, nbs, gocc, on, key, edge_val, lt_mask);
+      }
     }
-    // a source puts its share in every bin
+    // a source puts its share in every bin (BAL: a thick source keeps its
+    // photons of the step apart)
     int vsrc = -1;
     if (lane < kGroup && vg + lane < a.n) vsrc = a.vc[vg + lane].src;
     uint32_t srcs = __ballot_sync(0xffffffffu, vsrc >= 0);
@@ -622,6 +460,13 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       const int g = __ffs(srcs) - 1;
       srcs &= srcs - 1u;
       const int slot = __shfl_sync(0xffffffffu, vsrc, g);
+      if constexpr (BAL) {
+        if (s_thick[g0 + g]) {  // rate dt photons, in stored units
+          if (lane == 0) s_S[g0 + g] = (T)__dmul_rn(a.src_rate[slot], a.src_scale);
+          __syncwarp();
+          continue;
+        }
+      }
       T share;
       if constexpr (sizeof(T) == 8) share = a.src_share[slot]; else share = a.src_share_f[slot];
       T *row = grow + (size_t)g * nbs;
@@ -648,11 +493,32 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     if (v < a.n) {
       const VConst c = s_vc[vl];
       // N_in in stored units: the occupied bins of the vertex, ascending
+      // (BAL, thick: its in-edges ascending, then its source's photons)
       const T *row = s_I + (size_t)vl * nbs;
       typename Bud<T>::type nin_acc{};
+      bool thick_v = false;
+      if constexpr (BAL) {
+        thick_v = s_thick[vl] != 0;
+        if (thick_v) {
+          const int gw = vl / kGroup, gi = vl % kGroup;
+          const int dg = s_R[gw][gi + 1] - s_R[gw][gi];
+          for (int j = 0; j <= dg; ++j) {
+            const T x = j < dg ? s_E[vl][j] : s_S[vl];
+            if constexpr (sizeof(T) == 8) nin_acc = __dadd_rn(nin_acc, x);
+            else nin_acc = ff_add(nin_acc, x);
+          }
+        }
+      }
+      if constexpr (BAL) {
+        // a thick vertex without photons sends nothing: it passes on as a
+        // thin one (its masks are empty) and skips the per-edge sends
+        bool dark;
+        if constexpr (sizeof(T) == 8) dark = nin_acc == 0.0; else dark = nin_acc.hi == 0.f;
+        if (thick_v && dark) s_thick[vl] = 0;
+      }
 #pragma unroll
       for (int w = 0; w < MW; ++w) {
-        uint32_t m = s_occ[vl][w];
+        uint32_t m = thick_v ? 0u : s_occ[vl][w];
         while (m) {
           const int i = __ffs(m) - 1;
           m &= m - 1u;
@@ -720,6 +586,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * 32 * MW]
     int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
     if (lane < kGroup && vg + lane < a.n) vflags = s_vc[g0 + lane].flags;
+    if constexpr (BAL) {  // thick vertices send no bins either
+      if (lane < kGroup && s_thick[g0 + lane]) vflags |= 1;
+    }
     const uint32_t sinks = __ballot_sync(0xffffffffu, vflags & 1);
     // consecutive vertices ga .. gb - 1 whose out-edges fit in the staging area
     for (int ga = 0; ga < kGroup;) {
@@ -826,6 +695,58 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       __syncwarp();
       ga = gb;
     }
+    if constexpr (BAL) {
+      // thick vertices: the photons of in-edge j, O_j = f E_j, go in equal
+      // parts w_j = O_j / |S_j| to j's ballistic straight set S_j.  Lanes
+      // over the group's in-edges turn E_j into w_j in place; then lanes over
+      // its out-edges sum, for out-slot k, the w_j of the in-edges whose set
+      // holds k (j ascending), add the source's f S / degree and store the
+      // sum at the receiver's in-edge.
+      const int32_t EA = s_R[warp][0], EB = s_R[warp][kGroup];
+      for (int32_t e = EA + lane; e < EB; e += 32) {
+        int g = 0;
+#pragma unroll
+        for (int q = 1; q < kGroup; ++q) g += (e >= s_R[warp][q]) ? 1 : 0;
+        if (s_thick[g0 + g]) {
+          T &E = s_E[g0 + g][e - s_R[warp][g]];
+          const T o = E * s_f[g0 + g];
+          const int cnt = (int)(a.stb[e] >> 24);
+          if (cnt == 0) {
+            esc.add(o);  // no neighbour within 90 degrees: escaped
+            E = T(0);
+          } else {
+            fly.add(o);
+            if constexpr (sizeof(T) == 8) E = o / (T)cnt;
+            else E = o * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
+          }
+        }
+      }
+      if (lane < kGroup && s_thick[g0 + lane] && s_S[g0 + lane] != T(0)) {
+        const T os = s_S[g0 + lane] * s_f[g0 + lane];  // a source sends to all its neighbours
+        (s_R[warp][lane + 1] > s_R[warp][lane] ? fly : esc).add(os);
+      }
+      __syncwarp();
+      T *__restrict__ Bn = static_cast<T *>(a.B[cur]);
+      for (int32_t e = EA + lane; e < EB; e += 32) {
+        int g = 0;
+#pragma unroll
+        for (int q = 1; q < kGroup; ++q) g += (e >= s_R[warp][q]) ? 1 : 0;
+        if (s_thick[g0 + g]) {
+          const int32_t r0 = s_R[warp][g];
+          const int dg = s_R[warp][g + 1] - r0;
+          const unsigned ent = a.bpos[e];
+          const uint8_t *lst = a.binv + 3 * (int64_t)r0 + (ent & 0xFFu);
+          const T *Eg = s_E[g0 + g];
+          T acc = T(0);
+          for (unsigned i = 0; i < (ent >> 8); ++i) acc += Eg[lst[i]];
+          const T S = s_S[g0 + g];
+          if (S != T(0)) acc += (S * s_f[g0 + g]) / (T)dg;
+          Bn[a.edges[e].twin] = acc;
+        }
+      }
+      // every vertex's mode of this step, for its receivers in the next
+      if (lane < kGroup && vg + lane < a.n) a.mode[cur][vg + lane] = s_thick[g0 + lane];
+    }
   }
   if (warp < kTile / 32) {  // the chemistry lanes' subcycle counters
     unsigned ns = diag_nsub, nc = diag_capped;
@@ -885,6 +806,13 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_st
   step_tile<T, MW, G>(a, a.tab, blockIdx.x, true, false);
 }
 
+// Ballistic and combined transport: the same tiles with thick vertices (4
+// vertices per warp; the extra shared memory and registers allow 4 CTAs/SM).
+template <typename T, int MW>
+__global__ void __launch_bounds__(Shape<4>::kThreads, 4) k_step_bal(const StepArgs a) {
+  step_tile<T, MW, 4, true>(a, a.tab, blockIdx.x, true, false);
+}
+
 // Persistent CTAs pull (grid, tile) work items of a batch of grids from a
 // queue, `grab` (1..kBatchChunk) consecutive tiles at a time; a tile is one
 // grid's 32 consecutive vertices.
@@ -942,6 +870,17 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
   a.src_share_f = g.src_share_f;
   a.partials = g.partials;
   a.diag = g.diag;
+  a.B[0] = g.B[0];
+  a.B[1] = g.B[1];
+  a.mode[0] = g.mode[0];
+  a.mode[1] = g.mode[1];
+  a.stb = g.stb;
+  a.bpos = g.bpos;
+  a.binv = g.binv;
+  a.src_rate = g.src_rate;
+  a.src_scale = dt / g.punit;
+  a.transport = g.transport;
+  a.tau_switch = g.tau_switch;
   return a;
 }
 
@@ -990,12 +929,45 @@ struct StepLaunch {
   }
 };
 
+struct BalLaunch {
+  const StepArgs &a;
+  int64_t ntiles;
+  int nbins;
+  cudaStream_t st;
+  template <typename T, int MW>
+  cudaError_t run() const {
+    const size_t smem = sizeof(T) * (size_t)kTile * tile_stride(nbins);
+    static const bool done = [] {
+      cudaFuncSetAttribute(k_step_bal<T, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+      return true;
+    }();
+    (void)done;
+    k_step_bal<T, MW><<<(unsigned)ntiles, Shape<4>::kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+static cudaError_t dispatch_bal(int precision, int nbins, const BalLaunch &f) {
+  const int w = compute_words(nbins);
+  if (precision == 0) {
+    if (w == 1) return f.run<double, 1>();
+    if (w == 2) return f.run<double, 2>();
+    if (w == 3) return f.run<double, 3>();
+    return f.run<double, 4>();
+  }
+  if (w == 1) return f.run<float, 1>();
+  if (w == 2) return f.run<float, 2>();
+  if (w == 3) return f.run<float, 3>();
+  return f.run<float, 4>();
+}
+
 cudaError_t launch_step(DevGrid &g, int slot, double dt, double chem_frac, double chem_tol,
                         int chem_max_sub, cudaStream_t st) {
   if (g.nblocks <= 0) return cudaSuccess;
   if (slot < 0 || slot >= kRotAhead) return cudaErrorInvalidValue;
   StepArgs a = make_step_args(g, dt, chem_frac, chem_tol, chem_max_sub);
   a.tab = g.tabs + slot;
+  if (g.transport != kTransportDct) return dispatch_bal(g.precision, g.nbins, BalLaunch{a, g.nblocks, g.nbins, st});
   return dispatch_step(g.precision, g.nbins, g.group, StepLaunch{a, g.nblocks, g.nbins, st});
 }
 
@@ -1079,17 +1051,24 @@ cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Photons in flight towards every vertex after the last step (gather, FP64 sum).
+// Photons in flight towards every vertex after the last step (gather, FP64
+// sum): the bins its in-edges' masks name, or (ballistic and combined
+// transport) the edge packet where the sender was thick.
 template <typename T, int MW>
 __global__ void k_inflight(int64_t n, int nbins, int nbp, const int32_t *__restrict__ rp,
                            const Edge *__restrict__ edges, const T *__restrict__ P,
-                           const uint32_t *__restrict__ M, double *__restrict__ out) {
+                           const uint32_t *__restrict__ M, const uint8_t *__restrict__ mode,
+                           const T *__restrict__ B, double *__restrict__ out) {
   const int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (v >= n) return;
   double s = 0.0;
   for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
     const Edge E = edges[e];
+    if (mode && mode[E.col]) {
+      if (lane == 0) s += (double)B[e];
+      continue;
+    }
     uint32_t m[MW];
     load_mask<MW>(M, e, m);
 #pragma unroll
@@ -1106,16 +1085,19 @@ cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st) {
   // state after `step` steps lives in buffer (step - 1) & 1
   const int cur = (int)((step + 1) & 1);
   const unsigned blocks = (unsigned)((g.n * 32 + 255) / 256);
+  const uint8_t *mode = g.mode[cur];  // null in direction-conserving transport
   if (g.precision == 0) {
     const double *P = static_cast<const double *>(g.P[cur]);
-    if (g.mw == 1) k_inflight<double, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
-    else if (g.mw == 2) k_inflight<double, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
-    else k_inflight<double, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
+    const double *B = static_cast<const double *>(g.B[cur]);
+    if (g.mw == 1) k_inflight<double, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    else if (g.mw == 2) k_inflight<double, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    else k_inflight<double, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
   } else {
     const float *P = static_cast<const float *>(g.P[cur]);
-    if (g.mw == 1) k_inflight<float, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
-    else if (g.mw == 2) k_inflight<float, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
-    else k_inflight<float, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], g.s_out);
+    const float *B = static_cast<const float *>(g.B[cur]);
+    if (g.mw == 1) k_inflight<float, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    else if (g.mw == 2) k_inflight<float, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    else k_inflight<float, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
   }
   return cudaGetLastError();
 }

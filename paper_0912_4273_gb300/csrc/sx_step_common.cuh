@@ -1,0 +1,243 @@
+// sx_step_common.cuh -- device pieces shared by the step kernels of
+// direction-conserving transport (sx_step.cu) and of ballistic and combined
+// transport (sx_ballistic.cu): the chemistry of one cell, routing-mask words,
+// budget accumulators and ordered packet rounds.
+#pragma once
+
+#include "sx_internal.cuh"
+
+namespace sx {
+
+// ----------------------------------------------------------------------------
+// Chemistry of one cell over one step (Sect. 4.5): explicit subcycles at
+// constant flux F = N_in / dt; each subcycle absorbs F h (1 - e^-tau) photons
+// (one ionisation each) and transmits F h e^-tau; its length is
+// h = min(t_left, f_c / (Gamma + R)) with Gamma + R = ion / y + alpha_B n_e;
+// equilibrium (|dy| <= tol y) keeps the last subcycle's rates for the rest of
+// the step.  FP64.  One expm1 and one division per subcycle: e^-tau is
+// 1 + expm1(-tau) (its absolute error, 1e-16 of N_in, is what matters for the
+// transmitted photons), and f_c / (Gamma + R) = f_c y / (ion + R0 x y).
+// Returns the transmitted fraction f = (1/dt) sum e^-tau_k h_k.
+// ----------------------------------------------------------------------------
+static __device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt, double invA,
+                            double tau_max, double R0, double fc, double tol, int max_sub,
+                            int &nsub, int &capped) {
+  double y = y_io;
+  nsub = 0;
+  capped = 0;
+  if (invA == 0.0) return 1.0;  // no atoms: transparent, nothing to ionise
+  const double F = __dmul_rn(N_in, inv_dt);
+  double t_left = dt;
+  double trans_int = 0.0;
+  while (t_left > 0.0) {
+    const double em = expm1(-__dmul_rn(tau_max, y));
+    const double ab = -em;                   // absorbed fraction
+    const double tr = __dadd_rn(1.0, em);    // transmitted fraction
+    const double ion = __dmul_rn(__dmul_rn(F, ab), invA);  // photoionisations per atom per s
+    const double x = __dsub_rn(1.0, y);
+    const double r0x = __dmul_rn(R0, x);
+    const double rec = __dmul_rn(r0x, x);    // recombinations per atom per s
+    double h = t_left;
+    if (y > 0.0) {
+      const double den = __dadd_rn(ion, __dmul_rn(r0x, y));
+      if (den > 0.0) {
+        const double hc = __ddiv_rn(__dmul_rn(fc, y), den);
+        if (hc < h) h = hc;
+      }
+    } else {
+      const double rate = __dadd_rn(__dmul_rn(__dmul_rn(F, tau_max), invA), r0x);
+      if (rate > 0.0) {
+        const double hc = __ddiv_rn(fc, rate);
+        if (hc < h) h = hc;
+      }
+    }
+    const double y_new = __dadd_rn(y, __dmul_rn(__dsub_rn(rec, ion), h));
+    trans_int = __dadd_rn(trans_int, __dmul_rn(tr, h));
+    t_left = (h == t_left) ? 0.0 : __dsub_rn(t_left, h);
+    nsub++;
+    const bool eq = fabs(__dsub_rn(y_new, y)) <= __dmul_rn(tol, y_new);
+    y = y_new;
+    if (t_left > 0.0 && (eq || nsub >= max_sub)) {
+      if (!eq) capped = 1;
+      trans_int = __dadd_rn(trans_int, __dmul_rn(tr, t_left));
+      t_left = 0.0;
+    }
+  }
+  y_io = y;
+  return __dmul_rn(trans_int, inv_dt);
+}
+
+// ----------------------------------------------------------------------------
+// The same subcycles for FP32 transport: rates, subcycle lengths and the
+// exponentials in FP32 (the photon field is FP32 already), the neutral
+// fraction accumulated in FP64, from float copies of y and x = 1 - y that
+// follow the FP32 increments.  The transmitted and the absorbed time
+// integrals are summed apart, each accurate where it is small, and the
+// returned f is taken from the smaller: e^-tau in thick cells, 1 - absorbed
+// in thin ones; *absf is the absorbed fraction, f + absf = 1 up to rounding.
+// Fa = F / A, photoionisations per atom per second at full absorption.
+// ----------------------------------------------------------------------------
+static __device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau, float R0, float fc,
+                             float tol, int max_sub, int &nsub, int &capped, float &absf) {
+  double y = y_io;
+  float yf = (float)y, xf = (float)(1.0 - y);
+  nsub = 0;
+  capped = 0;
+  float t_left = dt, trans = 0.f, absd = 0.f;
+  while (t_left > 0.f) {
+    const float ty = tau * yf;
+    const float ab = -expm1f(-ty);  // absorbed fraction
+    const float tr = expf(-ty);     // transmitted fraction
+    const float ion = Fa * ab;
+    const float r0x = R0 * xf;
+    const float rec = r0x * xf;
+    float h = t_left;
+    if (yf > 0.f) {
+      const float den = ion + r0x * yf;
+      if (den > 0.f && fc * yf < den * t_left) h = __fdividef(fc * yf, den);
+    } else {
+      const float rate = Fa * tau + r0x;
+      if (rate > 0.f && fc < rate * t_left) h = __fdividef(fc, rate);
+    }
+    const float dy = (rec - ion) * h;
+    y += (double)dy;
+    yf += dy;
+    xf -= dy;
+    trans += tr * h;
+    absd += ab * h;
+    t_left = (h == t_left) ? 0.f : t_left - h;
+    nsub++;
+    const bool eq = fabsf(dy) <= tol * yf;
+    if (t_left > 0.f && (eq || nsub >= max_sub)) {
+      if (!eq) capped = 1;
+      trans += tr * t_left;
+      absd += ab * t_left;
+      t_left = 0.f;
+    }
+  }
+  y_io = y;
+  const float inv_dt = 1.f / dt;
+  const float fa = absd * inv_dt, ft = trans * inv_dt;
+  if (fa < ft) {
+    absf = fa;
+    return 1.f - fa;
+  }
+  absf = 1.f - ft;
+  return ft;
+}
+
+// ----------------------------------------------------------------------------
+// Mask words of one edge: bin b is bit b % 32 of word b / 32.  Memory holds
+// 1, 2 or 4 words per edge; 65..96 bins are handled as 3 words in registers
+// and kept at the 16-byte stride of 4 (the fourth word is zero).
+// ----------------------------------------------------------------------------
+template <int MW>
+__device__ __forceinline__ void load_mask(const uint32_t *__restrict__ M, int64_t e, uint32_t m[MW]) {
+  if constexpr (MW == 1) {
+    m[0] = __ldg(M + e);
+  } else if constexpr (MW == 2) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(M) + e);
+    m[0] = v.x; m[1] = v.y;
+  } else {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(M) + e);
+    m[0] = v.x; m[1] = v.y; m[2] = v.z;
+    if constexpr (MW == 4) m[3] = v.w;
+  }
+}
+template <int MW>
+__device__ __forceinline__ void store_mask(uint32_t *__restrict__ M, int64_t e, const uint32_t m[MW]) {
+  if constexpr (MW == 1) {
+    M[e] = m[0];
+  } else if constexpr (MW == 2) {
+    reinterpret_cast<uint2 *>(M)[e] = make_uint2(m[0], m[1]);
+  } else if constexpr (MW == 3) {
+    reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], 0u);  // 16-byte stride
+  } else {
+    reinterpret_cast<uint4 *>(M)[e] = make_uint4(m[0], m[1], m[2], m[3]);
+  }
+}
+
+// Row stride (elements) of the shared photon tile: odd, so that a lane per
+// vertex walking its own row touches 32 distinct banks.
+__host__ __device__ __forceinline__ int tile_stride(int nbins) { return nbins | 1; }
+
+// Per-lane budget accumulator: FP64 sum, or float-float in FP32 mode (the
+// FP64 pipe is narrow, so FP32-mode tiles combine their partial sums in
+// float-float and convert once).
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ void add(double x) { v = __dadd_rn(v, x); }
+};
+template <>
+struct Acc<float> {
+  FF v{0.f, 0.f};
+  __device__ void add(float x) { v = ff_add(v, x); }
+};
+
+// A budget term of one lane (the type of Acc<T>::v) and its sums.
+template <typename T>
+struct Bud;
+template <>
+struct Bud<double> {
+  using type = double;
+  __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ static double warp_sum(double v) { return warp_sum_d(v); }
+  __device__ static double to_double(double v) { return v; }
+  __device__ static double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+};
+template <>
+struct Bud<float> {
+  using type = FF;
+  __device__ static FF add(FF a, FF b) { return ff_add(a, b); }
+  __device__ static FF warp_sum(FF v) { return ff_warp_sum(v); }
+  __device__ static double to_double(FF v) { return ff_to_double(v); }
+  __device__ static FF shfl_xor(FF v, int o) {
+    return FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+  }
+};
+
+#ifndef SX_STEP_MIN_BLOCKS
+#define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
+#endif
+
+// A step kernel variant works on 32-vertex tiles with G consecutive vertices
+// per warp, so kTile / G warps per CTA: G = 4 (8 warps, 6 CTAs/SM) or G = 2
+// (16 warps, 3 CTAs/SM), both at 40 registers.
+template <int G>
+struct Shape {
+  static constexpr int kWarps = kTile / G;
+  static constexpr int kThreads = 32 * kWarps;
+  static constexpr int kMinBlocks = SX_STEP_MIN_BLOCKS * 8 / kWarps;
+  static constexpr int kCap = 18 * G;  // out-edges of a group staged at once in phase 3
+  static constexpr int kLanesPerVertex = 32 / G;
+};
+
+// One round of photon packets arriving at the vertices of a warp's group:
+// lane i adds `val` to bin `key & 127` of group vertex `key >> 7` (if `on`).
+// Lanes of equal key add in lane order, one rank at a time, so every bin
+// sums its packets in list order.  The rows start at zero.
+template <typename T, int MW>
+__device__ __forceinline__ void add_round(T *grow, int nbs, uint32_t (*gocc)[MW], bool on,
+                                          int key, T val, uint32_t lt_mask) {
+  const int k = on ? key : (1 << 12) + (int)(threadIdx.x & 31);  // idle lanes: unique keys
+  const uint32_t grp = __match_any_sync(0xffffffffu, k);
+  const unsigned rank = __popc(grp & lt_mask);
+  const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
+  T *dst = grow + (k >> 7) * nbs + (k & 127);
+  for (unsigned r = 0; r <= maxr; ++r) {
+    if (on && rank == r) *dst += val;
+    __syncwarp();
+  }
+  if (on) atomicOr(&gocc[k >> 7][(k & 127) >> 5], 1u << (k & 31));
+}
+
+// Bins 0..nbins-1 that fall in mask word w.
+__device__ __forceinline__ uint32_t word_bins(int nbins, int w) {
+  const int n = nbins - 32 * w;
+  return n >= 32 ? 0xffffffffu : (n <= 0 ? 0u : ((1u << n) - 1u));
+}
+
+}  // namespace sx

@@ -20,6 +20,7 @@ from . import build as _build
 
 SX_OK, SX_EINVAL, SX_ENOMEM, SX_ECUDA, SX_ESTATE, SX_ETIMEOUT = 0, -1, -2, -3, -4, -5
 SX_FP64, SX_FP32_TRANSPORT = 0, 1
+SX_TRANSPORT_DCT, SX_TRANSPORT_BALLISTIC, SX_TRANSPORT_COMBINED = 0, 1, 2
 SX_MAX_BINS = 128
 SX_MAX_DEGREE = 64
 SX_FLAG_SINK = 1
@@ -36,7 +37,8 @@ class sx_config(C.Structure):
     _fields_ = [("nbins", C.c_int32), ("precision", C.c_int32), ("seed", C.c_uint64),
                 ("sigma", C.c_double), ("alpha_B", C.c_double), ("kappa", C.c_double),
                 ("chem_frac", C.c_double), ("chem_tol", C.c_double),
-                ("chem_max_sub", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+                ("chem_max_sub", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
+                ("transport", C.c_int32), ("tau_switch", C.c_double)]
 
 
 class sx_budget(C.Structure):
@@ -379,7 +381,8 @@ class Batch:
 # Convenience: one grid with a torch-allocated device workspace
 # ---------------------------------------------------------------------------
 class Solver:
-    """A SimpleX2 DCT solve of one grid on one GPU.
+    """A SimpleX2 solve of one grid on one GPU: direction-conserving (default),
+    ballistic or combined transport (``transport``, ``tau_switch``).
 
     The workspace (per-grid device state) is a torch uint8 tensor on the
     context's device, so that memory comes from PyTorch's caching allocator;
@@ -389,7 +392,8 @@ class Solver:
     def __init__(self, bins: np.ndarray, precision: int = SX_FP32_TRANSPORT, seed: int = 0,
                  device: int = 0, stream=None, sigma: float = 6.3e-18, alpha_B: float = 2.59e-13,
                  kappa: float = 0.0, chem_frac: float = 0.5, chem_tol: float = 1e-5,
-                 chem_max_sub: int = 1000):
+                 chem_max_sub: int = 1000, transport: int = SX_TRANSPORT_DCT,
+                 tau_switch: float = 1.0):
         import torch
 
         self._torch = torch
@@ -405,6 +409,8 @@ class Solver:
         cfg.chem_frac = chem_frac
         cfg.chem_tol = chem_tol
         cfg.chem_max_sub = chem_max_sub
+        cfg.transport = transport
+        cfg.tau_switch = tau_switch
         cfg.device = device
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

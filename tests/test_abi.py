@@ -73,6 +73,18 @@ def test_argument_errors_without_gpu(libpath):
     with pytest.raises(S.SimplexError) as e:
         S.sx_create(cfg, I.fibonacci_bins(42))
     assert e.value.code == S.SX_EINVAL
+    cfg = S.sx_config_default()
+    assert cfg.transport == S.SX_TRANSPORT_DCT and cfg.tau_switch == 1.0
+    cfg.transport = 7
+    with pytest.raises(S.SimplexError) as e:
+        S.sx_create(cfg, I.fibonacci_bins(42))
+    assert e.value.code == S.SX_EINVAL and "transport" in str(e.value)
+    cfg = S.sx_config_default()
+    cfg.transport = S.SX_TRANSPORT_COMBINED
+    cfg.tau_switch = float("nan")
+    with pytest.raises(S.SimplexError) as e:
+        S.sx_create(cfg, I.fibonacci_bins(42))
+    assert e.value.code == S.SX_EINVAL
 
 
 def test_variant_and_autotune_argument_errors(libpath):
