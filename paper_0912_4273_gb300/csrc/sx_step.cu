@@ -807,9 +807,11 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_st
 }
 
 // Ballistic and combined transport: the same tiles with thick vertices (4
-// vertices per warp; the extra shared memory and registers allow 4 CTAs/SM).
+// vertices per warp), at 5 CTAs/SM (51 registers: a few bytes spill, and the
+// extra resident warps hide more of the dependent loads than 4 CTAs/SM at 64
+// registers do).
 template <typename T, int MW>
-__global__ void __launch_bounds__(Shape<4>::kThreads, 4) k_step_bal(const StepArgs a) {
+__global__ void __launch_bounds__(Shape<4>::kThreads, 5) k_step_bal(const StepArgs a) {
   step_tile<T, MW, 4, true>(a, a.tab, blockIdx.x, true, false);
 }
 
