@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "9408d42827a5df8b65a791e3803c7dc76b8885b1667185ae34cc6e3dc397fe04",
-               "bytes_per_launch": 1060.425e6 + 381.117e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "3efb7e2ce980e3a18904d02489045de6b5797a251f5667ba5c4cb1dd69bee2a7",
+               "bytes_per_launch": 1059.811e6 + 380.580e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------
@@ -573,6 +573,64 @@ def run_transport(args):
                       "warmup": args.warmup, **rows}), flush=True)
 
 
+def shadow_depth_profile(p, y, max_cells: int = 20):
+    """Ionised fraction (y < 0.5) of the vertices in the slab's geometric
+    shadow, behind it and inside 0.85 r_S, by their distance in cells from the
+    shadow cone's edge (bins of one cell); and the depth, in cells, of the
+    first bin that is mostly neutral (the front's penetration)."""
+    from paper_0912_4273_gb300 import inputs as I
+
+    lo, hi = np.array(p.meta["slab_lo"]), np.array(p.meta["slab_hi"])
+    c = p.pos[p.src_vertex[0]]
+    d = p.pos - c
+    rs = (3.0 * 5e48 / (4.0 * math.pi * I.ALPHA_B * 1e-6)) ** (1.0 / 3.0)
+    cell = p.box / int(p.meta["n_interior"]) ** (1.0 / 3.0)
+    near, far = lo[0] - c[0], hi[0] - c[0]
+    x = d[:, 0]
+    sel = (x > far + cell) & (np.linalg.norm(d, axis=1) < 0.85 * rs) & p.interior
+    depth = np.minimum(0.5 * (hi[1] - lo[1]) * x / near - np.abs(d[:, 1]),
+                       0.5 * (hi[2] - lo[2]) * x / near - np.abs(d[:, 2])) / cell
+    sel &= depth > 0
+    prof, pen = [], None
+    for k in range(max_cells):
+        m = sel & (depth >= k) & (depth < k + 1)
+        f = float((y[m] < 0.5).mean()) if m.any() else None
+        prof.append(f)
+        if pen is None and f is not None and f < 0.5:
+            pen = k
+    return prof, pen
+
+
+def run_shadow(args):
+    """Test 2 (Sect. 5.2): a point source and a slab 200 times denser than its
+    surroundings, 500 Myr at dt = 0.5 Myr, FP32 transport, on the Test-1 grid
+    at --shadow-res^3 points; 42 and 84 bins, and ballistic transport.
+    Reports, by depth in cells into the slab's shadow, the ionised fraction,
+    and the penetration depth (the paper: about 5 cells at 64^3; 8 (84 bins)
+    and 15 (42 bins) at 128^3)."""
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    n = args.shadow_res ** 3
+    t0 = time.perf_counter()
+    p = I.cached(I.shadow_problem, n, seed=args.seed)
+    t_grid = time.perf_counter() - t0
+    out = {}
+    for name, tp, nb in (("dct_84", S.SX_TRANSPORT_DCT, 84), ("dct_42", S.SX_TRANSPORT_DCT, 42),
+                         ("ballistic", S.SX_TRANSPORT_BALLISTIC, 84)):
+        s = S.Solver(I.fibonacci_bins(nb), precision=S.SX_FP32_TRANSPORT, seed=args.seed,
+                     transport=tp).load(p)
+        t0 = time.perf_counter()
+        s.step(0.5 * I.MYR_S, 1000)
+        y = s.y
+        el = time.perf_counter() - t0
+        s.close()
+        prof, pen = shadow_depth_profile(p, y)
+        out[name] = {"penetration_cells": pen, "ionised_fraction_by_depth": prof, "seconds": el}
+    print(json.dumps({"mode": "shadow", "resolution": args.shadow_res, "n_vertices": p.n,
+                      "grid_build_s": t_grid, **out}), flush=True)
+
+
 def run_clumpy(args):
     """The clumpy medium (2^22 points by default, lognormal density on a 128^3
     mesh, 16 sources, 84 bins, FP32 transport, dt = 0.5 Myr) with the dynamic
@@ -647,8 +705,9 @@ def main(argv=None):
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport"],
+    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport", "shadow"],
                     default="step")
+    ap.add_argument("--shadow-res", type=int, default=128)
     ap.add_argument("--clumpy-n", type=int, default=1 << 22)
     ap.add_argument("--clumpy-steps", type=int, default=200)
     ap.add_argument("--update-every", type=int, default=50)
@@ -675,6 +734,9 @@ def main(argv=None):
         return
     if args.mode == "transport":
         run_transport(args)
+        return
+    if args.mode == "shadow":
+        run_shadow(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

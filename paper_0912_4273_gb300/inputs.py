@@ -310,6 +310,29 @@ def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13
                    simplices=g.simplices)
 
 
+def shadow_problem(n_interior: int = 64 ** 3, seed: int = 0, contrast: float = 200.0,
+                   slab_pc=(855.0, 2138.0, 2138.0), distance_pc: float = 1096.0,
+                   **stromgren_kw) -> Problem:
+    """Shadowing behind a dense clump (Test 2 of Sect. 5.2): the Test-1 grid
+    and source, with a uniform rectangular slab `contrast` times denser than
+    its surroundings, `slab_pc` in size (x, y, z), its near face
+    `distance_pc` from the source along +x and centred on the source's line
+    of sight.  The paper prints the sizes in kpc, which cannot fit a
+    13.2 kpc box: they are read as pc.  The grid is sampled uniformly, as in
+    Test 1."""
+    p = stromgren_problem(n_interior, seed=seed, **stromgren_kw)
+    c = p.pos[p.src_vertex[0]]
+    pc = KPC_CM / 1e3
+    lo = c + np.array([distance_pc * pc, -0.5 * slab_pc[1] * pc, -0.5 * slab_pc[2] * pc])
+    hi = lo + np.array(slab_pc) * pc
+    inside = np.all((p.pos >= lo) & (p.pos <= hi), axis=1) & p.interior
+    nH = p.nH.copy()
+    nH[inside] *= contrast
+    meta = dict(p.meta, kind="shadow", contrast=contrast, slab_pc=list(slab_pc),
+                distance_pc=distance_pc, slab_lo=lo.tolist(), slab_hi=hi.tolist())
+    return dataclasses.replace(p, nH=nH, meta=meta)
+
+
 def survivor_problem(problem: Problem, removed) -> tuple:
     """The grid of the vertices that survive a removal (Sect. 2.1.4): the
     survivors in their old order, re-triangulated by QHull, with their media,
