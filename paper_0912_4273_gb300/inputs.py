@@ -270,11 +270,32 @@ def lognormal_density(mesh: int = 128, sigma_ln: float = 1.5, slope: float = -3.
     return nbar * np.exp(sigma_ln * d - 0.5 * sigma_ln**2)
 
 
+def hybrid_sampling(n, n0, alpha: float, d: int = 3):
+    """The sampling function of Eq. realistic_sampling: the harmonic mean of
+    (n/n0)^d and (n/n0)^alpha, so that densities below the reference n0 are
+    sampled to the d-th power (edge length proportional to the mean free
+    path, Eq. delaunay_vs_mfp) and those above it to the power alpha < d
+    (not undersampling the low-density regions)."""
+    y = np.asarray(n, dtype=np.float64) / n0
+    return 1.0 / (y ** (-float(d)) + y ** (-float(alpha)))
+
+
+def sampling_gradient_ratio(y, alpha: float, d: int = 3):
+    """Q_n / Q_y of the hybrid sampling at y = n / n0 (the relation below
+    Eq. realistic_sampling): how much flatter the point density is than the
+    medium density."""
+    y = np.asarray(y, dtype=np.float64)
+    return (y ** (-alpha) + y ** (-float(d))) / (y * (alpha * y ** (-alpha - 1.0) + d * y ** (-d - 1.0)))
+
+
 def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13.2,
                    nbar: float = 1e-3, sigma_ln: float = 1.5, nsrc: int = 16, seed: int = 0,
-                   margin_spacings: float = 1.5) -> Problem:
+                   margin_spacings: float = 1.5, sampling: str = "cbrt", alpha: float = 0.3,
+                   n0: float | None = None) -> Problem:
     """Clumpy medium: a lognormal density on a mesh^3 grid, vertices drawn with
-    probability ~ n^(1/3) per cell and placed uniformly inside their cell
+    probability ~ n^(1/3) per cell (or, with sampling="hybrid", the paper's
+    hybrid sampling function of n with reference density n0, default nbar,
+    and power alpha) and placed uniformly inside their cell
     (n_H of the cell, nearest grid point), a sink shell around the box, and
     nsrc sources at the centres of the nsrc densest cells with rates
     log-uniform in [1e47, 1e49] photons/s."""
@@ -282,7 +303,12 @@ def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13
     rho = lognormal_density(mesh, sigma_ln, -3.0, nbar, seed)
     L = box_kpc * KPC_CM
     h = L / mesh
-    w = np.cbrt(rho).ravel()
+    if sampling == "cbrt":
+        w = np.cbrt(rho).ravel()
+    elif sampling == "hybrid":  # Eq. realistic_sampling with d = 3
+        w = hybrid_sampling(rho, nbar if n0 is None else n0, alpha).ravel()
+    else:
+        raise ValueError("sampling must be 'cbrt' or 'hybrid'")
     counts = rng.multinomial(n_points - nsrc, w / w.sum())
     cell = np.repeat(np.arange(mesh**3), counts)
     ijk = np.stack(np.unravel_index(cell, (mesh,) * 3), axis=1)
@@ -306,7 +332,8 @@ def clumpy_problem(n_points: int = 1 << 22, mesh: int = 128, box_kpc: float = 13
     return Problem(pos=allp, row_ptr=g.row_ptr, col=g.col, nH=nh[order], volume=g.volume,
                    flags=flags[order], src_vertex=inv[:nsrc].astype(np.int32), src_rate=rates,
                    box=L, meta=dict(kind="clumpy", n_points=n_points, mesh=mesh, box_kpc=box_kpc,
-                                    nbar=nbar, sigma_ln=sigma_ln, nsrc=nsrc, seed=seed),
+                                    nbar=nbar, sigma_ln=sigma_ln, nsrc=nsrc, seed=seed,
+                                    sampling=sampling, alpha=alpha, n0=n0),
                    simplices=g.simplices)
 
 

@@ -46,3 +46,43 @@ def test_clumpy_problem_samples_density_to_the_third():
     cnt = np.bincount(np.ravel_multi_index(ijk.T, (16,) * 3), minlength=16**3)
     w = np.cbrt(rho.ravel())
     assert np.corrcoef(cnt, w)[0, 1] > 0.6
+
+
+def test_hybrid_sampling_function():
+    """Eq. realistic_sampling: the d-th power of n/n0 below the reference
+    density, the power alpha above it, 1/2 at n0; Q_n/Q_y (the relation
+    below it) is the inverse logarithmic slope of the sampling function."""
+    n0, a = 3.69e-5, 0.3
+    lo = np.array([1e-4, 1e-3]) * n0
+    hi = np.array([1e3, 1e4]) * n0
+    np.testing.assert_allclose(I.hybrid_sampling(lo, n0, a), (lo / n0) ** 3, rtol=1e-2)
+    np.testing.assert_allclose(I.hybrid_sampling(hi, n0, a), (hi / n0) ** a, rtol=1e-2)
+    assert I.hybrid_sampling(n0, n0, a) == pytest.approx(0.5)
+    y = np.geomspace(1e-3, 1e3, 25)
+    eps = 1e-6
+    slope = (np.log(I.hybrid_sampling(y * (1 + eps), 1.0, a)) - np.log(I.hybrid_sampling(y * (1 - eps), 1.0, a))) / (
+        np.log(1 + eps) - np.log(1 - eps))
+    np.testing.assert_allclose(I.sampling_gradient_ratio(y, a), 1.0 / slope, rtol=1e-6)
+    # the limits of that ratio: 1/d well below n0, 1/alpha well above
+    assert I.sampling_gradient_ratio(1e-6, a) == pytest.approx(1 / 3, rel=1e-3)
+    assert I.sampling_gradient_ratio(1e6, a) == pytest.approx(1 / a, rel=1e-3)
+
+
+def test_clumpy_problem_with_hybrid_sampling():
+    n0 = 1e-3
+    p = I.clumpy_problem(20000, mesh=16, nsrc=16, seed=3, sampling="hybrid", alpha=0.3, n0=n0)
+    rho = I.lognormal_density(16, 1.5, -3.0, 1e-3, seed=3)
+    h = p.box / 16
+    ijk = np.clip((p.pos[p.interior] / h).astype(int), 0, 15)
+    cnt = np.bincount(np.ravel_multi_index(ijk.T, (16,) * 3), minlength=16**3)
+    w = I.hybrid_sampling(rho.ravel(), n0, 0.3)
+    assert np.corrcoef(cnt, w)[0, 1] > 0.6
+    # low-density cells (below n0, sampled to the third power) hold fewer
+    # points than with n^(1/3) sampling
+    q = I.clumpy_problem(20000, mesh=16, nsrc=16, seed=3)
+    ijk = np.clip((q.pos[q.interior] / h).astype(int), 0, 15)
+    cq = np.bincount(np.ravel_multi_index(ijk.T, (16,) * 3), minlength=16**3)
+    low = rho.ravel() < 0.1 * n0
+    assert cnt[low].sum() < 0.5 * cq[low].sum()
+    with pytest.raises(ValueError):
+        I.clumpy_problem(1000, mesh=8, sampling="square")
