@@ -98,3 +98,62 @@ def test_direction_conserving_only_calls_are_refused(grid, tmp_path):
     s.close()
     with pytest.raises(S.SimplexError):
         S.Solver(bins, transport=7)
+
+
+def _star(narms=64):
+    """A source at the centre with narms arms of two vertices (inner at 1 kpc,
+    outer at 2 kpc, the outer ones sinks): the centre has the largest degree
+    a non-sink vertex may have."""
+    d = I.fibonacci_bins(narms)
+    pos = np.concatenate([np.zeros((1, 3)), d * I.KPC_CM, 2 * d * I.KPC_CM])
+    n = len(pos)
+    nbr = [list(range(1, narms + 1))]
+    nbr += [[0, narms + i] for i in range(1, narms + 1)]
+    nbr += [[i] for i in range(1, narms + 1)]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum([len(x) for x in nbr])
+    col = np.concatenate([np.sort(x) for x in nbr]).astype(np.int32)
+    flags = np.zeros(n, dtype=np.uint8)
+    flags[narms + 1:] = I.FLAG_SINK
+    return I.Problem(pos=pos, row_ptr=row_ptr, col=col, nH=np.full(n, 1e-3),
+                     volume=np.full(n, (0.5 * I.KPC_CM) ** 3), flags=flags,
+                     src_vertex=np.array([0], dtype=np.int32), src_rate=np.array([5e48]),
+                     box=4 * I.KPC_CM, meta=dict(kind="star"))
+
+
+@pytest.mark.parametrize("transport", [S.SX_TRANSPORT_DCT, BAL, COMB])
+@pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
+                                                 (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
+def test_largest_degree_and_empty_straight_sets(transport, precision, ytol, btol):
+    """The centre (degree 64) fills a thick vertex's 64 in-edge slots and both
+    halves of the warp in the send; an inner arm vertex sends nothing back
+    towards the centre (its only other edge is beyond 90 degrees of the
+    incoming direction, so photons from outside escape)."""
+    prob = _star()
+    assert np.diff(prob.row_ptr)[0] == 64
+    bins = I.fibonacci_bins(42)
+    ref = O.OracleSim(prob, O.Params(nbins=42, seed=4, transport=transport, tau_switch=1.0), bins)
+    s = S.Solver(bins, precision=precision, seed=4, kappa=ref.kappa, transport=transport,
+                 tau_switch=1.0).load(prob)
+    for steps in (1, 2, 9):
+        ref.step(DT, steps)
+        s.step(DT, steps)
+        assert np.abs(s.y - ref.y).max() <= ytol
+        assert _budget_err(s.budget, ref.budget) <= btol
+        assert np.abs(s.photons() - ref.photons()).max() <= btol * ref.budget["emitted"]
+    s.close()
+
+
+@pytest.mark.parametrize("nbins", [21, 128])
+def test_mask_word_counts(grid, nbins):
+    """One and four mask words (21 and 128 bins) through the thick-vertex
+    paths of combined transport, FP64."""
+    bins = I.fibonacci_bins(nbins)
+    ref = O.OracleSim(grid, O.Params(nbins=nbins, seed=5, transport=COMB, tau_switch=1.0), bins)
+    s = S.Solver(bins, precision=S.SX_FP64, seed=5, kappa=ref.kappa, transport=COMB,
+                 tau_switch=1.0).load(grid)
+    ref.step(DT, 25)
+    s.step(DT, 25)
+    assert np.abs(s.y - ref.y).max() <= 1e-9
+    assert _budget_err(s.budget, ref.budget) <= 1e-9
+    s.close()

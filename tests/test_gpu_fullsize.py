@@ -118,3 +118,34 @@ def test_thousand_steps(grid, oracle_setup):
     assert np.abs(y32 - s64.y).max() <= 1e-4
     assert abs(budget_residual(s64.budget)) <= 1e-10
     s64.close()
+
+
+def test_combined_transport_full_size(grid, oracle_setup):
+    """Combined transport (tau_switch = 1) on the full grid, FP32: the
+    chemistry of sampled vertices one by one against the oracle (whatever a
+    vertex's mode, the photons in flight towards it are its N_in of the next
+    step), the photon budget, and 0 <= y <= 1."""
+    bins, _, ref = oracle_setup
+    A, tau, R0 = ref.vertex_consts()
+    s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa,
+                 transport=S.SX_TRANSPORT_COMBINED, tau_switch=1.0).load(grid)
+    ordinary = grid.interior.copy()
+    ordinary[grid.src_vertex] = False
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    done = 0
+    for stop in (150, 300):
+        s.step(DT, stop - done)
+        y_prev, n_in = s.y, s.photons()
+        s.step(DT, 1)
+        done = stop + 1
+        y_new = s.y
+        lit = np.flatnonzero(ordinary & (n_in > 0))
+        for v in rng.choice(lit, size=min(2000, len(lit)), replace=False):
+            y_or, _, _, _ = O.chem(float(y_prev[v]), float(n_in[v]), DT, float(A[v]),
+                                   float(tau[v]), float(R0[v]))
+            worst = max(worst, abs(y_new[v] - y_or))
+        assert worst <= 1e-4, (stop, worst)
+        assert y_new.min() >= 0.0 and y_new.max() <= 1.0
+        assert abs(budget_residual(s.budget)) <= 1e-5
+    s.close()
