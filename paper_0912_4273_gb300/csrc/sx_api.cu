@@ -12,6 +12,20 @@
 #include "simplexgb.h"
 #include "sx_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+// A named NVTX range over a call of the C ABI: profilers (nsys, ncu --nvtx)
+// see the library's calls around its kernels; without one attached a range
+// costs nothing.
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
+
 struct sx_ctx {
   sx_config cfg;
   cudaStream_t stream = nullptr;
@@ -307,6 +321,7 @@ int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes
 int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr,
                  const int32_t *col, const double *nH, const double *volume, const uint8_t *flags,
                  const double *y0, void *d_workspace, int64_t workspace_bytes) {
+  NvtxRange nvtx_range_("sx_load_grid");
   if (!c) return SX_EINVAL;
   c->loaded = false;
   if (c->graph) {
@@ -333,6 +348,7 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
 
 int sx_grid_update_mark(sx_ctx *c, double y_thresh, double min_spacing, int32_t *removed,
                         int64_t *n_removed) {
+  NvtxRange nvtx_range_("sx_grid_update_mark");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "the dynamic grid update")) return rc;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
@@ -363,6 +379,7 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
                          const int32_t *col, const double *nH, const double *volume,
                          const uint8_t *flags, const int32_t *old_of_new, void *d_workspace,
                          int64_t workspace_bytes) {
+  NvtxRange nvtx_range_("sx_grid_update_apply");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "the dynamic grid update")) return rc;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
@@ -524,6 +541,7 @@ static int step_direct(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets)
 extern "C" {
 
 int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
+  NvtxRange nvtx_range_("sx_step");
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
@@ -568,6 +586,7 @@ int sx_step(sx_ctx *c, double dt, int32_t nsteps) {
 }
 
 int sx_step_budgets(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets) {
+  NvtxRange nvtx_range_("sx_step_budgets");
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail(c, SX_EINVAL, "dt must be > 0 and nsteps >= 0");
@@ -579,6 +598,7 @@ int sx_step_budgets(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets) {
 }
 
 int sx_sync(sx_ctx *c) {
+  NvtxRange nvtx_range_("sx_sync");
   if (!c) return SX_EINVAL;
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
   SX_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -586,6 +606,7 @@ int sx_sync(sx_ctx *c) {
 }
 
 int sx_read_neutral_fraction(sx_ctx *c, double *y_out) {
+  NvtxRange nvtx_range_("sx_read_neutral_fraction");
   if (!c || !y_out) return fail(c, SX_EINVAL, "NULL argument");
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
@@ -668,6 +689,7 @@ int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz) {
 }
 
 int sx_save(sx_ctx *c, const char *path) {
+  NvtxRange nvtx_range_("sx_save");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "a checkpoint")) return rc;
   if (!path) return fail(c, SX_EINVAL, "NULL path");
@@ -723,6 +745,7 @@ int sx_save(sx_ctx *c, const char *path) {
 }
 
 int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace_bytes) {
+  NvtxRange nvtx_range_("sx_restore");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "a checkpoint")) return rc;
   if (!path || !d_workspace) return fail(c, SX_EINVAL, "NULL argument");
@@ -814,6 +837,7 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
 }
 
 int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {
+  NvtxRange nvtx_range_("sx_read_photons");
   if (!c) return SX_EINVAL;
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
@@ -888,6 +912,7 @@ int sx_get_variant(sx_ctx *c, int32_t *variant) {
 
 int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scratch_bytes,
                 sx_tune_result *out) {
+  NvtxRange nvtx_range_("sx_autotune");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "the autotuner")) return rc;
   if (!out || !scratch) return fail(c, SX_EINVAL, "NULL argument");
@@ -1022,6 +1047,7 @@ int sx_batch_create(int32_t max_grids, int32_t device, void *stream, void *d_wor
   } while (0)
 
 int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_s, int32_t nsteps) {
+  NvtxRange nvtx_range_("sx_batch_step");
   if (!b) return SX_EINVAL;
   if (!ctxs || !dt_s || n < 1 || n > b->max_grids || nsteps < 0)
     return bfail(b, SX_EINVAL, "bad arguments");

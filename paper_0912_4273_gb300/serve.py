@@ -22,8 +22,10 @@ count, a time step and a number of steps.  The server
     its workspace and records its latency (finish - arrival).
 
 Failures are handled on the host: a request larger than the whole budget is
-rejected, a load error fails that request only and returns its memory, and a
-request can be cancelled while it waits or runs.
+rejected, a load error fails that request only and returns its memory, a
+chunk whose step fails (the worker "crashes") releases its requests and puts
+them back at the head of the queue to start over, up to ``max_retries``
+times, and a request can be cancelled while it waits or runs.
 
 The device work goes through a backend object; ``GpuBackend`` is the real one
 (the C ABI through ``simplex``); the tests drive the scheduling logic on the
@@ -56,6 +58,7 @@ class Request:
     budget: Optional[dict] = None
     t_admit: float = float("nan")
     t_done: float = float("nan")
+    retries: int = 0           # restarts after a failed chunk
 
     @property
     def nbins(self) -> int:
@@ -135,7 +138,7 @@ class Server:
     def __init__(self, backend, hbm_budget: int, chunk_steps: int = 8, max_grids: int = 256,
                  clock: Callable[[], float] = time.perf_counter, first_fit: bool = True,
                  fill_vertices: Optional[int] = DEFAULT_FILL_VERTICES,
-                 max_wait_s: Optional[float] = DEFAULT_MAX_WAIT_S):
+                 max_wait_s: Optional[float] = DEFAULT_MAX_WAIT_S, max_retries: int = 1):
         self.backend = backend
         self.budget = int(hbm_budget)
         self.chunk = int(chunk_steps)
@@ -144,6 +147,7 @@ class Server:
         self.first_fit = first_fit
         self.fill = None if fill_vertices is None else int(fill_vertices)
         self.max_wait = None if max_wait_s is None else float(max_wait_s)
+        self.max_retries = int(max_retries)
         self.pending: collections.deque = collections.deque()
         self.active: Dict[tuple, List[list]] = collections.defaultdict(list)  # key -> [[req, solver, done, bytes]]
         self.used = 0
@@ -253,7 +257,11 @@ class Server:
             sel = self._select(lst)
             n = min(self.chunk, min(ent[0].steps - ent[2] for ent in sel))
             if n > 0:
-                self.backend.step(key, [ent[1] for ent in sel], [ent[0].dt for ent in sel], n)
+                try:
+                    self.backend.step(key, [ent[1] for ent in sel], [ent[0].dt for ent in sel], n)
+                except Exception as e:  # the chunk failed: its requests start over
+                    self._restart(lst, sel, str(e))
+                    continue
                 for ent in sel:
                     ent[2] += n
             done = [ent for ent in sel if ent[2] >= ent[0].steps]
@@ -269,6 +277,30 @@ class Server:
                 req.t_done = self.now()
                 self.used -= ent[3]
                 self.finished.append(req)
+
+    def _restart(self, lst: List[list], sel: List[list], why: str):
+        """Release the grids of a failed chunk; requeue their requests at the
+        head of the queue (or fail those out of retries)."""
+        requeue = []
+        for ent in sel:
+            lst.remove(ent)
+            try:
+                self.backend.release(ent[1])
+            except Exception:
+                pass
+            self.used -= ent[3]
+            req = ent[0]
+            req.error = why
+            if req.retries < self.max_retries:
+                req.retries += 1
+                req.status = "pending"
+                requeue.append(req)
+            else:
+                req.status = "failed"
+                req.t_done = self.now()
+                self.finished.append(req)
+        for req in sorted(requeue, key=lambda r: (r.arrival, r.rid), reverse=True):
+            self.pending.appendleft(req)
 
     def run(self, requests=(), idle_sleep: float = 1e-4) -> List[Request]:
         """Serve ``requests`` (plus anything submitted before) to completion."""

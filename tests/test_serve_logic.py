@@ -128,6 +128,41 @@ def test_a_request_past_the_maximum_wait_goes_first():
     assert t[0] < t[1]
 
 
+class CrashingBackend(FakeBackend):
+    """The step of chunk number `crash_at` fails (a worker crash)."""
+
+    def __init__(self, crash_at, times=1):
+        super().__init__()
+        self.calls = 0
+        self.crash_at = crash_at
+        self.times = times
+
+    def step(self, key, solvers, dts, n):
+        self.calls += 1
+        if self.crash_at <= self.calls < self.crash_at + self.times:
+            raise RuntimeError("worker crashed")
+        super().step(key, solvers, dts, n)
+
+
+def test_a_crashed_chunk_restarts_its_requests():
+    be = CrashingBackend(crash_at=2)
+    srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock())
+    out = srv.run([req(0, 100, 12), req(1, 200, 9)])
+    by = {r.rid: r for r in out}
+    assert all(r.status == "done" for r in out)
+    # restarted from a fresh load: exactly its steps, once more loaded
+    assert all(r.y[0] == r.steps for r in out)
+    assert all(r.retries == 1 and "crashed" in r.error for r in out)
+    assert sorted(be.loaded) == [0, 0, 1, 1]
+    assert srv.used == 0
+    # out of retries: failed, memory returned
+    be = CrashingBackend(crash_at=1, times=10)
+    srv = SV.Server(be, hbm_budget=10**9, chunk_steps=4, clock=Clock(), max_retries=2)
+    out = srv.run([req(0, 100, 12)])
+    assert out[0].status == "failed" and out[0].retries == 2 and srv.used == 0
+    assert be.released.count(0) == 3
+
+
 def test_rejection_failure_and_cancellation():
     be = FakeBackend(fail_rids={1})
     srv = SV.Server(be, hbm_budget=100 * 1000, clock=Clock())
