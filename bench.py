@@ -52,8 +52,8 @@ WORKLOADS = {
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, the launch of step 300), valid only for the kernel
 # source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "3efb7e2ce980e3a18904d02489045de6b5797a251f5667ba5c4cb1dd69bee2a7",
-               "bytes_per_launch": 1059.811e6 + 380.580e6, "workload": "c1"}
+NCU_TRAFFIC = {"sx_step.cu_sha256": "2eef7a061f5b79cf43abb99d798f8549935d5ede867458a77947c88eec8b7e94",
+               "bytes_per_launch": 1059.800e6 + 380.462e6, "workload": "c1"}
 
 
 # ---------------------------------------------------------------------------

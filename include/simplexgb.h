@@ -121,6 +121,8 @@ typedef struct {
     int32_t nsources;
     double step_kernel_ms;   /* summed duration of the timed step-kernel launches */
     int64_t step_kernel_launches;
+    int64_t index_errors;    /* debug builds (SX_DEBUG): indices the step kernels found out of
+                                range and skipped; always 0 in release builds, which do not check */
 } sx_info;
 
 /* Fill cfg with the Test-1 defaults of Sect. 5.1 (42 bins, FP32 transport,

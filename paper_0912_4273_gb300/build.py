@@ -14,6 +14,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")  # -DSX_DEBUG: the kernels check their indices
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBNAME = "libsimplexgb.so"
 SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_update.cu", "sx_noalloc.cu"]
@@ -29,8 +30,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def lib_path() -> str:
-    return os.path.join(BUILD, LIBNAME)
+def lib_path(debug: bool = False) -> str:
+    return os.path.join(BUILD_DEBUG if debug else BUILD, LIBNAME)
 
 
 def _stale(out: str, deps) -> bool:
@@ -40,15 +41,20 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile the library (with debug, a second build with -DSX_DEBUG into
+    its own folder); returns its path."""
+    bdir = BUILD_DEBUG if debug else BUILD
+    if debug:
+        extra = ["-DSX_DEBUG", *extra]
+    os.makedirs(bdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     objs = []
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [src, __file__] + headers):
             jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj])
@@ -58,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
             if verbose and (r.stdout or r.stderr):
                 print(r.stdout + r.stderr)
-    out = lib_path()
+    out = lib_path(debug)
     if force or jobs or _stale(out, objs):
         tmp = out + f".tmp{os.getpid()}"
         r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
@@ -71,5 +77,5 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 if __name__ == "__main__":
     import sys
 
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv,
                 extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))

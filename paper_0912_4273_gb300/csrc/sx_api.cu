@@ -998,6 +998,7 @@ int sx_get_info(sx_ctx *c, sx_info *info) {
   info->kappa = kappa;
   info->subcycles = (int64_t)diag[sx::kDiagSubcycles];
   info->capped = (int64_t)diag[sx::kDiagCapped];
+  info->index_errors = (int64_t)diag[sx::kDiagIndex];
   info->max_degree = c->max_degree;
   info->nsources = (int32_t)c->src_vertex.size();
   return SX_OK;

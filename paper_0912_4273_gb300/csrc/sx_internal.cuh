@@ -104,7 +104,21 @@ struct StepArgs {
   double tau_switch;
 };
 
-enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagCount = 8 };
+enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagIndex = 4,
+            kDiagCount = 8 };
+
+// Debug builds (-DSX_DEBUG) check the data-dependent indices of the step
+// kernels: an index out of range is counted in diag[kDiagIndex] and its
+// access skipped (never a trap).  Release builds do not evaluate the check.
+#ifdef SX_DEBUG
+__device__ __forceinline__ bool sx_index_ok(bool ok, unsigned long long *diag) {
+  if (!ok) atomicAdd(&diag[kDiagIndex], 1ull);
+  return ok;
+}
+#define SX_INDEX_OK(cond, diag) ::sx::sx_index_ok((cond), (diag))
+#else
+#define SX_INDEX_OK(cond, diag) true
+#endif
 
 // Error bits reported by the load kernels.
 enum : unsigned long long {

@@ -357,6 +357,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       T edge_val = T(0);  // BAL: a packet that a thick sender routed along this edge
       if (e < R[kGroup]) {
         my_src = a.col[e];
+        if (!SX_INDEX_OK((unsigned)my_src < (unsigned)a.n, a.diag)) my_src = 0;
         if constexpr (BAL) {
           if (a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
           else load_mask<MW>(M_prev, (int64_t)e, my_m);
@@ -374,7 +375,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
               }
               my_m[w] = 0u;
             }
-            s_E[g0 + g][e - R[g]] = acc + edge_val;
+            if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc + edge_val;
             edge_val = T(0);
           }
         } else {
@@ -422,7 +423,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         }
         int key = 0;
         T val = T(0);
-        if (on) {
+        if (on && SX_INDEX_OK(bo < nbins, a.diag)) {
           val = Pp[(size_t)src * nbp + bo];
           key = (gk << 7) | s_fwd[bo];
         }
@@ -678,7 +679,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
                 fly.add(O);
                 Pn[(size_t)(vg + g) * nbp + b] = P;
                 const uint32_t bit = 1u << (b & 31);
-                for (int m = 0; m < cnt; ++m) atomicOr(&s_am[ka + ((stw >> (8 * m)) & 0xFFu)][b >> 5], bit);
+                for (int m = 0; m < cnt; ++m) {
+                  const int sl = (int)((stw >> (8 * m)) & 0xFFu);
+                  if (SX_INDEX_OK(sl < dg && ka + sl < kGroupCap, a.diag)) atomicOr(&s_am[ka + sl][b >> 5], bit);
+                }
               }
             }
           }
@@ -690,7 +694,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         uint32_t m[MW];
 #pragma unroll
         for (int w = 0; w < MW; ++w) m[w] = idx < kGroupCap ? s_am[idx][w] : 0u;
-        store_mask<MW>(M_next, (int64_t)a.edges[e].twin, m);  // at the receiver's in-edge index
+        const int32_t tw = a.edges[e].twin;
+        if (SX_INDEX_OK((unsigned)tw < (unsigned)a.row_ptr[a.n], a.diag))
+          store_mask<MW>(M_next, (int64_t)tw, m);  // at the receiver's in-edge index
       }
       __syncwarp();
       ga = gb;
@@ -738,10 +744,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           const uint8_t *lst = a.binv + 3 * (int64_t)r0 + (ent & 0xFFu);
           const T *Eg = s_E[g0 + g];
           T acc = T(0);
-          for (unsigned i = 0; i < (ent >> 8); ++i) acc += Eg[lst[i]];
+          for (unsigned i = 0; i < (ent >> 8); ++i)
+            if (SX_INDEX_OK(lst[i] < dg, a.diag)) acc += Eg[lst[i]];
           const T S = s_S[g0 + g];
           if (S != T(0)) acc += (S * s_f[g0 + g]) / (T)dg;
-          Bn[a.edges[e].twin] = acc;
+          const int32_t tw = a.edges[e].twin;
+          if (SX_INDEX_OK((unsigned)tw < (unsigned)a.row_ptr[a.n], a.diag)) Bn[tw] = acc;
         }
       }
       // every vertex's mode of this step, for its receivers in the next

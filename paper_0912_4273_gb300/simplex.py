@@ -64,7 +64,7 @@ class sx_info(C.Structure):
                 ("workspace_bytes", C.c_int64), ("kappa", C.c_double),
                 ("subcycles", C.c_int64), ("capped", C.c_int64), ("max_degree", C.c_int32),
                 ("nsources", C.c_int32), ("step_kernel_ms", C.c_double),
-                ("step_kernel_launches", C.c_int64)]
+                ("step_kernel_launches", C.c_int64), ("index_errors", C.c_int64)]
 
 
 _LIB = None
