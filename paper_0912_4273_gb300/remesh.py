@@ -37,30 +37,46 @@ def _in_any_tet(p: np.ndarray, tets: np.ndarray, eps: float = 1e-9) -> np.ndarra
     return ok.any(axis=1)
 
 
-def _fill_cavity(pos: np.ndarray, v: int, star: np.ndarray):
-    """Tetrahedra (old vertex ids) that fill the cavity of v, whose star is
-    `star` (tetrahedra holding v), or None if they do not fill it."""
+def _fill_cavities(jobs):
+    """New tetrahedra of each cavity (global ids), or None where QHull
+    refuses: jobs are (link ids, link positions relative to the removed
+    vertex, the star's tetrahedra as relative corner positions)."""
     from scipy.spatial import Delaunay
 
-    link = np.unique(star[star != v])
-    if len(link) < 4:
-        return None
-    origin = pos[v]
-    p = pos[link] - origin  # coordinates relative to v: better conditioned
-    try:
-        cand = Delaunay(p).simplices
-    except Exception:  # QHull refuses (e.g. a flat neighbourhood)
-        return None
-    inside = _in_any_tet(p[cand].mean(axis=1), pos[star] - origin)
-    new = link[cand[inside]]
-    v_old = I.tet_volumes(pos, star).sum()
-    v_new = I.tet_volumes(pos, new).sum()
-    if not abs(v_new - v_old) <= 1e-9 * v_old:
-        return None
-    return new
+    out = []
+    for link, p, star_xyz in jobs:
+        if len(link) < 4:
+            out.append(None)
+            continue
+        try:
+            cand = Delaunay(p).simplices
+        except Exception:  # QHull refuses (e.g. a flat neighbourhood)
+            out.append(None)
+            continue
+        inside = _in_any_tet(p[cand].mean(axis=1), star_xyz)
+        out.append(link[cand[inside]])
+    return out
 
 
-def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True) -> tuple:
+_POOL = None
+
+
+def _pool(workers: int):
+    """Worker processes for the cavities, started once (spawned: the caller
+    may already hold a CUDA context, which a forked child must not inherit)."""
+    global _POOL
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    if _POOL is None or _POOL._max_workers != workers:
+        if _POOL is not None:
+            _POOL.shutdown()
+        _POOL = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    return _POOL
+
+
+def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True,
+                    workers: int | None = None) -> tuple:
     """The grid without the `removed` vertices (an independent set of the
     graph): survivors in their old order, their Delaunay graph, cell volumes
     (1/4 of the incident tetrahedra), media, flags, sources and tetrahedra.
@@ -68,7 +84,9 @@ def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True) -
 
     Needs the grid's tetrahedra (``problem.simplices``); a grid without them,
     or a cavity that cannot be filled locally, is rebuilt by QHull (or, with
-    ``allow_rebuild=False``, raises RuntimeError)."""
+    ``allow_rebuild=False``, raises RuntimeError).  The cavities are filled
+    by `workers` processes (default: the host's cores when there are more
+    than 256 cavities, else in this process)."""
 
     def rebuild(why):
         if not allow_rebuild:
@@ -83,47 +101,72 @@ def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True) -
     if np.any(rem[problem.src_vertex]):
         raise ValueError("sources are never removed")
     simp = np.asarray(problem.simplices)
-    hit = rem[simp]
-    cnt = hit.sum(axis=1)
+    hit = rem.view(np.uint8)[simp]
+    cnt = hit.sum(axis=1, dtype=np.uint8)
     if np.any(cnt > 1):
         raise ValueError("removed vertices must not be adjacent")
     star_ids = np.flatnonzero(cnt == 1)
     st = simp[star_ids].astype(np.int64)
-    owner = st[hit[star_ids]]
+    owner = st[hit[star_ids].astype(bool)]
     order = np.argsort(owner, kind="stable")
     st, owner = st[order], owner[order]
     cuts = np.flatnonzero(np.diff(owner)) + 1
     pos = problem.pos
-    new_tets = []
-    for grp, v in zip(np.split(st, cuts), owner[np.r_[0, cuts]] if len(owner) else []):
-        t = _fill_cavity(pos, int(v), grp)
+    vs = owner[np.r_[0, cuts]] if len(owner) else np.zeros(0, dtype=np.int64)
+    jobs = []
+    for grp, v in zip(np.split(st, cuts), vs):
+        link = np.unique(grp[grp != v])
+        origin = pos[v]  # coordinates relative to v: better conditioned
+        jobs.append((link, pos[link] - origin, pos[grp] - origin))
+    if workers is None:
+        import os
+
+        workers = min(16, os.cpu_count() or 1) if len(jobs) > 256 else 1
+    if workers > 1 and len(jobs) > 1:
+        nchunk = min(len(jobs), 4 * workers)
+        bounds = np.linspace(0, len(jobs), nchunk + 1).astype(int)
+        parts = _pool(workers).map(_fill_cavities, [jobs[i:j] for i, j in zip(bounds[:-1], bounds[1:])])
+        filled = [t for part in parts for t in part]
+    else:
+        filled = _fill_cavities(jobs)
+    for t, v in zip(filled, vs):
         if t is None:
             return rebuild(f"the cavity of vertex {int(v)} cannot be filled locally")
-        new_tets.append(t)
-    new = np.concatenate(new_tets) if new_tets else np.zeros((0, 4), dtype=np.int64)
+    new = np.concatenate(filled) if filled else np.zeros((0, 4), dtype=np.int64)
+    # every cavity's new tetrahedra fill its volume (a vertex on the hull does not)
+    if len(vs):
+        cav_of_new = np.repeat(np.arange(len(vs)), [len(t) for t in filled])
+        cav_of_old = np.repeat(np.arange(len(vs)), np.diff(np.r_[0, cuts, len(st)]))
+        v_old = np.bincount(cav_of_old, weights=I.tet_volumes(pos, st), minlength=len(vs))
+        v_new = np.bincount(cav_of_new, weights=I.tet_volumes(pos, new), minlength=len(vs))
+        bad = np.flatnonzero(~(np.abs(v_new - v_old) <= 1e-9 * v_old))
+        if len(bad):
+            return rebuild(f"the cavity of vertex {int(vs[bad[0]])} cannot be filled locally")
 
     # the graph: old edges without the removed vertices, plus the cavity
     # tetrahedra's edges not already present (keys src * n + dst, sorted)
     deg = np.diff(problem.row_ptr)
-    src = np.repeat(np.arange(n, dtype=np.int64), deg)
-    dst = problem.col.astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int32), deg)
+    dst = problem.col
     keep_e = ~(rem[src] | rem[dst])
-    key = src[keep_e] * n + dst[keep_e]
+    src, dst = src[keep_e], dst[keep_e]
+    key = src.astype(np.int64) * n + dst
     pairs = np.concatenate([new[:, [a, b]] for a, b in
                             ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
     add = np.unique(np.concatenate([pairs[:, 0] * n + pairs[:, 1], pairs[:, 1] * n + pairs[:, 0]]))
     at = np.searchsorted(key, add)
     present = (at < len(key)) & (key[np.minimum(at, len(key) - 1)] == add)
-    key = np.insert(key, at[~present], add[~present])
+    at, add = at[~present], add[~present]
+    src = np.insert(src, at, (add // n).astype(np.int32))
+    dst = np.insert(dst, at, (add % n).astype(np.int32))
 
     keep = np.flatnonzero(~rem)
-    new_of_old = np.full(n, -1, dtype=np.int64)
-    new_of_old[keep] = np.arange(len(keep))
     n2 = len(keep)
-    src2 = new_of_old[key // n]
-    col2 = new_of_old[key % n].astype(np.int32)
+    new_of_old = np.full(n, -1, dtype=np.int32)
+    new_of_old[keep] = np.arange(n2, dtype=np.int32)
+    col2 = new_of_old[dst]
     row_ptr2 = np.zeros(n2 + 1, dtype=np.int64)
-    np.cumsum(np.bincount(src2, minlength=n2), out=row_ptr2[1:])
+    np.cumsum(np.bincount(new_of_old[src], minlength=n2), out=row_ptr2[1:])
 
     # cell volumes: the cavity's old tetrahedra leave their vertices, the new
     # ones join theirs, a quarter each
@@ -131,10 +174,10 @@ def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True) -
     np.add.at(vol, st.ravel(), -np.repeat(I.tet_volumes(pos, st) * 0.25, 4))
     np.add.at(vol, new.ravel(), np.repeat(I.tet_volumes(pos, new) * 0.25, 4))
 
-    simp2 = np.concatenate([simp[cnt == 0].astype(np.int64), new])
+    simp2 = np.concatenate([new_of_old[simp[cnt == 0]], new_of_old[new]])
     p = I.Problem(pos=np.ascontiguousarray(pos[keep]), row_ptr=row_ptr2, col=col2,
                   nH=problem.nH[keep].copy(), volume=vol[keep], flags=problem.flags[keep].copy(),
                   src_vertex=new_of_old[problem.src_vertex].astype(np.int32),
                   src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta),
-                  simplices=new_of_old[simp2].astype(np.int32))
+                  simplices=simp2)
     return p, keep.astype(np.int32)

@@ -89,3 +89,13 @@ def test_removal_rules():
     q, _ = R.remove_vertices(p, rem)
     full, _ = I.survivor_problem(p, rem)
     _same_grid(q, full)
+
+
+def test_worker_processes_give_the_same_grid():
+    p = I.stromgren_problem(3000, seed=22)
+    rem = _independent_interior(p, 300, seed=5)
+    a, oa = R.remove_vertices(p, rem, allow_rebuild=False, workers=1)
+    b, ob = R.remove_vertices(p, rem, allow_rebuild=False, workers=2)
+    assert np.array_equal(oa, ob)
+    assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.volume, b.volume) and np.array_equal(a.simplices, b.simplices)
