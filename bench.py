@@ -257,7 +257,14 @@ def run_ours(args, wl, rank, world, local_rank):
     budget = solver.budget
     solver.close()
 
-    e2e = run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream) if not args.no_e2e else None
+    e2e = None
+    if not args.no_e2e:  # whole job: every rank's replica, the slowest rank's time
+        barrier(world, device)
+        e2e = run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream)
+        max_s = reduce_max(e2e["seconds"], world, device)
+        e2e.update(value=aggregate(n_int * wl["nbins"] * args.steps, world, max_s * 1e3),
+                   seconds=max_s, h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
+                   d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline(wl, prob, bins, dt, seed)
