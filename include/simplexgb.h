@@ -204,6 +204,35 @@ int sx_read_photons(sx_ctx *ctx, double *per_vertex, sx_budget *budget);
 /* Counters of the grid; synchronises the stream if kernel timing is on. */
 int sx_get_info(sx_ctx *ctx, sx_info *info);
 
+/* Host side of the dynamic grid update, Sect. 2.1.4: remove an independent set
+   of vertices (no two adjacent) from a Delaunay tetrahedralisation by
+   re-triangulating their cavities.  Each removed vertex's cavity (the union
+   of its tetrahedra) is filled with the Delaunay tetrahedra of its neighbours
+   that lie inside it, built by Bowyer-Watson insertion in host memory; the
+   graph, the cell volumes (1/4 of the incident tetrahedra) and the
+   tetrahedra are patched, and the survivors renumbered in their old order.
+     pos n x 3, row_ptr n + 1 (int64), col nnz (ascending rows, symmetric),
+     tets ntet x 4, volume n; removed nrem vertex ids.
+   On success *out holds the new grid in arrays this call allocates (free them
+   with sx_remesh_free).  A cavity whose new tetrahedra do not fill its
+   volume (a vertex on the convex hull, a degenerate neighbourhood) returns
+   SX_EINVAL with out->bad_vertex set: the caller rebuilds the grid instead.
+   Errors: SX_EINVAL (bad arguments, adjacent removed vertices: bad_vertex
+   -1), SX_ENOMEM.  No device memory or GPU is used. */
+typedef struct {
+    int64_t n, nnz, ntet;
+    int64_t *row_ptr;     /* n + 1 */
+    int32_t *col;         /* nnz */
+    double *volume;       /* n */
+    int32_t *tets;        /* ntet x 4 */
+    int32_t *old_of_new;  /* n: the old id of each survivor */
+    int32_t bad_vertex;   /* a removed vertex whose cavity could not be filled, or -1 */
+} sx_remesh_result;
+int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row_ptr, const int32_t *col,
+                     int64_t ntet, const int32_t *tets, const double *volume, int64_t nrem,
+                     const int32_t *removed, sx_remesh_result *out);
+void sx_remesh_free(sx_remesh_result *result);
+
 /* Dynamic grid, Sect. 2.1.4: where the optical depth fell, vertices are removed
    down to a minimum resolution and the survivors are re-triangulated.
    sx_grid_update_mark lists the vertices to remove: not sinks, not sources,

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")  # -DSX_DEBUG: the kernels check their indices
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBNAME = "libsimplexgb.so"
-SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_update.cu", "sx_noalloc.cu"]
+SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_update.cu", "sx_noalloc.cu", "sx_remesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE]
@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = Fa
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(bdir, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, os.path.splitext(s)[0] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, __file__] + headers):
             jobs.append([nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj])

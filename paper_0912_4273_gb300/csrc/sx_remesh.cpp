@@ -1,0 +1,365 @@
+// sx_remesh.cpp -- host side of the dynamic grid update (Sect. 2.1.4):
+// removes an independent set of vertices from a Delaunay tetrahedralisation
+// by re-triangulating their cavities, and patches the graph (CSR), the cell
+// volumes and the tetrahedra.
+//
+// Removing vertex v leaves a cavity, the union of the tetrahedra around v.
+// The tetrahedra outside keep their empty circumspheres, so the cavity is
+// filled by the Delaunay tetrahedra of v's neighbours (its link) that lie in
+// it.  The link's Delaunay tetrahedralisation is built here by Bowyer-Watson
+// insertion (tens of points), in coordinates relative to v; its tetrahedra
+// whose centroid lies in one of v's tetrahedra are kept, and they must fill
+// the cavity's volume (else the call reports the cavity and the caller
+// rebuilds the grid).  No two removed vertices are adjacent, so no
+// tetrahedron holds two of them and the cavities are filled independently.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "simplexgb.h"
+
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 sub(const V3 &a, const V3 &b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline double dot(const V3 &a, const V3 &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline V3 cross(const V3 &a, const V3 &b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+// 6 x the signed volume of (a, b, c, d): positive when d is on the side of
+// (a, b, c) that the right-hand rule points to
+inline double orient(const V3 &a, const V3 &b, const V3 &c, const V3 &d) {
+  return dot(cross(sub(b, a), sub(c, a)), sub(d, a));
+}
+// > 0 when e lies inside the circumsphere of the positively oriented (a, b, c, d)
+double insphere(const V3 &a, const V3 &b, const V3 &c, const V3 &d, const V3 &e) {
+  const V3 pa = sub(a, e), pb = sub(b, e), pc = sub(c, e), pd = sub(d, e);
+  const double la = dot(pa, pa), lb = dot(pb, pb), lc = dot(pc, pc), ld = dot(pd, pd);
+  // D = det of the 4 x 4 matrix with rows (p, |p|^2), by cofactors along the
+  // last column: D = -la det(pb,pc,pd) + lb det(pa,pc,pd) - lc det(pa,pb,pd)
+  // + ld det(pa,pb,pc); for a positively oriented tetrahedron D < 0 exactly
+  // when e is inside, so the result is -D
+  const double ob = dot(cross(pc, pd), pb), oa = dot(cross(pc, pd), pa), oc = dot(cross(pb, pd), pa),
+               od = dot(cross(pb, pc), pa);
+  return la * ob - lb * oa + lc * oc - ld * od;
+}
+
+struct Tet {
+  int v[4];
+};
+
+// Delaunay tetrahedralisation of m points by Bowyer-Watson insertion into a
+// bounding tetrahedron; tetrahedra are kept positively oriented.  Returns the
+// tetrahedra of the points (those without a bounding vertex).
+bool delaunay_small(const std::vector<V3> &pts, std::vector<Tet> &out) {
+  const int m = (int)pts.size();
+  double r = 0.0;
+  for (const V3 &p : pts) r = std::max(r, std::sqrt(dot(p, p)));
+  if (!(r > 0.0)) return false;
+  std::vector<V3> P(pts);
+  const double s = 64.0 * r;  // the bounding tetrahedron, far outside
+  P.push_back({-s, -s, -s});
+  P.push_back({3 * s, -s, -s});
+  P.push_back({-s, 3 * s, -s});
+  P.push_back({-s, -s, 3 * s});
+  std::vector<Tet> T;
+  T.push_back({{m, m + 1, m + 2, m + 3}});
+  if (orient(P[m], P[m + 1], P[m + 2], P[m + 3]) < 0) std::swap(T[0].v[0], T[0].v[1]);
+  std::vector<char> bad;
+  struct Face {
+    int a, b, c;
+  };
+  std::vector<Face> faces;
+  for (int i = 0; i < m; ++i) {
+    bad.assign(T.size(), 0);
+    bool any = false;
+    for (size_t t = 0; t < T.size(); ++t) {
+      const Tet &q = T[t];
+      if (insphere(P[q.v[0]], P[q.v[1]], P[q.v[2]], P[q.v[3]], P[i]) > 0) {
+        bad[t] = 1;
+        any = true;
+      }
+    }
+    if (!any) return false;
+    // the cavity's boundary: faces of bad tetrahedra not shared with another
+    // bad one, oriented as seen from inside the bad tetrahedron
+    faces.clear();
+    for (size_t t = 0; t < T.size(); ++t) {
+      if (!bad[t]) continue;
+      const int *v = T[t].v;
+      const int f[4][3] = {{v[1], v[2], v[3]}, {v[0], v[3], v[2]}, {v[0], v[1], v[3]}, {v[0], v[2], v[1]}};
+      for (int k = 0; k < 4; ++k) {
+        int key[3] = {f[k][0], f[k][1], f[k][2]};
+        std::sort(key, key + 3);
+        bool shared = false;
+        for (size_t u = 0; u < T.size() && !shared; ++u) {
+          if (u == t || !bad[u]) continue;
+          const int *w = T[u].v;
+          int c = 0;
+          for (int a = 0; a < 4; ++a) c += (w[a] == key[0]) + (w[a] == key[1]) + (w[a] == key[2]);
+          shared = c == 3;
+        }
+        if (!shared) faces.push_back({f[k][0], f[k][1], f[k][2]});
+      }
+    }
+    std::vector<Tet> keep;
+    keep.reserve(T.size() + faces.size());
+    for (size_t t = 0; t < T.size(); ++t)
+      if (!bad[t]) keep.push_back(T[t]);
+    for (const Face &f : faces) {
+      // (a, b, c) faces outward from the removed tetrahedron's interior, so
+      // the new point on its inner side gives orient(a, c, b, i) > 0
+      Tet q{{f.a, f.c, f.b, i}};
+      if (!(orient(P[q.v[0]], P[q.v[1]], P[q.v[2]], P[q.v[3]]) > 0)) return false;
+      keep.push_back(q);
+    }
+    T.swap(keep);
+  }
+  out.clear();
+  for (const Tet &q : T)
+    if (q.v[0] < m && q.v[1] < m && q.v[2] < m && q.v[3] < m) out.push_back(q);
+  return true;
+}
+
+// Whether point p lies in tetrahedron (a, b, c, d) (barycentric, with slack).
+bool in_tet(const V3 &p, const V3 &a, const V3 &b, const V3 &c, const V3 &d) {
+  const double vol = orient(a, b, c, d);
+  if (vol == 0.0) return false;
+  const double eps = -1e-9 * std::fabs(vol);
+  const double l0 = orient(p, b, c, d), l1 = orient(a, p, c, d), l2 = orient(a, b, p, d),
+               l3 = orient(a, b, c, p);
+  if (vol > 0) return l0 >= eps && l1 >= eps && l2 >= eps && l3 >= eps;
+  return l0 <= -eps && l1 <= -eps && l2 <= -eps && l3 <= -eps;
+}
+
+double tet_volume(const double *pos, const int32_t *t) {
+  const V3 a{pos[3 * (int64_t)t[0]], pos[3 * (int64_t)t[0] + 1], pos[3 * (int64_t)t[0] + 2]};
+  const V3 b{pos[3 * (int64_t)t[1]], pos[3 * (int64_t)t[1] + 1], pos[3 * (int64_t)t[1] + 2]};
+  const V3 c{pos[3 * (int64_t)t[2]], pos[3 * (int64_t)t[2] + 1], pos[3 * (int64_t)t[2] + 2]};
+  const V3 d{pos[3 * (int64_t)t[3]], pos[3 * (int64_t)t[3] + 1], pos[3 * (int64_t)t[3] + 2]};
+  return std::fabs(orient(a, b, c, d)) / 6.0;
+}
+
+template <typename X>
+X *dup(const std::vector<X> &v) {
+  X *p = static_cast<X *>(std::malloc(sizeof(X) * (v.size() ? v.size() : 1)));
+  if (p && !v.empty()) std::memcpy(p, v.data(), sizeof(X) * v.size());
+  return p;
+}
+
+}  // namespace
+
+extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row_ptr, const int32_t *col,
+                                int64_t ntet, const int32_t *tets, const double *volume, int64_t nrem,
+                                const int32_t *removed, sx_remesh_result *out) {
+  if (!out) return SX_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->bad_vertex = -1;
+  if (n < 1 || !pos || !row_ptr || !col || !volume || (ntet > 0 && !tets) || nrem < 0 ||
+      (nrem > 0 && !removed))
+    return SX_EINVAL;
+  try {
+    std::vector<char> rem((size_t)n, 0);
+    for (int64_t k = 0; k < nrem; ++k) {
+      if (removed[k] < 0 || removed[k] >= n) return SX_EINVAL;
+      rem[(size_t)removed[k]] = 1;
+    }
+    // the star of every removed vertex
+    std::vector<int64_t> cav_of((size_t)n, -1);
+    std::vector<int32_t> vs;
+    for (int64_t v = 0; v < n; ++v)
+      if (rem[(size_t)v]) {
+        cav_of[(size_t)v] = (int64_t)vs.size();
+        vs.push_back((int32_t)v);
+      }
+    const size_t ncav = vs.size();
+    std::vector<int64_t> star_cnt(ncav + 1, 0);
+    std::vector<char> tet_hit((size_t)ntet, 0);
+    for (int64_t t = 0; t < ntet; ++t) {
+      int h = 0, who = -1;
+      for (int k = 0; k < 4; ++k)
+        if (rem[(size_t)tets[4 * t + k]]) {
+          ++h;
+          who = tets[4 * t + k];
+        }
+      if (h > 1) return SX_EINVAL;  // removed vertices must not be adjacent
+      if (h == 1) {
+        tet_hit[(size_t)t] = 1;
+        ++star_cnt[(size_t)cav_of[(size_t)who] + 1];
+      }
+    }
+    for (size_t c = 0; c < ncav; ++c) star_cnt[c + 1] += star_cnt[c];
+    std::vector<int64_t> star((size_t)star_cnt[ncav]);
+    {
+      std::vector<int64_t> fill(star_cnt.begin(), star_cnt.end() - 1);
+      for (int64_t t = 0; t < ntet; ++t) {
+        if (!tet_hit[(size_t)t]) continue;
+        int who = -1;
+        for (int k = 0; k < 4; ++k)
+          if (rem[(size_t)tets[4 * t + k]]) who = tets[4 * t + k];
+        star[(size_t)fill[(size_t)cav_of[(size_t)who]]++] = t;
+      }
+    }
+    // fill every cavity
+    std::vector<int32_t> new_tets;
+    std::vector<V3> lp;
+    std::vector<int32_t> link;
+    std::vector<Tet> dt;
+    for (size_t c = 0; c < ncav; ++c) {
+      const int32_t v = vs[c];
+      const V3 o{pos[3 * (int64_t)v], pos[3 * (int64_t)v + 1], pos[3 * (int64_t)v + 2]};
+      link.clear();
+      double vol_old = 0.0;
+      for (int64_t s = star_cnt[c]; s < star_cnt[c + 1]; ++s) {
+        const int32_t *q = tets + 4 * star[(size_t)s];
+        vol_old += tet_volume(pos, q);
+        for (int k = 0; k < 4; ++k)
+          if (q[k] != v) link.push_back(q[k]);
+      }
+      std::sort(link.begin(), link.end());
+      link.erase(std::unique(link.begin(), link.end()), link.end());
+      lp.resize(link.size());
+      for (size_t i = 0; i < link.size(); ++i)
+        lp[i] = {pos[3 * (int64_t)link[i]] - o.x, pos[3 * (int64_t)link[i] + 1] - o.y,
+                 pos[3 * (int64_t)link[i] + 2] - o.z};
+      bool ok = link.size() >= 4 && delaunay_small(lp, dt);
+      double vol_new = 0.0;
+      const size_t first = new_tets.size();
+      for (size_t k = 0; ok && k < dt.size(); ++k) {
+        const Tet &q = dt[k];
+        const V3 cen{(lp[q.v[0]].x + lp[q.v[1]].x + lp[q.v[2]].x + lp[q.v[3]].x) / 4,
+                     (lp[q.v[0]].y + lp[q.v[1]].y + lp[q.v[2]].y + lp[q.v[3]].y) / 4,
+                     (lp[q.v[0]].z + lp[q.v[1]].z + lp[q.v[2]].z + lp[q.v[3]].z) / 4};
+        bool inside = false;
+        for (int64_t s = star_cnt[c]; s < star_cnt[c + 1] && !inside; ++s) {
+          const int32_t *w = tets + 4 * star[(size_t)s];
+          V3 p4[4];
+          for (int a = 0; a < 4; ++a)
+            p4[a] = {pos[3 * (int64_t)w[a]] - o.x, pos[3 * (int64_t)w[a] + 1] - o.y,
+                     pos[3 * (int64_t)w[a] + 2] - o.z};
+          inside = in_tet(cen, p4[0], p4[1], p4[2], p4[3]);
+        }
+        if (!inside) continue;
+        int32_t g[4] = {link[q.v[0]], link[q.v[1]], link[q.v[2]], link[q.v[3]]};
+        vol_new += tet_volume(pos, g);
+        new_tets.insert(new_tets.end(), g, g + 4);
+      }
+      if (!ok || !(std::fabs(vol_new - vol_old) <= 1e-9 * vol_old)) {
+        new_tets.resize(first);
+        out->bad_vertex = v;
+        return SX_EINVAL;
+      }
+    }
+    const int64_t nnew = (int64_t)new_tets.size() / 4;
+    // new edges per vertex (both directions), sorted and unique
+    std::vector<std::vector<int32_t>> add_of;  // indexed by position among the link vertices
+    std::vector<int64_t> add_idx((size_t)n, -1);
+    for (int64_t t = 0; t < nnew; ++t)
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) {
+          if (a == b) continue;
+          const int32_t u = new_tets[4 * t + a], w = new_tets[4 * t + b];
+          if (add_idx[(size_t)u] < 0) {
+            add_idx[(size_t)u] = (int64_t)add_of.size();
+            add_of.emplace_back();
+          }
+          add_of[(size_t)add_idx[(size_t)u]].push_back(w);
+        }
+    for (auto &l : add_of) {
+      std::sort(l.begin(), l.end());
+      l.erase(std::unique(l.begin(), l.end()), l.end());
+    }
+    // renumbering of the survivors, in their old order
+    std::vector<int32_t> new_of_old((size_t)n, -1);
+    int64_t n2 = 0;
+    for (int64_t v = 0; v < n; ++v)
+      if (!rem[(size_t)v]) new_of_old[(size_t)v] = (int32_t)n2++;
+    // the graph: each survivor's row without removed neighbours, merged with
+    // its new neighbours (both ascending)
+    std::vector<int64_t> rp2((size_t)n2 + 1, 0);
+    std::vector<int32_t> col2;
+    col2.reserve((size_t)row_ptr[n]);
+    for (int64_t v = 0; v < n; ++v) {
+      if (rem[(size_t)v]) continue;
+      const std::vector<int32_t> *ad = add_idx[(size_t)v] >= 0 ? &add_of[(size_t)add_idx[(size_t)v]] : nullptr;
+      size_t ai = 0;
+      for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const int32_t w = col[e];
+        while (ad && ai < ad->size() && (*ad)[ai] < w) {
+          if (!rem[(size_t)(*ad)[ai]]) col2.push_back(new_of_old[(size_t)(*ad)[ai]]);
+          ++ai;
+        }
+        if (ad && ai < ad->size() && (*ad)[ai] == w) ++ai;  // already an edge
+        if (!rem[(size_t)w]) col2.push_back(new_of_old[(size_t)w]);
+      }
+      while (ad && ai < ad->size()) {
+        if (!rem[(size_t)(*ad)[ai]]) col2.push_back(new_of_old[(size_t)(*ad)[ai]]);
+        ++ai;
+      }
+      rp2[(size_t)new_of_old[(size_t)v] + 1] = (int64_t)col2.size();
+    }
+    // cell volumes: a quarter of each old cavity tetrahedron leaves its
+    // corners, a quarter of each new one joins them
+    std::vector<double> vol(volume, volume + n);
+    for (size_t s = 0; s < star.size(); ++s) {
+      const int32_t *q = tets + 4 * star[s];
+      const double qv = 0.25 * tet_volume(pos, q);
+      for (int k = 0; k < 4; ++k) vol[(size_t)q[k]] -= qv;
+    }
+    for (int64_t t = 0; t < nnew; ++t) {
+      const double qv = 0.25 * tet_volume(pos, &new_tets[4 * t]);
+      for (int k = 0; k < 4; ++k) vol[(size_t)new_tets[4 * t + k]] += qv;
+    }
+    std::vector<double> vol2((size_t)n2);
+    std::vector<int32_t> old_of_new((size_t)n2);
+    for (int64_t v = 0; v < n; ++v) {
+      const int32_t w = new_of_old[(size_t)v];
+      if (w < 0) continue;
+      vol2[(size_t)w] = vol[(size_t)v];
+      old_of_new[(size_t)w] = (int32_t)v;
+    }
+    // tetrahedra: the untouched ones, then the new ones, renumbered
+    std::vector<int32_t> tets2;
+    tets2.reserve(4 * (size_t)(ntet - (int64_t)star.size() + nnew));
+    for (int64_t t = 0; t < ntet; ++t) {
+      if (tet_hit[(size_t)t]) continue;
+      for (int k = 0; k < 4; ++k) tets2.push_back(new_of_old[(size_t)tets[4 * t + k]]);
+    }
+    for (int64_t t = 0; t < 4 * nnew; ++t) tets2.push_back(new_of_old[(size_t)new_tets[t]]);
+    out->n = n2;
+    out->nnz = (int64_t)col2.size();
+    out->ntet = (int64_t)tets2.size() / 4;
+    out->row_ptr = dup(rp2);
+    out->col = dup(col2);
+    out->volume = dup(vol2);
+    out->tets = dup(tets2);
+    out->old_of_new = dup(old_of_new);
+    if (!out->row_ptr || !out->col || !out->volume || !out->tets || !out->old_of_new) {
+      sx_remesh_free(out);
+      return SX_ENOMEM;
+    }
+    return SX_OK;
+  } catch (const std::bad_alloc &) {
+    return SX_ENOMEM;
+  }
+}
+
+extern "C" void sx_remesh_free(sx_remesh_result *r) {
+  if (!r) return;
+  std::free(r->row_ptr);
+  std::free(r->col);
+  std::free(r->volume);
+  std::free(r->tets);
+  std::free(r->old_of_new);
+  r->row_ptr = nullptr;
+  r->col = nullptr;
+  r->volume = nullptr;
+  r->tets = nullptr;
+  r->old_of_new = nullptr;
+}

@@ -76,7 +76,7 @@ def _pool(workers: int):
 
 
 def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True,
-                    workers: int | None = None) -> tuple:
+                    workers: int | None = None, method: str = "native") -> tuple:
     """The grid without the `removed` vertices (an independent set of the
     graph): survivors in their old order, their Delaunay graph, cell volumes
     (1/4 of the incident tetrahedra), media, flags, sources and tetrahedra.
@@ -84,9 +84,13 @@ def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True,
 
     Needs the grid's tetrahedra (``problem.simplices``); a grid without them,
     or a cavity that cannot be filled locally, is rebuilt by QHull (or, with
-    ``allow_rebuild=False``, raises RuntimeError).  The cavities are filled
-    by `workers` processes (default: the host's cores when there are more
-    than 256 cavities, else in this process)."""
+    ``allow_rebuild=False``, raises RuntimeError).
+
+    method="native" (default) runs the whole removal in the library
+    (sx_remesh_remove: Bowyer-Watson per cavity, single-pass patches);
+    method="qhull" fills the cavities with QHull in `workers` processes
+    (default: the host's cores when there are more than 256 cavities) and
+    patches the arrays with numpy."""
 
     def rebuild(why):
         if not allow_rebuild:
@@ -100,6 +104,27 @@ def remove_vertices(problem: "I.Problem", removed, allow_rebuild: bool = True,
         return rebuild("the grid has no tetrahedra")
     if np.any(rem[problem.src_vertex]):
         raise ValueError("sources are never removed")
+    if method == "native":
+        from . import simplex as S
+
+        try:
+            r = S.sx_remesh_remove(problem.pos, problem.row_ptr, problem.col, problem.simplices,
+                                   problem.volume, np.flatnonzero(rem))
+        except S.RemeshError as e:
+            if e.vertex < 0:
+                raise ValueError("removed vertices must not be adjacent") from e
+            return rebuild(f"the cavity of vertex {e.vertex} cannot be filled locally")
+        keep = r["old_of_new"].astype(np.int64)
+        new_of_old = np.full(n, -1, dtype=np.int64)
+        new_of_old[keep] = np.arange(len(keep))
+        p = I.Problem(pos=np.ascontiguousarray(problem.pos[keep]), row_ptr=r["row_ptr"], col=r["col"],
+                      nH=problem.nH[keep].copy(), volume=r["volume"], flags=problem.flags[keep].copy(),
+                      src_vertex=new_of_old[problem.src_vertex].astype(np.int32),
+                      src_rate=problem.src_rate.copy(), box=problem.box, meta=dict(problem.meta),
+                      simplices=r["tets"])
+        return p, r["old_of_new"]
+    if method != "qhull":
+        raise ValueError("method must be 'native' or 'qhull'")
     simp = np.asarray(problem.simplices)
     hit = rem.view(np.uint8)[simp]
     cnt = hit.sum(axis=1, dtype=np.uint8)

@@ -53,6 +53,13 @@ class sx_budget(C.Structure):
 SX_TUNE_MAX_CANDIDATES = 4
 
 
+class sx_remesh_result(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("ntet", C.c_int64),
+                ("row_ptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("volume", C.POINTER(C.c_double)), ("tets", C.POINTER(C.c_int32)),
+                ("old_of_new", C.POINTER(C.c_int32)), ("bad_vertex", C.c_int32)]
+
+
 class sx_tune_result(C.Structure):
     _fields_ = [("variant", C.c_int32), ("ncandidates", C.c_int32),
                 ("candidates", C.c_int32 * SX_TUNE_MAX_CANDIDATES),
@@ -112,6 +119,10 @@ _SIGS = [
                                    _P(C.c_uint8), C.c_int32, _P(C.c_double), C.c_int32,
                                    C.c_void_p, _P(C.c_double)]),
     ("sx_kappa_noalloc_last_error", C.c_char_p, []),
+    ("sx_remesh_remove", C.c_int, [C.c_int64, _P(C.c_double), _P(C.c_int64), _P(C.c_int32),
+                                   C.c_int64, _P(C.c_int32), _P(C.c_double), C.c_int64,
+                                   _P(C.c_int32), _P(sx_remesh_result)]),
+    ("sx_remesh_free", None, [_P(sx_remesh_result)]),
 ]
 
 
@@ -200,6 +211,43 @@ def sx_step_budgets(ctx, dt_s: float, nsteps: int, budgets: np.ndarray):
         raise ValueError("budgets must be a C-contiguous float64 array of nsteps x 4")
     _check(ctx, lib().sx_step_budgets(ctx, float(dt_s), int(nsteps),
                                       budgets.ctypes.data_as(C.POINTER(sx_budget))))
+
+
+class RemeshError(ValueError):
+    """A cavity could not be re-triangulated locally (``vertex`` is the
+    removed vertex), or the removal is invalid (``vertex`` is -1)."""
+
+    def __init__(self, code: int, vertex: int):
+        super().__init__(f"sx_remesh_remove: code {code}, vertex {vertex}")
+        self.code = code
+        self.vertex = vertex
+
+
+def sx_remesh_remove(pos, row_ptr, col, tets, volume, removed) -> dict:
+    """The grid without the `removed` vertices (see include/simplexgb.h):
+    dict of row_ptr, col, volume, tets, old_of_new (numpy copies)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    tt = np.ascontiguousarray(tets, dtype=np.int32)
+    vol = np.ascontiguousarray(volume, dtype=np.float64)
+    rem = np.ascontiguousarray(removed, dtype=np.int32)
+    res = sx_remesh_result()
+    rc = lib().sx_remesh_remove(len(pos), _ptr(pos, C.c_double), _ptr(rp, C.c_int64),
+                                _ptr(cl, C.c_int32), len(tt), _ptr(tt, C.c_int32),
+                                _ptr(vol, C.c_double), len(rem), _ptr(rem, C.c_int32), C.byref(res))
+    if rc != SX_OK:
+        raise RemeshError(rc, res.bad_vertex)
+    try:
+        out = dict(row_ptr=np.ctypeslib.as_array(res.row_ptr, (res.n + 1,)).copy(),
+                   col=np.ctypeslib.as_array(res.col, (max(res.nnz, 1),))[:res.nnz].copy(),
+                   volume=np.ctypeslib.as_array(res.volume, (res.n,)).copy(),
+                   tets=np.ctypeslib.as_array(res.tets, (max(res.ntet, 1) * 4,))[:4 * res.ntet]
+                   .reshape(res.ntet, 4).copy(),
+                   old_of_new=np.ctypeslib.as_array(res.old_of_new, (res.n,)).copy())
+    finally:
+        lib().sx_remesh_free(C.byref(res))
+    return out
 
 
 def sx_sync(ctx):

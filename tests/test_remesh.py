@@ -42,15 +42,16 @@ def _same_grid(a, b):
     assert np.array_equal(_canon(a.simplices), _canon(b.simplices))
 
 
+@pytest.mark.parametrize("method", ["native", "qhull"])
 @pytest.mark.parametrize("make", [lambda: I.stromgren_problem(3000, seed=21),
                                   lambda: I.clumpy_problem(4000, mesh=16, nsrc=4, seed=2)])
-def test_local_removal_equals_full_rebuild(make):
+def test_local_removal_equals_full_rebuild(make, method):
     p = make()
     for rnd in range(2):  # twice: the second removal starts from the patched tetrahedra
         rem = _independent_interior(p, 150, seed=rnd)
         assert len(rem) == 150
         full, o2n_full = I.survivor_problem(p, rem)
-        loc, o2n = R.remove_vertices(p, rem, allow_rebuild=False)  # every cavity filled locally
+        loc, o2n = R.remove_vertices(p, rem, allow_rebuild=False, method=method)  # every cavity local
         assert np.array_equal(o2n, o2n_full)
         _same_grid(loc, full)
         # the volume of the cells is conserved
@@ -75,8 +76,9 @@ def test_removal_rules():
     from scipy.spatial import ConvexHull
 
     hull_v = int(ConvexHull(p.pos).vertices[0])
-    with pytest.raises(RuntimeError):
-        R.remove_vertices(p, [hull_v], allow_rebuild=False)
+    for method in ("native", "qhull"):
+        with pytest.raises(RuntimeError):
+            R.remove_vertices(p, [hull_v], allow_rebuild=False, method=method)
     q, o2n = R.remove_vertices(p, [hull_v])
     full, o2n_full = I.survivor_problem(p, [hull_v])
     assert np.array_equal(o2n, o2n_full)
@@ -92,10 +94,11 @@ def test_removal_rules():
 
 
 def test_worker_processes_give_the_same_grid():
+    """The QHull method in worker processes equals it in this process."""
     p = I.stromgren_problem(3000, seed=22)
     rem = _independent_interior(p, 300, seed=5)
-    a, oa = R.remove_vertices(p, rem, allow_rebuild=False, workers=1)
-    b, ob = R.remove_vertices(p, rem, allow_rebuild=False, workers=2)
+    a, oa = R.remove_vertices(p, rem, allow_rebuild=False, workers=1, method="qhull")
+    b, ob = R.remove_vertices(p, rem, allow_rebuild=False, workers=2, method="qhull")
     assert np.array_equal(oa, ob)
     assert np.array_equal(a.row_ptr, b.row_ptr) and np.array_equal(a.col, b.col)
     assert np.array_equal(a.volume, b.volume) and np.array_equal(a.simplices, b.simplices)
