@@ -223,6 +223,11 @@ class RemeshError(ValueError):
         self.vertex = vertex
 
 
+def sx_remesh_free(result: "sx_remesh_result"):
+    """Free the arrays of a result of the C call sx_remesh_remove."""
+    lib().sx_remesh_free(C.byref(result))
+
+
 def sx_remesh_remove(pos, row_ptr, col, tets, volume, removed) -> dict:
     """The grid without the `removed` vertices (see include/simplexgb.h):
     dict of row_ptr, col, volume, tets, old_of_new (numpy copies)."""
@@ -246,7 +251,7 @@ def sx_remesh_remove(pos, row_ptr, col, tets, volume, removed) -> dict:
                    .reshape(res.ntet, 4).copy(),
                    old_of_new=np.ctypeslib.as_array(res.old_of_new, (res.n,)).copy())
     finally:
-        lib().sx_remesh_free(C.byref(res))
+        sx_remesh_free(res)
     return out
 
 
