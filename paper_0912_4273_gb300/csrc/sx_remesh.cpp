@@ -18,6 +18,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "simplexgb.h"
@@ -73,7 +74,8 @@ bool delaunay_small(const std::vector<V3> &pts, std::vector<Tet> &out) {
   if (orient(P[m], P[m + 1], P[m + 2], P[m + 3]) < 0) std::swap(T[0].v[0], T[0].v[1]);
   std::vector<char> bad;
   struct Face {
-    int a, b, c;
+    int a, b, c;  // as oriented in its tetrahedron
+    int key[3];   // the same vertices, ascending
   };
   std::vector<Face> faces;
   for (int i = 0; i < m; ++i) {
@@ -88,25 +90,30 @@ bool delaunay_small(const std::vector<V3> &pts, std::vector<Tet> &out) {
     }
     if (!any) return false;
     // the cavity's boundary: faces of bad tetrahedra not shared with another
-    // bad one, oriented as seen from inside the bad tetrahedron
+    // bad one (a shared face appears twice among them), oriented outward
     faces.clear();
     for (size_t t = 0; t < T.size(); ++t) {
       if (!bad[t]) continue;
       const int *v = T[t].v;
       const int f[4][3] = {{v[1], v[2], v[3]}, {v[0], v[3], v[2]}, {v[0], v[1], v[3]}, {v[0], v[2], v[1]}};
       for (int k = 0; k < 4; ++k) {
-        int key[3] = {f[k][0], f[k][1], f[k][2]};
-        std::sort(key, key + 3);
-        bool shared = false;
-        for (size_t u = 0; u < T.size() && !shared; ++u) {
-          if (u == t || !bad[u]) continue;
-          const int *w = T[u].v;
-          int c = 0;
-          for (int a = 0; a < 4; ++a) c += (w[a] == key[0]) + (w[a] == key[1]) + (w[a] == key[2]);
-          shared = c == 3;
-        }
-        if (!shared) faces.push_back({f[k][0], f[k][1], f[k][2]});
+        Face fc{f[k][0], f[k][1], f[k][2], {f[k][0], f[k][1], f[k][2]}};
+        std::sort(fc.key, fc.key + 3);
+        faces.push_back(fc);
       }
+    }
+    std::sort(faces.begin(), faces.end(), [](const Face &x, const Face &y) {
+      return std::lexicographical_compare(x.key, x.key + 3, y.key, y.key + 3);
+    });
+    {
+      size_t w = 0;
+      for (size_t k = 0; k < faces.size();) {
+        size_t e = k + 1;
+        while (e < faces.size() && std::equal(faces[e].key, faces[e].key + 3, faces[k].key)) ++e;
+        if (e - k == 1) faces[w++] = faces[k];
+        k = e;
+      }
+      faces.resize(w);
     }
     std::vector<Tet> keep;
     keep.reserve(T.size() + faces.size());
@@ -144,13 +151,6 @@ double tet_volume(const double *pos, const int32_t *t) {
   const V3 c{pos[3 * (int64_t)t[2]], pos[3 * (int64_t)t[2] + 1], pos[3 * (int64_t)t[2] + 2]};
   const V3 d{pos[3 * (int64_t)t[3]], pos[3 * (int64_t)t[3] + 1], pos[3 * (int64_t)t[3] + 2]};
   return std::fabs(orient(a, b, c, d)) / 6.0;
-}
-
-template <typename X>
-X *dup(const std::vector<X> &v) {
-  X *p = static_cast<X *>(std::malloc(sizeof(X) * (v.size() ? v.size() : 1)));
-  if (p && !v.empty()) std::memcpy(p, v.data(), sizeof(X) * v.size());
-  return p;
 }
 
 }  // namespace
@@ -206,55 +206,88 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
         star[(size_t)fill[(size_t)cav_of[(size_t)who]]++] = t;
       }
     }
-    // fill every cavity
-    std::vector<int32_t> new_tets;
-    std::vector<V3> lp;
-    std::vector<int32_t> link;
-    std::vector<Tet> dt;
-    for (size_t c = 0; c < ncav; ++c) {
-      const int32_t v = vs[c];
-      const V3 o{pos[3 * (int64_t)v], pos[3 * (int64_t)v + 1], pos[3 * (int64_t)v + 2]};
-      link.clear();
-      double vol_old = 0.0;
-      for (int64_t s = star_cnt[c]; s < star_cnt[c + 1]; ++s) {
-        const int32_t *q = tets + 4 * star[(size_t)s];
-        vol_old += tet_volume(pos, q);
-        for (int k = 0; k < 4; ++k)
-          if (q[k] != v) link.push_back(q[k]);
-      }
-      std::sort(link.begin(), link.end());
-      link.erase(std::unique(link.begin(), link.end()), link.end());
-      lp.resize(link.size());
-      for (size_t i = 0; i < link.size(); ++i)
-        lp[i] = {pos[3 * (int64_t)link[i]] - o.x, pos[3 * (int64_t)link[i] + 1] - o.y,
-                 pos[3 * (int64_t)link[i] + 2] - o.z};
-      bool ok = link.size() >= 4 && delaunay_small(lp, dt);
-      double vol_new = 0.0;
-      const size_t first = new_tets.size();
-      for (size_t k = 0; ok && k < dt.size(); ++k) {
-        const Tet &q = dt[k];
-        const V3 cen{(lp[q.v[0]].x + lp[q.v[1]].x + lp[q.v[2]].x + lp[q.v[3]].x) / 4,
-                     (lp[q.v[0]].y + lp[q.v[1]].y + lp[q.v[2]].y + lp[q.v[3]].y) / 4,
-                     (lp[q.v[0]].z + lp[q.v[1]].z + lp[q.v[2]].z + lp[q.v[3]].z) / 4};
-        bool inside = false;
-        for (int64_t s = star_cnt[c]; s < star_cnt[c + 1] && !inside; ++s) {
-          const int32_t *w = tets + 4 * star[(size_t)s];
-          V3 p4[4];
-          for (int a = 0; a < 4; ++a)
-            p4[a] = {pos[3 * (int64_t)w[a]] - o.x, pos[3 * (int64_t)w[a] + 1] - o.y,
-                     pos[3 * (int64_t)w[a] + 2] - o.z};
-          inside = in_tet(cen, p4[0], p4[1], p4[2], p4[3]);
+    // fill every cavity: threads take contiguous ranges of cavities, and their
+    // tetrahedra are joined in cavity order (the result does not depend on
+    // the thread count)
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const unsigned nth = ncav < 64 ? 1u : std::min<unsigned>(hw, (unsigned)(ncav / 32));
+    std::vector<std::vector<int32_t>> part(nth);
+    std::vector<int32_t> failed(nth, -1);
+    std::vector<char> no_memory(nth, 0);
+    auto fill_range = [&](unsigned th) {
+      try {
+        const size_t c0 = ncav * th / nth, c1 = ncav * (th + 1) / nth;
+        std::vector<int32_t> &nt = part[th];
+        std::vector<V3> lp;
+        std::vector<int32_t> link;
+        std::vector<Tet> dt;
+        for (size_t c = c0; c < c1; ++c) {
+          const int32_t v = vs[c];
+          const V3 o{pos[3 * (int64_t)v], pos[3 * (int64_t)v + 1], pos[3 * (int64_t)v + 2]};
+          link.clear();
+          double vol_old = 0.0;
+          for (int64_t s = star_cnt[c]; s < star_cnt[c + 1]; ++s) {
+            const int32_t *q = tets + 4 * star[(size_t)s];
+            vol_old += tet_volume(pos, q);
+            for (int k = 0; k < 4; ++k)
+              if (q[k] != v) link.push_back(q[k]);
+          }
+          std::sort(link.begin(), link.end());
+          link.erase(std::unique(link.begin(), link.end()), link.end());
+          lp.resize(link.size());
+          for (size_t i = 0; i < link.size(); ++i)
+            lp[i] = {pos[3 * (int64_t)link[i]] - o.x, pos[3 * (int64_t)link[i] + 1] - o.y,
+                     pos[3 * (int64_t)link[i] + 2] - o.z};
+          bool ok = link.size() >= 4 && delaunay_small(lp, dt);
+          double vol_new = 0.0;
+          for (size_t k = 0; ok && k < dt.size(); ++k) {
+            const Tet &q = dt[k];
+            const V3 cen{(lp[q.v[0]].x + lp[q.v[1]].x + lp[q.v[2]].x + lp[q.v[3]].x) / 4,
+                         (lp[q.v[0]].y + lp[q.v[1]].y + lp[q.v[2]].y + lp[q.v[3]].y) / 4,
+                         (lp[q.v[0]].z + lp[q.v[1]].z + lp[q.v[2]].z + lp[q.v[3]].z) / 4};
+            bool inside = false;
+            for (int64_t s = star_cnt[c]; s < star_cnt[c + 1] && !inside; ++s) {
+              const int32_t *w = tets + 4 * star[(size_t)s];
+              V3 p4[4];
+              for (int a = 0; a < 4; ++a)
+                p4[a] = {pos[3 * (int64_t)w[a]] - o.x, pos[3 * (int64_t)w[a] + 1] - o.y,
+                         pos[3 * (int64_t)w[a] + 2] - o.z};
+              inside = in_tet(cen, p4[0], p4[1], p4[2], p4[3]);
+            }
+            if (!inside) continue;
+            const int32_t g[4] = {link[q.v[0]], link[q.v[1]], link[q.v[2]], link[q.v[3]]};
+            vol_new += tet_volume(pos, g);
+            nt.insert(nt.end(), g, g + 4);
+          }
+          if (!ok || !(std::fabs(vol_new - vol_old) <= 1e-9 * vol_old)) {
+            failed[th] = v;
+            return;
+          }
         }
-        if (!inside) continue;
-        int32_t g[4] = {link[q.v[0]], link[q.v[1]], link[q.v[2]], link[q.v[3]]};
-        vol_new += tet_volume(pos, g);
-        new_tets.insert(new_tets.end(), g, g + 4);
+      } catch (const std::bad_alloc &) {  // an exception must not leave a thread
+        no_memory[th] = 1;
       }
-      if (!ok || !(std::fabs(vol_new - vol_old) <= 1e-9 * vol_old)) {
-        new_tets.resize(first);
-        out->bad_vertex = v;
+    };
+    if (nth == 1) {
+      fill_range(0);
+    } else {
+      std::vector<std::thread> pool;
+      for (unsigned th = 0; th < nth; ++th) pool.emplace_back(fill_range, th);
+      for (std::thread &t : pool) t.join();
+    }
+    for (unsigned th = 0; th < nth; ++th)
+      if (no_memory[th]) return SX_ENOMEM;
+    for (unsigned th = 0; th < nth; ++th)
+      if (failed[th] >= 0) {
+        out->bad_vertex = failed[th];
         return SX_EINVAL;
       }
+    std::vector<int32_t> new_tets;
+    {
+      size_t tot = 0;
+      for (const auto &pv : part) tot += pv.size();
+      new_tets.reserve(tot);
+      for (const auto &pv : part) new_tets.insert(new_tets.end(), pv.begin(), pv.end());
     }
     const int64_t nnew = (int64_t)new_tets.size() / 4;
     // new edges per vertex (both directions), sorted and unique
@@ -280,11 +313,26 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
     int64_t n2 = 0;
     for (int64_t v = 0; v < n; ++v)
       if (!rem[(size_t)v]) new_of_old[(size_t)v] = (int32_t)n2++;
+    // the outputs, allocated once at their final size (the graph at an upper
+    // bound, trimmed at the end)
+    size_t nadd = 0;
+    for (const auto &l : add_of) nadd += l.size();
+    const int64_t ntet2 = ntet - (int64_t)star.size() + nnew;
+    out->row_ptr = static_cast<int64_t *>(std::malloc(sizeof(int64_t) * ((size_t)n2 + 1)));
+    out->col = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * ((size_t)row_ptr[n] + nadd + 1)));
+    out->volume = static_cast<double *>(std::malloc(sizeof(double) * ((size_t)n2 + 1)));
+    out->old_of_new = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * ((size_t)n2 + 1)));
+    out->tets = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * (4 * (size_t)ntet2 + 1)));
+    if (!out->row_ptr || !out->col || !out->volume || !out->old_of_new || !out->tets) {
+      sx_remesh_free(out);
+      return SX_ENOMEM;
+    }
     // the graph: each survivor's row without removed neighbours, merged with
     // its new neighbours (both ascending)
-    std::vector<int64_t> rp2((size_t)n2 + 1, 0);
-    std::vector<int32_t> col2;
-    col2.reserve((size_t)row_ptr[n]);
+    int64_t *rp2 = out->row_ptr;
+    int32_t *col2 = out->col;
+    int64_t m = 0;
+    rp2[0] = 0;
     for (int64_t v = 0; v < n; ++v) {
       if (rem[(size_t)v]) continue;
       const std::vector<int32_t> *ad = add_idx[(size_t)v] >= 0 ? &add_of[(size_t)add_idx[(size_t)v]] : nullptr;
@@ -292,18 +340,20 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
       for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
         const int32_t w = col[e];
         while (ad && ai < ad->size() && (*ad)[ai] < w) {
-          if (!rem[(size_t)(*ad)[ai]]) col2.push_back(new_of_old[(size_t)(*ad)[ai]]);
+          if (!rem[(size_t)(*ad)[ai]]) col2[m++] = new_of_old[(size_t)(*ad)[ai]];
           ++ai;
         }
         if (ad && ai < ad->size() && (*ad)[ai] == w) ++ai;  // already an edge
-        if (!rem[(size_t)w]) col2.push_back(new_of_old[(size_t)w]);
+        if (!rem[(size_t)w]) col2[m++] = new_of_old[(size_t)w];
       }
       while (ad && ai < ad->size()) {
-        if (!rem[(size_t)(*ad)[ai]]) col2.push_back(new_of_old[(size_t)(*ad)[ai]]);
+        if (!rem[(size_t)(*ad)[ai]]) col2[m++] = new_of_old[(size_t)(*ad)[ai]];
         ++ai;
       }
-      rp2[(size_t)new_of_old[(size_t)v] + 1] = (int64_t)col2.size();
+      rp2[(size_t)new_of_old[(size_t)v] + 1] = m;
     }
+    if (int32_t *shrunk = static_cast<int32_t *>(std::realloc(out->col, sizeof(int32_t) * ((size_t)m + 1))))
+      out->col = shrunk;
     // cell volumes: a quarter of each old cavity tetrahedron leaves its
     // corners, a quarter of each new one joins them
     std::vector<double> vol(volume, volume + n);
@@ -316,36 +366,25 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
       const double qv = 0.25 * tet_volume(pos, &new_tets[4 * t]);
       for (int k = 0; k < 4; ++k) vol[(size_t)new_tets[4 * t + k]] += qv;
     }
-    std::vector<double> vol2((size_t)n2);
-    std::vector<int32_t> old_of_new((size_t)n2);
     for (int64_t v = 0; v < n; ++v) {
       const int32_t w = new_of_old[(size_t)v];
       if (w < 0) continue;
-      vol2[(size_t)w] = vol[(size_t)v];
-      old_of_new[(size_t)w] = (int32_t)v;
+      out->volume[w] = vol[(size_t)v];
+      out->old_of_new[w] = (int32_t)v;
     }
     // tetrahedra: the untouched ones, then the new ones, renumbered
-    std::vector<int32_t> tets2;
-    tets2.reserve(4 * (size_t)(ntet - (int64_t)star.size() + nnew));
+    int32_t *t2 = out->tets;
     for (int64_t t = 0; t < ntet; ++t) {
       if (tet_hit[(size_t)t]) continue;
-      for (int k = 0; k < 4; ++k) tets2.push_back(new_of_old[(size_t)tets[4 * t + k]]);
+      for (int k = 0; k < 4; ++k) *t2++ = new_of_old[(size_t)tets[4 * t + k]];
     }
-    for (int64_t t = 0; t < 4 * nnew; ++t) tets2.push_back(new_of_old[(size_t)new_tets[t]]);
+    for (int64_t t = 0; t < 4 * nnew; ++t) *t2++ = new_of_old[(size_t)new_tets[t]];
     out->n = n2;
-    out->nnz = (int64_t)col2.size();
-    out->ntet = (int64_t)tets2.size() / 4;
-    out->row_ptr = dup(rp2);
-    out->col = dup(col2);
-    out->volume = dup(vol2);
-    out->tets = dup(tets2);
-    out->old_of_new = dup(old_of_new);
-    if (!out->row_ptr || !out->col || !out->volume || !out->tets || !out->old_of_new) {
-      sx_remesh_free(out);
-      return SX_ENOMEM;
-    }
+    out->nnz = m;
+    out->ntet = ntet2;
     return SX_OK;
   } catch (const std::bad_alloc &) {
+    sx_remesh_free(out);
     return SX_ENOMEM;
   }
 }
