@@ -117,3 +117,22 @@ def test_checkpoint_argument_errors(libpath, tmp_path):
                                 ctypes.byref(nnz)) == S.SX_EINVAL
     with pytest.raises(S.SimplexError):
         S.sx_checkpoint_info(str(bad))
+
+
+def test_remesh_argument_errors(libpath):
+    """sx_remesh_remove is host code: its refusals need no GPU."""
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    L = S.lib()
+    assert L.sx_remesh_remove(0, None, None, None, 0, None, None, 0, None, None) == S.SX_EINVAL
+    p = I.stromgren_problem(500, seed=4)
+    with pytest.raises(S.RemeshError) as e:  # an id out of range
+        S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [p.n])
+    assert e.value.code == S.SX_EINVAL and e.value.vertex == -1
+    v = int(np.flatnonzero(p.interior)[3])
+    with pytest.raises(S.RemeshError) as e:  # two adjacent vertices
+        S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [v, int(p.col[p.row_ptr[v]])])
+    assert e.value.vertex == -1
+    r = S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [])
+    assert np.array_equal(r["col"], p.col) and np.array_equal(r["old_of_new"], np.arange(p.n))
