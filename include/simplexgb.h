@@ -217,8 +217,9 @@ int sx_get_info(sx_ctx *ctx, sx_info *info);
    with sx_remesh_free).  A cavity whose new tetrahedra do not fill its
    volume (a vertex on the convex hull, a degenerate neighbourhood) returns
    SX_EINVAL with out->bad_vertex set: the caller rebuilds the grid instead.
-   Errors: SX_EINVAL (bad arguments, adjacent removed vertices: bad_vertex
-   -1), SX_ENOMEM.  No device memory or GPU is used. */
+   Errors: SX_EINVAL (bad arguments, a row_ptr that decreases, a col or tets
+   entry outside [0, n), adjacent removed vertices: bad_vertex -1),
+   SX_ENOMEM.  No device memory or GPU is used. */
 typedef struct {
     int64_t n, nnz, ntet;
     int64_t *row_ptr;     /* n + 1 */

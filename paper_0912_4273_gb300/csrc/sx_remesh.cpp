@@ -18,6 +18,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <stdexcept>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -164,6 +166,14 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
   if (n < 1 || !pos || !row_ptr || !col || !volume || (ntet > 0 && !tets) || nrem < 0 ||
       (nrem > 0 && !removed))
     return SX_EINVAL;
+  // the graph and the tetrahedra index the arrays below: check them first
+  if (row_ptr[0] != 0) return SX_EINVAL;
+  for (int64_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return SX_EINVAL;
+  for (int64_t e = 0; e < row_ptr[n]; ++e)
+    if (col[e] < 0 || col[e] >= n) return SX_EINVAL;
+  for (int64_t i = 0; i < 4 * ntet; ++i)
+    if (tets[i] < 0 || tets[i] >= n) return SX_EINVAL;
   try {
     std::vector<char> rem((size_t)n, 0);
     for (int64_t k = 0; k < nrem; ++k) {
@@ -264,15 +274,20 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
             return;
           }
         }
-      } catch (const std::bad_alloc &) {  // an exception must not leave a thread
+      } catch (const std::exception &) {  // an exception must not leave a thread
         no_memory[th] = 1;
       }
     };
-    if (nth == 1) {
-      fill_range(0);
-    } else {
+    {
+      // ranges that get no thread (the system refuses one) run on this one
       std::vector<std::thread> pool;
-      for (unsigned th = 0; th < nth; ++th) pool.emplace_back(fill_range, th);
+      pool.reserve(nth);
+      unsigned started = 0;
+      try {
+        for (; nth > 1 && started < nth; ++started) pool.emplace_back(fill_range, started);
+      } catch (const std::system_error &) {
+      }
+      for (unsigned th = started; th < nth; ++th) fill_range(th);
       for (std::thread &t : pool) t.join();
     }
     for (unsigned th = 0; th < nth; ++th)
@@ -383,7 +398,7 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
     out->nnz = m;
     out->ntet = ntet2;
     return SX_OK;
-  } catch (const std::bad_alloc &) {
+  } catch (const std::exception &) {  // bad_alloc, or a size beyond what a vector holds
     sx_remesh_free(out);
     return SX_ENOMEM;
   }

@@ -134,5 +134,17 @@ def test_remesh_argument_errors(libpath):
     with pytest.raises(S.RemeshError) as e:  # two adjacent vertices
         S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [v, int(p.col[p.row_ptr[v]])])
     assert e.value.vertex == -1
+    # a malformed graph or tetrahedron list is refused before it is indexed
+    tets = p.simplices.copy()
+    tets[7, 2] = p.n
+    col = p.col.copy()
+    col[11] = -1
+    rp = p.row_ptr.copy()
+    rp[4] = rp[5] + 1
+    for args in ((p.pos, p.row_ptr, p.col, tets), (p.pos, p.row_ptr, col, p.simplices),
+                 (p.pos, rp, p.col, p.simplices)):
+        with pytest.raises(S.RemeshError) as e:
+            S.sx_remesh_remove(*args, p.volume, [v])
+        assert e.value.code == S.SX_EINVAL and e.value.vertex == -1
     r = S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [])
     assert np.array_equal(r["col"], p.col) and np.array_equal(r["old_of_new"], np.arange(p.n))
