@@ -3,7 +3,8 @@
 What lives here:
   * ``build()`` -- compiles ``sx_oracle.c`` and ``delaunay3d.c`` with gcc;
   * thin wrappers of the C entry points (Philox, rotation, tables, chemistry,
-    the DCT sweep, the Delaunay builder);
+    the DCT sweep with optional diffuse recombination radiation, the
+    Delaunay builder);
   * the analytic Test-1 solutions of Sect. 5.1: Stromgren radius
     (Eq. stromgren_radius), I-front history (Eq. IFront_pos, IFront_vel) and
     the equilibrium ionisation profile (Eq. inner_stromgren_region).
@@ -63,6 +64,10 @@ def lib():
             L.ox_kappa.restype = d
             L.ox_chem.argtypes = [P(d), d, d, d, d, d, d, d, C.c_int, P(C.c_int), P(C.c_int)]
             L.ox_chem.restype = d
+            L.ox_chem_rec.argtypes = [P(d), d, d, d, d, d, d, d, C.c_int, P(C.c_int), P(C.c_int), P(d)]
+            L.ox_chem_rec.restype = d
+            L.ox_get_diffuse.argtypes = [C.c_void_p, P(d)]
+            L.ox_get_diffuse.restype = d
             L.ox_create.argtypes = [C.c_void_p, i64, P(d), P(i64), P(i32), P(d), P(d), P(u8), P(d),
                                     P(d)]
             L.ox_create.restype = C.c_void_p
@@ -158,6 +163,19 @@ def chem(y: float, N_in: float, dt: float, A: float, tau_max: float, R0: float,
     return yy.value, f, ns.value, cp.value
 
 
+def chem_rec(y: float, N_in: float, dt: float, A: float, tau_max: float, R0: float,
+             fc: float = 0.5, tol: float = 1e-5, max_sub: int = 1000):
+    """As ``chem``, and the recombinations per atom during the step:
+    returns (y_new, transmitted fraction, recombinations per atom, nsub, capped)."""
+    yy = C.c_double(y)
+    ns = C.c_int(0)
+    cp = C.c_int(0)
+    rec = C.c_double(0.0)
+    f = lib().ox_chem_rec(C.byref(yy), N_in, dt, A, tau_max, R0, fc, tol, max_sub, C.byref(ns),
+                          C.byref(cp), C.byref(rec))
+    return yy.value, f, rec.value, ns.value, cp.value
+
+
 # ---------------------------------------------------------------------------
 # The sweep
 # ---------------------------------------------------------------------------
@@ -173,13 +191,15 @@ class Params:
     chem_max_sub: int = 1000
     transport: int = 0          # 0 direction conserving, 1 ballistic, 2 combined
     tau_switch: float = 1.0     # combined: ballistic where y tau_max >= tau_switch (Sect. 5.1.3)
+    alpha_A: float = 0.0        # 0: on-the-spot (case B); > 0: case A with the ground-level
+                                # recombination photons re-emitted (Sect. 2.2.1; DCT only)
 
 
 class _CParams(C.Structure):
     _fields_ = [("nbins", C.c_int), ("seed", C.c_uint64), ("sigma", C.c_double),
                 ("alpha_B", C.c_double), ("kappa", C.c_double), ("chem_frac", C.c_double),
                 ("chem_tol", C.c_double), ("chem_max_sub", C.c_int), ("transport", C.c_int),
-                ("tau_switch", C.c_double)]
+                ("tau_switch", C.c_double), ("alpha_A", C.c_double)]
 
 
 class OracleSim:
@@ -204,7 +224,7 @@ class OracleSim:
         k = self._keep
         cp = _CParams(params.nbins, params.seed, params.sigma, params.alpha_B, params.kappa,
                       params.chem_frac, params.chem_tol, params.chem_max_sub, params.transport,
-                      params.tau_switch)
+                      params.tau_switch, params.alpha_A)
         y0p = None
         if y0 is not None:
             k["y0"] = np.ascontiguousarray(y0, dtype=np.float64)
@@ -213,6 +233,9 @@ class OracleSim:
                              _p(k["col"], C.c_int32), _p(k["nH"], C.c_double),
                              _p(k["vol"], C.c_double), _p(k["flags"], C.c_uint8), y0p,
                              _p(k["bins"], C.c_double))
+        if not self.h:
+            raise ValueError("diffuse radiation needs direction-conserving transport and "
+                             "alpha_A >= alpha_B")
         for v, r in zip(problem.src_vertex, problem.src_rate):
             if L.ox_add_source(self.h, int(v), float(r)) != 0:
                 raise ValueError("bad source vertex")
@@ -252,6 +275,14 @@ class OracleSim:
         out = np.zeros(self.n)
         lib().ox_get_inflight(self.h, _p(out, C.c_double))
         return out
+
+    def diffuse(self):
+        """(pending, emitted) of diffuse recombination radiation: each cell's
+        ground-level recombination photons of the last step, which it emits
+        in the next one, and the photons recombining cells have emitted."""
+        out = np.zeros(self.n)
+        emitted = lib().ox_get_diffuse(self.h, _p(out, C.c_double))
+        return out, emitted
 
     def ballistic(self):
         """(stb nnz x 4, twin nnz, thick n) of ballistic or combined transport:
@@ -311,6 +342,8 @@ class OracleSim:
         budget and sources carried to the new grid (a new OracleSim)."""
         if self.p.transport != 0:
             raise NotImplementedError("the dynamic update carries bins: direction conserving only")
+        if self.p.alpha_A > 0:
+            raise NotImplementedError("the dynamic update does not carry diffuse photons")
         removed = np.ascontiguousarray(removed, dtype=np.int32)
         I = np.ascontiguousarray(self.I)
         lib().ox_hand_over(self.h, len(removed), _p(removed, C.c_int32), _p(I, C.c_double))

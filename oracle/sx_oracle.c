@@ -27,6 +27,12 @@
  *   Sect. 2.2.4  combined transport: ballistic where the optical depth is
  *                high, direction conserving where it is low; photons change
  *                representation (bins <-> edges) on arrival.
+ *   Sect. 2.2.1, 4.5  diffuse recombination radiation (optional; the paper's
+ *                tests use the on-the-spot approximation instead): case A
+ *                recombination, and every recombination straight to the
+ *                ground level emits an ionising photon that leaves its cell
+ *                with no memory of direction, so every ionised cell is a
+ *                source.
  *
  * Readings of points the paper leaves open (all listed in the design notes):
  *   - association: bin b of vertex i goes with the edge k maximising the dot
@@ -51,7 +57,14 @@
  *     photons per in-edge (bins arriving along an edge summed into it), a
  *     direction-conserving vertex keeps bins (a packet arriving along an edge
  *     goes to the bin closest to the direction it travelled);
- *   - a ballistic source sends its photons in equal parts along all edges.
+ *   - a ballistic source sends its photons in equal parts along all edges;
+ *   - diffuse radiation (direction conserving only): the recombinations of
+ *     a step are summed over its subcycles (the hold after equilibrium at
+ *     the last subcycle's rate); a fraction (alpha_A - alpha_B) / alpha_A of
+ *     them emit one photon each; a cell's photons of one step enter its
+ *     incoming store in the next step, an equal share in every bin, after
+ *     the sources' photons, as a source's photons do (the cell absorbs
+ *     first).
  *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
  * (-ffp-contract=off keeps every a*b+c a separate multiply and add so that the
@@ -286,14 +299,20 @@ double ox_kappa(int64_t n, const double *pos, const int64_t *row_ptr, const int3
 /* Returns the transmitted fraction f = (1/dt) sum_k e^{-tau_k} h_k, so that */
 /* N_out = f N_in and N_abs = (1 - f) N_in.                                  */
 /* ------------------------------------------------------------------------ */
-double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, double R0,
-               double fc, double tol, int max_sub, int *nsub_out, int *capped_out) {
+/* rec_out (may be NULL): recombinations per atom during the step,         */
+/* sum_k R0 x_k^2 h_k (the hold after equilibrium at the last subcycle's     */
+/* rate).                                                                    */
+double ox_chem_rec(double *y_io, double N_in, double dt, double A, double tau_max, double R0,
+                   double fc, double tol, int max_sub, int *nsub_out, int *capped_out,
+                   double *rec_out) {
     double y = *y_io;
+    if (rec_out) *rec_out = 0.0;
     if (!(A > 0.0)) {              /* no atoms (n_H = 0): tau = 0, the cell is transparent */
         if (nsub_out) *nsub_out = 0;
         if (capped_out) *capped_out = 0;
         return 1.0;
     }
+    double rec_int = 0.0;          /* integral of R0 x^2 dt */
     double F = N_in / dt;          /* photons per second, constant over the step */
     double t_left = dt;
     double trans_int = 0.0;        /* integral of e^{-tau} dt */
@@ -314,6 +333,7 @@ double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, d
         }
         double y_new = y + (rec - ion) * h;
         trans_int += tr * h;
+        rec_int += rec * h;
         t_left = (h == t_left) ? 0.0 : t_left - h;
         nsub++;
         int eq = fabs(y_new - y) <= tol * y_new;
@@ -322,13 +342,20 @@ double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, d
             /* equilibrium (or cap): keep the last subcycle's values */
             if (!eq) capped = 1;
             trans_int += tr * t_left;
+            rec_int += rec * t_left;
             t_left = 0.0;
         }
     }
     *y_io = y;
     if (nsub_out) *nsub_out = nsub;
     if (capped_out) *capped_out = capped;
+    if (rec_out) *rec_out = rec_int;
     return trans_int / dt;
+}
+
+double ox_chem(double *y_io, double N_in, double dt, double A, double tau_max, double R0,
+               double fc, double tol, int max_sub, int *nsub_out, int *capped_out) {
+    return ox_chem_rec(y_io, N_in, dt, A, tau_max, R0, fc, tol, max_sub, nsub_out, capped_out, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -433,6 +460,10 @@ typedef struct {
     double *Ev;             /* nnz: a thick vertex's photons per in-edge */
     double *S;              /* n: a thick source's photons of this step */
     uint8_t *thick;         /* n: the vertex's mode in the current step */
+    /* diffuse recombination radiation (Sect. 2.2.1, 4.5) */
+    double ground;          /* (alpha_A - alpha_B) / alpha_A */
+    double *D;              /* n, or NULL: recombination photons of the last step, emitted next */
+    double diffuse_emitted; /* photons emitted by recombining cells so far */
 } ox_sim;
 
 typedef struct {
@@ -442,11 +473,14 @@ typedef struct {
     int chem_max_sub;
     int transport;      /* 0 direction conserving, 1 ballistic, 2 combined */
     double tau_switch;  /* combined: ballistic where y tau_max >= tau_switch */
+    double alpha_A;     /* 0: on-the-spot (case B); > 0: case A with the ground-level
+                           recombination photons re-emitted (direction conserving only) */
 } ox_params;
 
 ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_t *row_ptr,
                   const int32_t *col, const double *nH, const double *vol, const uint8_t *flags,
                   const double *y0, const double *bins) {
+    if (p->alpha_A != 0.0 && (p->transport != 0 || !(p->alpha_A >= p->alpha_B))) return NULL;
     ox_sim *s = (ox_sim *)calloc(1, sizeof(ox_sim));
     int64_t nnz = row_ptr[n];
     s->n = n;
@@ -474,7 +508,7 @@ ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_
     for (int64_t i = 0; i < n; ++i) {
         s->A[i] = nH[i] * vol[i];
         s->tau_max[i] = nH[i] * p->sigma * (s->kappa * s->mean_len[i]);
-        s->R0[i] = p->alpha_B * nH[i];
+        s->R0[i] = (p->alpha_A > 0.0 ? p->alpha_A : p->alpha_B) * nH[i];
         s->y[i] = y0 ? y0[i] : 1.0;
     }
     size_t nI = (size_t)n * (size_t)p->nbins;
@@ -486,6 +520,10 @@ ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_
     s->max_sub = p->chem_max_sub;
     s->transport = p->transport;
     s->tau_switch = p->tau_switch;
+    if (p->alpha_A > 0.0) {
+        s->ground = (p->alpha_A - p->alpha_B) / p->alpha_A;
+        s->D = (double *)calloc((size_t)n + 1, sizeof(double));
+    }
     if (s->transport != 0) {
         size_t m = nnz ? (size_t)nnz : 1;
         s->stb = (uint8_t *)malloc(4 * m);
@@ -508,7 +546,7 @@ void ox_destroy(ox_sim *s) {
     free(s->straight); free(s->mean_len); free(s->A); free(s->tau_max); free(s->R0);
     free(s->y); free(s->I); free(s->Inew); free(s->src_v); free(s->src_rate);
     free(s->stb); free(s->twin); free(s->Pb); free(s->Pbn); free(s->Pe); free(s->Pen);
-    free(s->Ev); free(s->S); free(s->thick);
+    free(s->Ev); free(s->S); free(s->thick); free(s->D);
     free(s);
 }
 
@@ -559,6 +597,20 @@ static void ox_one_step(ox_sim *s, double dt) {
         s->budget[0] += Nstep;
     }
 
+    /* diffuse radiation: every cell emits the ground-level recombination
+       photons of the last step like a source, an equal share in every bin */
+    if (s->D) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(s->D[i] > 0.0)) continue;
+            double share = s->D[i] / nb;
+            double *Iv = s->I + (size_t)i * nb;
+            for (int b = 0; b < nb; ++b) Iv[b] += share;
+            s->budget[0] += s->D[i];
+            s->diffuse_emitted += s->D[i];
+            s->D[i] = 0.0;
+        }
+    }
+
     memset(s->Inew, 0, sizeof(double) * (size_t)n * nb);
     for (int64_t i = 0; i < n; ++i) {
         double *Ii = s->I + (size_t)i * nb;
@@ -569,10 +621,12 @@ static void ox_one_step(ox_sim *s, double dt) {
             continue;
         }
         int nsub = 0, capped = 0;
-        double f = ox_chem(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
-                           s->max_sub, &nsub, &capped);
+        double rec = 0.0;
+        double f = ox_chem_rec(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
+                               s->max_sub, &nsub, &capped, &rec);
         s->total_sub += nsub;
         s->total_capped += capped;
+        if (s->D) s->D[i] = s->ground * (s->A[i] * rec);
         int64_t r0 = s->row_ptr[i], r1 = s->row_ptr[i + 1];
         double out_sum = 0.0;
         for (int b = 0; b < nb; ++b) {
@@ -898,4 +952,11 @@ void ox_hand_over(const ox_sim *s, int64_t nr, const int32_t *removed, double *I
 }
 
 void ox_set_step(ox_sim *s, int64_t step) { s->step = step; }
+
+/* Diffuse radiation: each cell's photons waiting for the next step (zeros
+   without diffuse radiation) and the photons recombining cells emitted. */
+double ox_get_diffuse(const ox_sim *s, double *pending) {
+    for (int64_t i = 0; i < s->n; ++i) pending[i] = s->D ? s->D[i] : 0.0;
+    return s->diffuse_emitted;
+}
 void ox_set_budget(ox_sim *s, const double *b) { memcpy(s->budget, b, sizeof(double) * 4); }
