@@ -292,7 +292,6 @@ int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz);
 int sx_restore(sx_ctx *ctx, const char *path, void *d_workspace, int64_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
- * Launch shape of the step kernel/* ---------------------------------------------------------------------------
  * Launch shape of the step kernel (a system choice, no counterpart in the
  * paper).  A step launch works on 32-vertex tiles; its variant is the number
  * of consecutive vertices one warp works on: 4 (8 warps per tile, the

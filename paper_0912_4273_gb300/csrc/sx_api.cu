@@ -74,8 +74,9 @@ struct sx_ctx {
 static thread_local std::string g_create_err;
 static constexpr int kGraphSteps = sx::kRotAhead;  // one rotation launch per graph
 static_assert(sx::kRotAhead == SX_STEP_BLOCK, "the step block of the header");
-static_assert(sx::kTransportDct == SX_TRANSPORT_DCT && sx::kTransportBallistic == SX_TRANSPORT_BALLISTIC &&
-                  sx::kTransportCombined == SX_TRANSPORT_COMBINED,
+static_assert(int(sx::kTransportDct) == int(SX_TRANSPORT_DCT) &&
+                  int(sx::kTransportBallistic) == int(SX_TRANSPORT_BALLISTIC) &&
+                  int(sx::kTransportCombined) == int(SX_TRANSPORT_COMBINED),
               "transport values of the header");
 
 static int fail(sx_ctx *c, int code, const std::string &msg) {
@@ -195,7 +196,7 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   SX_CUDA(c, cudaMemcpyAsync(*bins_dev, c->bins.data(), sizeof(double) * c->bins.size(),
                              cudaMemcpyHostToDevice, st));
   // tables
-  SX_CUDA(c, sx::launch_setup(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa, st));
+  SX_CUDA(c, sx::launch_setup(g, st));
   if (g.stb) {  // ballistic and combined transport: no packets yet, every vertex thin so far
     SX_CUDA(c, cudaMemsetAsync(base + L.off_B0, 0, L.off_stb - L.off_B0, st));
     SX_CUDA(c, sx::launch_ballistic_tables(g, st));

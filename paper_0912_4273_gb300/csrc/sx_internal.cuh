@@ -270,8 +270,7 @@ struct Layout {
 Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transport = 0);
 void bind_layout(DevGrid &g, void *base, const Layout &L);
 
-cudaError_t launch_setup(DevGrid &g, const double *bins_dev, double sigma, double alpha_B,
-                         double kappa_cfg, cudaStream_t st);
+cudaError_t launch_setup(DevGrid &g, cudaStream_t st);
 cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double sigma,
                                     double alpha_B, double kappa_cfg, const double *y0_dev,
                                     cudaStream_t st);

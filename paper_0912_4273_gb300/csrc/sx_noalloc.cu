@@ -131,7 +131,7 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   if (nnz) NA_CUDA(cudaMemcpyAsync(g.s_col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemcpyAsync(g.s_flags, flags, n, cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemcpyAsync(bins_dev, bin_dirs, sizeof(double) * 3 * nbins, cudaMemcpyHostToDevice, st));
-  NA_CUDA(sx::launch_setup(g, bins_dev, 0.0, 0.0, 0.0, st));
+  NA_CUDA(sx::launch_setup(g, st));
   NA_CUDA(sx::launch_rotation(g, bins_dev, 0, 1, 1, 1.0, st));
   NA_CUDA(sx::launch_kappa(g, bins_dev, st));
   unsigned long long diag[sx::kDiagCount];

@@ -405,17 +405,14 @@ __global__ void k_vconst(int64_t n, const double *__restrict__ nH, const double 
   y[i] = y0 ? y0[i] : 1.0;
 }
 
-cudaError_t launch_setup(DevGrid &g, const double *bins_dev, double sigma, double alpha_B,
-                         double kappa_cfg, cudaStream_t st) {
+cudaError_t launch_setup(DevGrid &g, cudaStream_t st) {
   const int64_t n = g.n;
   const int T = 256;
   k_row_ptr<<<(unsigned)((n + 1 + T - 1) / T), T, 0, st>>>(n, g.s_row_ptr, g.s_flags, g.row_ptr,
                                                           g.diag);
   k_edges<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(n, g.pos, g.row_ptr, g.s_col, g.edges,
                                                      g.mean_len, g.s_ev, g.diag);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double sigma,
