@@ -192,7 +192,7 @@ class Params:
     transport: int = 0          # 0 direction conserving, 1 ballistic, 2 combined
     tau_switch: float = 1.0     # combined: ballistic where y tau_max >= tau_switch (Sect. 5.1.3)
     alpha_A: float = 0.0        # 0: on-the-spot (case B); > 0: case A with the ground-level
-                                # recombination photons re-emitted (Sect. 2.2.1; DCT only)
+                                # recombination photons re-emitted (Sect. 2.2.1)
 
 
 class _CParams(C.Structure):
@@ -234,8 +234,7 @@ class OracleSim:
                              _p(k["vol"], C.c_double), _p(k["flags"], C.c_uint8), y0p,
                              _p(k["bins"], C.c_double))
         if not self.h:
-            raise ValueError("diffuse radiation needs direction-conserving transport and "
-                             "alpha_A >= alpha_B")
+            raise ValueError("diffuse radiation needs alpha_A >= alpha_B")
         for v, r in zip(problem.src_vertex, problem.src_rate):
             if L.ox_add_source(self.h, int(v), float(r)) != 0:
                 raise ValueError("bad source vertex")

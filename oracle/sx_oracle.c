@@ -58,13 +58,14 @@
  *     direction-conserving vertex keeps bins (a packet arriving along an edge
  *     goes to the bin closest to the direction it travelled);
  *   - a ballistic source sends its photons in equal parts along all edges;
- *   - diffuse radiation (direction conserving only): the recombinations of
- *     a step are summed over its subcycles (the hold after equilibrium at
- *     the last subcycle's rate); a fraction (alpha_A - alpha_B) / alpha_A of
- *     them emit one photon each; a cell's photons of one step enter its
- *     incoming store in the next step, an equal share in every bin, after
- *     the sources' photons, as a source's photons do (the cell absorbs
- *     first).
+ *   - diffuse radiation: the recombinations of a step are summed over its
+ *     subcycles (the hold after equilibrium at the last subcycle's rate); a
+ *     fraction (alpha_A - alpha_B) / alpha_A of them emit one photon each; a
+ *     cell's photons of one step enter in the next step, after the sources'
+ *     photons and as a source's photons do (the cell absorbs first): an
+ *     equal share in every bin at a direction-conserving vertex, the
+ *     vertex's own photons, sent to all neighbours in equal parts, at a
+ *     ballistic one.
  *
  * Build: cc -O2 -std=c11 -ffp-contract=off -fno-fast-math -fPIC -shared
  * (-ffp-contract=off keeps every a*b+c a separate multiply and add so that the
@@ -474,13 +475,13 @@ typedef struct {
     int transport;      /* 0 direction conserving, 1 ballistic, 2 combined */
     double tau_switch;  /* combined: ballistic where y tau_max >= tau_switch */
     double alpha_A;     /* 0: on-the-spot (case B); > 0: case A with the ground-level
-                           recombination photons re-emitted (direction conserving only) */
+                           recombination photons re-emitted */
 } ox_params;
 
 ox_sim *ox_create(const ox_params *p, int64_t n, const double *pos, const int64_t *row_ptr,
                   const int32_t *col, const double *nH, const double *vol, const uint8_t *flags,
                   const double *y0, const double *bins) {
-    if (p->alpha_A != 0.0 && (p->transport != 0 || !(p->alpha_A >= p->alpha_B))) return NULL;
+    if (p->alpha_A != 0.0 && !(p->alpha_A >= p->alpha_B)) return NULL;
     ox_sim *s = (ox_sim *)calloc(1, sizeof(ox_sim));
     int64_t nnz = row_ptr[n];
     s->n = n;
@@ -667,8 +668,8 @@ static void ox_one_step(ox_sim *s, double dt) {
    the bin closest to the direction they travelled), a thick vertex per
    in-edge.  A thin vertex sends its bins as in ox_one_step; a thick vertex
    sends the photons of each in-edge to that edge's ballistic straight set,
-   and a thick source its own photons to all neighbours in equal parts
-   (Sect. 2.2.1). */
+   and a thick source (or a thick cell re-emitting recombination photons)
+   its own photons to all neighbours in equal parts (Sect. 2.2.1). */
 static void ox_one_step_ballistic(ox_sim *s, double dt) {
     const int nb = s->nbins;
     const int64_t n = s->n;
@@ -734,6 +735,24 @@ static void ox_one_step_ballistic(ox_sim *s, double dt) {
         }
     }
 
+    /* diffuse radiation: the ground-level recombination photons of the last
+       step, emitted like a source's */
+    if (s->D) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (!(s->D[i] > 0.0)) continue;
+            if (s->thick[i]) {
+                s->S[i] += s->D[i];
+            } else {
+                double share = s->D[i] / nb;
+                double *Iv = s->I + (size_t)i * nb;
+                for (int b = 0; b < nb; ++b) Iv[b] += share;
+            }
+            s->budget[0] += s->D[i];
+            s->diffuse_emitted += s->D[i];
+            s->D[i] = 0.0;
+        }
+    }
+
     /* interaction and transport */
     memset(s->Pbn, 0, sizeof(double) * (size_t)(nnz ? nnz : 1) * nb);
     memset(s->Pen, 0, sizeof(double) * (size_t)(nnz ? nnz : 1));
@@ -752,10 +771,12 @@ static void ox_one_step_ballistic(ox_sim *s, double dt) {
             continue;
         }
         int nsub = 0, capped = 0;
-        double f = ox_chem(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
-                           s->max_sub, &nsub, &capped);
+        double rec = 0.0;
+        double f = ox_chem_rec(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
+                               s->max_sub, &nsub, &capped, &rec);
         s->total_sub += nsub;
         s->total_capped += capped;
+        if (s->D) s->D[i] = s->ground * (s->A[i] * rec);
         double out_sum = 0.0;
         if (!s->thick[i]) {
             for (int b = 0; b < nb; ++b) {
