@@ -110,3 +110,23 @@ def test_interior_profile_close_to_equilibrium(run42, paper):
 def test_bin_count_converged(run42):
     _, _, out84 = _run(84)
     assert abs(out84[-1][1] / run42[2][-1][1] - 1) < 0.03
+
+
+def test_subcycling_reading_does_not_move_the_front():
+    """The paper does not fix the subcycle length or the equilibrium test
+    (Sect. 4.5).  A ten times shorter subcycle (0.05 / (Gamma + R)), a
+    10^4 cap and a 1e-9 equilibrium tolerance move the Test-1 front by
+    less than 0.5% at every sampled time, at five times the subcycles."""
+    prob = I.stromgren_problem(8192, seed=0)
+    bins = I.fibonacci_bins(42)
+    runs = []
+    for kw in ({}, dict(chem_frac=0.05, chem_tol=1e-9, chem_max_sub=10000)):
+        s = O.OracleSim(prob, O.Params(nbins=42, seed=0, **kw), bins)
+        r = []
+        for _ in range(5):
+            s.step(2.5 * I.MYR_S, 40)
+            r.append(O.ionised_radius_sphere(s.y, prob.volume, prob.interior))
+        runs.append((np.array(r), s.stats))
+    (r0, st0), (r1, st1) = runs
+    assert np.abs(r1 / r0 - 1).max() < 5e-3
+    assert st1["subcycles"] > 3 * st0["subcycles"] and st0["capped"] == st1["capped"] == 0
