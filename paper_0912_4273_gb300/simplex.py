@@ -410,6 +410,7 @@ class Batch:
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         nbytes = sx_batch_workspace_bytes(max_grids)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.workspace.record_stream(self.stream)  # freed memory waits for this stream's work
         self.handle = sx_batch_create(max_grids, device, self.stream.cuda_stream,
                                       self.workspace.data_ptr(), nbytes)
 
@@ -440,6 +441,9 @@ class Solver:
     The workspace (per-grid device state) is a torch uint8 tensor on the
     context's device, so that memory comes from PyTorch's caching allocator;
     ``stream`` is a ``torch.cuda.Stream`` (default: the current stream).
+    Every workspace is marked as used on that stream, so the allocator does
+    not hand its memory out again (after ``close``, a reload or an update)
+    before the steps queued there have run.
     """
 
     def __init__(self, bins: np.ndarray, precision: int = SX_FP32_TRANSPORT, seed: int = 0,
@@ -477,6 +481,11 @@ class Solver:
     def workspace_bytes(self, n: int, nnz: int) -> int:
         return sx_workspace_bytes(self.ctx, n, nnz)
 
+    def _new_workspace(self, nbytes: int):
+        ws = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        ws.record_stream(self.stream)
+        return ws
+
     def load(self, problem=None, *, pos=None, row_ptr=None, col=None, nH=None, volume=None,
              flags=None, y0=None, workspace=None):
         if problem is not None:
@@ -492,7 +501,9 @@ class Solver:
         n = len(pos)
         nbytes = self.workspace_bytes(n, int(row_ptr[-1]))
         if workspace is None:
-            workspace = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+            workspace = self._new_workspace(nbytes)
+        else:
+            workspace.record_stream(self.stream)
         self.workspace = workspace
         sx_load_grid(self.ctx, n, pos, row_ptr, col, nH, volume, flags, y0,
                      workspace.data_ptr(), workspace.numel())
@@ -549,8 +560,7 @@ class Solver:
         vol = np.ascontiguousarray(problem_new.volume, dtype=np.float64)
         fl = np.ascontiguousarray(problem_new.flags, dtype=np.uint8)
         o2n = np.ascontiguousarray(old_of_new, dtype=np.int32)
-        nbytes = self.workspace_bytes(len(pos), int(rp[-1]))
-        ws = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        ws = self._new_workspace(self.workspace_bytes(len(pos), int(rp[-1])))
         sx_grid_update_apply(self.ctx, len(pos), pos, rp, col, nH, vol, fl, o2n, ws.data_ptr(),
                              ws.numel())
         self.workspace = ws
@@ -568,8 +578,7 @@ class Solver:
         """Replace the grid and state by a checkpoint's (same bins and
         precision); the workspace is allocated here for its size."""
         n, nnz = sx_checkpoint_info(path)
-        nbytes = self.workspace_bytes(n, nnz)
-        ws = self._torch.empty(nbytes, dtype=self._torch.uint8, device=self.device)
+        ws = self._new_workspace(self.workspace_bytes(n, nnz))
         sx_restore(self.ctx, path, ws.data_ptr(), ws.numel())
         self.workspace = ws
         self.n = n
@@ -588,7 +597,7 @@ class Solver:
         """Time every step-kernel variant for nsteps steps from the current
         state and keep the fastest; the state is saved in a scratch copy of
         the workspace (allocated here for the call) and restored."""
-        scratch = self._torch.empty_like(self.workspace)
+        scratch = self._new_workspace(self.workspace.numel())
         try:
             r = sx_autotune(self.ctx, dt, nsteps, scratch.data_ptr(), scratch.numel())
         finally:
