@@ -17,6 +17,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <stdexcept>
 #include <system_error>
@@ -155,6 +156,33 @@ double tet_volume(const double *pos, const int32_t *t) {
   return std::fabs(orient(a, b, c, d)) / 6.0;
 }
 
+// Runs fn(0) .. fn(nth - 1) on threads; a range whose thread the system
+// refuses runs on the calling thread.  fn must not throw.
+template <class F>
+void run_threads(unsigned nth, F &&fn) {
+  std::vector<std::thread> pool;
+  pool.reserve(nth);
+  unsigned started = 0;
+  try {
+    for (; nth > 1 && started < nth; ++started) pool.emplace_back(std::ref(fn), started);
+  } catch (const std::system_error &) {
+  }
+  for (unsigned th = started; th < nth; ++th) fn(th);
+  for (std::thread &t : pool) t.join();
+}
+
+unsigned hardware_threads() { return std::max(1u, std::min(16u, std::thread::hardware_concurrency())); }
+
+// Threads for a pass over `count` items: one per 2^16 items, at most 16.
+unsigned pass_threads(int64_t count) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(hardware_threads(), count >> 16));
+}
+
+// Start of range th of nth contiguous ranges over [0, count).
+inline int64_t range_start(int64_t count, unsigned th, unsigned nth) {
+  return count * (int64_t)th / (int64_t)nth;
+}
+
 }  // namespace
 
 extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row_ptr, const int32_t *col,
@@ -166,15 +194,30 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
   if (n < 1 || !pos || !row_ptr || !col || !volume || (ntet > 0 && !tets) || nrem < 0 ||
       (nrem > 0 && !removed))
     return SX_EINVAL;
-  // the graph and the tetrahedra index the arrays below: check them first
-  if (row_ptr[0] != 0) return SX_EINVAL;
-  for (int64_t v = 0; v < n; ++v)
-    if (row_ptr[v + 1] < row_ptr[v]) return SX_EINVAL;
-  for (int64_t e = 0; e < row_ptr[n]; ++e)
-    if (col[e] < 0 || col[e] >= n) return SX_EINVAL;
-  for (int64_t i = 0; i < 4 * ntet; ++i)
-    if (tets[i] < 0 || tets[i] >= n) return SX_EINVAL;
   try {
+    // the graph and the tetrahedra index the arrays below: check them first
+    if (row_ptr[0] != 0) return SX_EINVAL;
+    for (int64_t v = 0; v < n; ++v)
+      if (row_ptr[v + 1] < row_ptr[v]) return SX_EINVAL;
+    const int64_t nnz = row_ptr[n];
+    {
+      const unsigned nt = pass_threads(nnz + 4 * ntet);
+      std::vector<char> bad(nt, 0);
+      run_threads(nt, [&](unsigned th) {
+        for (int64_t e = range_start(nnz, th, nt), e1 = range_start(nnz, th + 1, nt); e < e1; ++e)
+          if (col[e] < 0 || col[e] >= n) {
+            bad[th] = 1;
+            return;
+          }
+        for (int64_t i = range_start(4 * ntet, th, nt), i1 = range_start(4 * ntet, th + 1, nt); i < i1; ++i)
+          if (tets[i] < 0 || tets[i] >= n) {
+            bad[th] = 1;
+            return;
+          }
+      });
+      for (char b : bad)
+        if (b) return SX_EINVAL;
+    }
     std::vector<char> rem((size_t)n, 0);
     for (int64_t k = 0; k < nrem; ++k) {
       if (removed[k] < 0 || removed[k] >= n) return SX_EINVAL;
@@ -189,38 +232,54 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
         vs.push_back((int32_t)v);
       }
     const size_t ncav = vs.size();
+    // the tetrahedra with a removed corner, found by threads over ranges of
+    // tetrahedra; each star lists its tetrahedra in ascending order
     std::vector<int64_t> star_cnt(ncav + 1, 0);
     std::vector<char> tet_hit((size_t)ntet, 0);
-    for (int64_t t = 0; t < ntet; ++t) {
-      int h = 0, who = -1;
-      for (int k = 0; k < 4; ++k)
-        if (rem[(size_t)tets[4 * t + k]]) {
-          ++h;
-          who = tets[4 * t + k];
-        }
-      if (h > 1) return SX_EINVAL;  // removed vertices must not be adjacent
-      if (h == 1) {
-        tet_hit[(size_t)t] = 1;
-        ++star_cnt[(size_t)cav_of[(size_t)who] + 1];
-      }
-    }
-    for (size_t c = 0; c < ncav; ++c) star_cnt[c + 1] += star_cnt[c];
-    std::vector<int64_t> star((size_t)star_cnt[ncav]);
+    std::vector<int64_t> star;
     {
-      std::vector<int64_t> fill(star_cnt.begin(), star_cnt.end() - 1);
-      for (int64_t t = 0; t < ntet; ++t) {
-        if (!tet_hit[(size_t)t]) continue;
-        int who = -1;
-        for (int k = 0; k < 4; ++k)
-          if (rem[(size_t)tets[4 * t + k]]) who = tets[4 * t + k];
-        star[(size_t)fill[(size_t)cav_of[(size_t)who]]++] = t;
+      const unsigned nt = pass_threads(ntet);
+      std::vector<std::vector<int64_t>> hits(nt);
+      std::vector<char> adjacent(nt, 0), oom(nt, 0);
+      run_threads(nt, [&](unsigned th) {
+        try {
+          for (int64_t t = range_start(ntet, th, nt), t1 = range_start(ntet, th + 1, nt); t < t1; ++t) {
+            int h = 0;
+            for (int k = 0; k < 4; ++k) h += rem[(size_t)tets[4 * t + k]];
+            if (h > 1) {  // removed vertices must not be adjacent
+              adjacent[th] = 1;
+              return;
+            }
+            if (h == 1) {
+              tet_hit[(size_t)t] = 1;
+              hits[th].push_back(t);
+            }
+          }
+        } catch (const std::exception &) {
+          oom[th] = 1;
+        }
+      });
+      for (unsigned th = 0; th < nt; ++th) {
+        if (oom[th]) return SX_ENOMEM;
+        if (adjacent[th]) return SX_EINVAL;
       }
+      auto cavity = [&](int64_t t) {
+        for (int k = 0; k < 4; ++k)
+          if (rem[(size_t)tets[4 * t + k]]) return cav_of[(size_t)tets[4 * t + k]];
+        return (int64_t)-1;
+      };
+      for (const auto &hv : hits)
+        for (int64_t t : hv) ++star_cnt[(size_t)cavity(t) + 1];
+      for (size_t c = 0; c < ncav; ++c) star_cnt[c + 1] += star_cnt[c];
+      star.resize((size_t)star_cnt[ncav]);
+      std::vector<int64_t> fill(star_cnt.begin(), star_cnt.end() - 1);
+      for (const auto &hv : hits)
+        for (int64_t t : hv) star[(size_t)fill[(size_t)cavity(t)]++] = t;
     }
     // fill every cavity: threads take contiguous ranges of cavities, and their
     // tetrahedra are joined in cavity order (the result does not depend on
     // the thread count)
-    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const unsigned nth = ncav < 64 ? 1u : std::min<unsigned>(hw, (unsigned)(ncav / 32));
+    const unsigned nth = ncav < 64 ? 1u : std::min<unsigned>(hardware_threads(), (unsigned)(ncav / 32));
     std::vector<std::vector<int32_t>> part(nth);
     std::vector<int32_t> failed(nth, -1);
     std::vector<char> no_memory(nth, 0);
@@ -278,18 +337,7 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
         no_memory[th] = 1;
       }
     };
-    {
-      // ranges that get no thread (the system refuses one) run on this one
-      std::vector<std::thread> pool;
-      pool.reserve(nth);
-      unsigned started = 0;
-      try {
-        for (; nth > 1 && started < nth; ++started) pool.emplace_back(fill_range, started);
-      } catch (const std::system_error &) {
-      }
-      for (unsigned th = started; th < nth; ++th) fill_range(th);
-      for (std::thread &t : pool) t.join();
-    }
+    run_threads(nth, fill_range);
     for (unsigned th = 0; th < nth; ++th)
       if (no_memory[th]) return SX_ENOMEM;
     for (unsigned th = 0; th < nth; ++th)
@@ -305,23 +353,38 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
       for (const auto &pv : part) new_tets.insert(new_tets.end(), pv.begin(), pv.end());
     }
     const int64_t nnew = (int64_t)new_tets.size() / 4;
-    // new edges per vertex (both directions), sorted and unique
-    std::vector<std::vector<int32_t>> add_of;  // indexed by position among the link vertices
-    std::vector<int64_t> add_idx((size_t)n, -1);
-    for (int64_t t = 0; t < nnew; ++t)
-      for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) {
-          if (a == b) continue;
-          const int32_t u = new_tets[4 * t + a], w = new_tets[4 * t + b];
-          if (add_idx[(size_t)u] < 0) {
-            add_idx[(size_t)u] = (int64_t)add_of.size();
-            add_of.emplace_back();
-          }
-          add_of[(size_t)add_idx[(size_t)u]].push_back(w);
+    // new edges per vertex (both directions), sorted and unique: one list per
+    // link vertex (add_idx: its list, or -1), laid out by counting
+    std::vector<int32_t> add_idx((size_t)n, -1);
+    std::vector<int64_t> add_ptr(1, 0);
+    for (int64_t i = 0; i < 4 * nnew; ++i) {
+      const int32_t u = new_tets[(size_t)i];
+      if (add_idx[(size_t)u] < 0) {
+        add_idx[(size_t)u] = (int32_t)(add_ptr.size() - 1);
+        add_ptr.push_back(0);
+      }
+      add_ptr[(size_t)add_idx[(size_t)u] + 1] += 3;
+    }
+    const size_t nlink = add_ptr.size() - 1;
+    for (size_t k = 0; k < nlink; ++k) add_ptr[k + 1] += add_ptr[k];
+    std::vector<int32_t> add_col((size_t)add_ptr[nlink]);
+    {
+      std::vector<int64_t> fill(add_ptr.begin(), add_ptr.end() - 1);
+      for (int64_t t = 0; t < nnew; ++t)
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b)
+            if (a != b) add_col[(size_t)fill[(size_t)add_idx[(size_t)new_tets[4 * t + a]]]++] = new_tets[4 * t + b];
+    }
+    std::vector<int64_t> add_len(nlink);  // each list sorted, its unique entries first
+    {
+      const unsigned nt = pass_threads(add_ptr[nlink]);
+      run_threads(nt, [&](unsigned th) {
+        for (int64_t k = range_start((int64_t)nlink, th, nt), k1 = range_start((int64_t)nlink, th + 1, nt); k < k1; ++k) {
+          int32_t *b = add_col.data() + add_ptr[(size_t)k], *e = add_col.data() + add_ptr[(size_t)k + 1];
+          std::sort(b, e);
+          add_len[(size_t)k] = std::unique(b, e) - b;
         }
-    for (auto &l : add_of) {
-      std::sort(l.begin(), l.end());
-      l.erase(std::unique(l.begin(), l.end()), l.end());
+      });
     }
     // renumbering of the survivors, in their old order
     std::vector<int32_t> new_of_old((size_t)n, -1);
@@ -331,10 +394,10 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
     // the outputs, allocated once at their final size (the graph at an upper
     // bound, trimmed at the end)
     size_t nadd = 0;
-    for (const auto &l : add_of) nadd += l.size();
+    for (int64_t len : add_len) nadd += (size_t)len;
     const int64_t ntet2 = ntet - (int64_t)star.size() + nnew;
     out->row_ptr = static_cast<int64_t *>(std::malloc(sizeof(int64_t) * ((size_t)n2 + 1)));
-    out->col = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * ((size_t)row_ptr[n] + nadd + 1)));
+    out->col = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * ((size_t)nnz + nadd + 1)));
     out->volume = static_cast<double *>(std::malloc(sizeof(double) * ((size_t)n2 + 1)));
     out->old_of_new = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * ((size_t)n2 + 1)));
     out->tets = static_cast<int32_t *>(std::malloc(sizeof(int32_t) * (4 * (size_t)ntet2 + 1)));
@@ -343,57 +406,92 @@ extern "C" int sx_remesh_remove(int64_t n, const double *pos, const int64_t *row
       return SX_ENOMEM;
     }
     // the graph: each survivor's row without removed neighbours, merged with
-    // its new neighbours (both ascending)
+    // its new neighbours (both ascending); threads over ranges of vertices
+    // count the rows, then write them at their offsets
     int64_t *rp2 = out->row_ptr;
     int32_t *col2 = out->col;
-    int64_t m = 0;
-    rp2[0] = 0;
-    for (int64_t v = 0; v < n; ++v) {
-      if (rem[(size_t)v]) continue;
-      const std::vector<int32_t> *ad = add_idx[(size_t)v] >= 0 ? &add_of[(size_t)add_idx[(size_t)v]] : nullptr;
-      size_t ai = 0;
+    auto merge_row = [&](int64_t v, auto &&emit) {
+      const int32_t *a = nullptr, *a1 = nullptr;  // v's new neighbours, ascending
+      if (add_idx[(size_t)v] >= 0) {
+        a = add_col.data() + add_ptr[(size_t)add_idx[(size_t)v]];
+        a1 = a + add_len[(size_t)add_idx[(size_t)v]];
+      }
       for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
         const int32_t w = col[e];
-        while (ad && ai < ad->size() && (*ad)[ai] < w) {
-          if (!rem[(size_t)(*ad)[ai]]) col2[m++] = new_of_old[(size_t)(*ad)[ai]];
-          ++ai;
-        }
-        if (ad && ai < ad->size() && (*ad)[ai] == w) ++ai;  // already an edge
-        if (!rem[(size_t)w]) col2[m++] = new_of_old[(size_t)w];
+        for (; a < a1 && *a < w; ++a)
+          if (!rem[(size_t)*a]) emit(new_of_old[(size_t)*a]);
+        if (a < a1 && *a == w) ++a;  // already an edge
+        if (!rem[(size_t)w]) emit(new_of_old[(size_t)w]);
       }
-      while (ad && ai < ad->size()) {
-        if (!rem[(size_t)(*ad)[ai]]) col2[m++] = new_of_old[(size_t)(*ad)[ai]];
-        ++ai;
+      for (; a < a1; ++a)
+        if (!rem[(size_t)*a]) emit(new_of_old[(size_t)*a]);
+    };
+    const unsigned ntg = pass_threads(nnz);
+    rp2[0] = 0;
+    run_threads(ntg, [&](unsigned th) {
+      for (int64_t v = range_start(n, th, ntg), v1 = range_start(n, th + 1, ntg); v < v1; ++v) {
+        if (rem[(size_t)v]) continue;
+        int64_t len = 0;
+        merge_row(v, [&](int32_t) { ++len; });
+        rp2[(size_t)new_of_old[(size_t)v] + 1] = len;
       }
-      rp2[(size_t)new_of_old[(size_t)v] + 1] = m;
-    }
+    });
+    for (int64_t i = 0; i < n2; ++i) rp2[i + 1] += rp2[i];
+    run_threads(ntg, [&](unsigned th) {
+      for (int64_t v = range_start(n, th, ntg), v1 = range_start(n, th + 1, ntg); v < v1; ++v) {
+        if (rem[(size_t)v]) continue;
+        int64_t m = rp2[(size_t)new_of_old[(size_t)v]];
+        merge_row(v, [&](int32_t w) { col2[m++] = w; });
+      }
+    });
+    const int64_t m = rp2[n2];
     if (int32_t *shrunk = static_cast<int32_t *>(std::realloc(out->col, sizeof(int32_t) * ((size_t)m + 1))))
       out->col = shrunk;
-    // cell volumes: a quarter of each old cavity tetrahedron leaves its
-    // corners, a quarter of each new one joins them
-    std::vector<double> vol(volume, volume + n);
+    // cell volumes: each survivor's old volume, then a quarter of each old
+    // cavity tetrahedron leaves its surviving corners and a quarter of each
+    // new one joins its corners (all survivors: the link of a removed vertex
+    // holds no removed vertex)
+    run_threads(pass_threads(n), [&, nt = pass_threads(n)](unsigned th) {
+      for (int64_t v = range_start(n, th, nt), v1 = range_start(n, th + 1, nt); v < v1; ++v) {
+        const int32_t w = new_of_old[(size_t)v];
+        if (w < 0) continue;
+        out->volume[w] = volume[v];
+        out->old_of_new[w] = (int32_t)v;
+      }
+    });
     for (size_t s = 0; s < star.size(); ++s) {
       const int32_t *q = tets + 4 * star[s];
       const double qv = 0.25 * tet_volume(pos, q);
-      for (int k = 0; k < 4; ++k) vol[(size_t)q[k]] -= qv;
+      for (int k = 0; k < 4; ++k)
+        if (new_of_old[(size_t)q[k]] >= 0) out->volume[new_of_old[(size_t)q[k]]] -= qv;
     }
     for (int64_t t = 0; t < nnew; ++t) {
       const double qv = 0.25 * tet_volume(pos, &new_tets[4 * t]);
-      for (int k = 0; k < 4; ++k) vol[(size_t)new_tets[4 * t + k]] += qv;
+      for (int k = 0; k < 4; ++k) out->volume[new_of_old[(size_t)new_tets[4 * t + k]]] += qv;
     }
-    for (int64_t v = 0; v < n; ++v) {
-      const int32_t w = new_of_old[(size_t)v];
-      if (w < 0) continue;
-      out->volume[w] = vol[(size_t)v];
-      out->old_of_new[w] = (int32_t)v;
+    // tetrahedra: the untouched ones (threads over ranges, each writing at
+    // the count of untouched ones before its range), then the new ones,
+    // renumbered
+    {
+      const unsigned nt = pass_threads(ntet);
+      std::vector<int64_t> base(nt + 1, 0);
+      run_threads(nt, [&](unsigned th) {
+        int64_t c = 0;
+        for (int64_t t = range_start(ntet, th, nt), t1 = range_start(ntet, th + 1, nt); t < t1; ++t)
+          c += !tet_hit[(size_t)t];
+        base[th + 1] = c;
+      });
+      for (unsigned th = 0; th < nt; ++th) base[th + 1] += base[th];
+      run_threads(nt, [&](unsigned th) {
+        int32_t *t2 = out->tets + 4 * base[th];
+        for (int64_t t = range_start(ntet, th, nt), t1 = range_start(ntet, th + 1, nt); t < t1; ++t) {
+          if (tet_hit[(size_t)t]) continue;
+          for (int k = 0; k < 4; ++k) *t2++ = new_of_old[(size_t)tets[4 * t + k]];
+        }
+      });
+      int32_t *t2 = out->tets + 4 * base[nt];
+      for (int64_t t = 0; t < 4 * nnew; ++t) *t2++ = new_of_old[(size_t)new_tets[t]];
     }
-    // tetrahedra: the untouched ones, then the new ones, renumbered
-    int32_t *t2 = out->tets;
-    for (int64_t t = 0; t < ntet; ++t) {
-      if (tet_hit[(size_t)t]) continue;
-      for (int k = 0; k < 4; ++k) *t2++ = new_of_old[(size_t)tets[4 * t + k]];
-    }
-    for (int64_t t = 0; t < 4 * nnew; ++t) *t2++ = new_of_old[(size_t)new_tets[t]];
     out->n = n2;
     out->nnz = m;
     out->ntet = ntet2;

@@ -228,9 +228,35 @@ def sx_remesh_free(result: "sx_remesh_result"):
     lib().sx_remesh_free(C.byref(result))
 
 
+class _RemeshArrays:
+    """Owns the arrays of one sx_remesh_remove result and frees them when the
+    last numpy array over any of them is gone."""
+
+    def __init__(self, res: "sx_remesh_result"):
+        self.res = res
+        self._free = lib().sx_remesh_free  # bound now: no lock in the finaliser
+
+    def view(self, ptr, ctype, count: int, dtype, shape=None) -> np.ndarray:
+        if count == 0:
+            a = np.empty(0, dtype=dtype)
+        else:
+            buf = (ctype * count).from_address(C.cast(ptr, C.c_void_p).value)
+            buf._owner = self  # every array over the result keeps it alive
+            a = np.frombuffer(buf, dtype=dtype)
+        return a.reshape(shape) if shape is not None else a
+
+    def __del__(self):
+        try:
+            self._free(C.byref(self.res))
+        except Exception:
+            pass
+
+
 def sx_remesh_remove(pos, row_ptr, col, tets, volume, removed) -> dict:
     """The grid without the `removed` vertices (see include/simplexgb.h):
-    dict of row_ptr, col, volume, tets, old_of_new (numpy copies)."""
+    dict of row_ptr, col, volume, tets, old_of_new.  The arrays lie in the
+    memory the library allocated (no copy); it is freed when the last of
+    them is gone."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     cl = np.ascontiguousarray(col, dtype=np.int32)
@@ -243,16 +269,12 @@ def sx_remesh_remove(pos, row_ptr, col, tets, volume, removed) -> dict:
                                 _ptr(vol, C.c_double), len(rem), _ptr(rem, C.c_int32), C.byref(res))
     if rc != SX_OK:
         raise RemeshError(rc, res.bad_vertex)
-    try:
-        out = dict(row_ptr=np.ctypeslib.as_array(res.row_ptr, (res.n + 1,)).copy(),
-                   col=np.ctypeslib.as_array(res.col, (max(res.nnz, 1),))[:res.nnz].copy(),
-                   volume=np.ctypeslib.as_array(res.volume, (res.n,)).copy(),
-                   tets=np.ctypeslib.as_array(res.tets, (max(res.ntet, 1) * 4,))[:4 * res.ntet]
-                   .reshape(res.ntet, 4).copy(),
-                   old_of_new=np.ctypeslib.as_array(res.old_of_new, (res.n,)).copy())
-    finally:
-        sx_remesh_free(res)
-    return out
+    owner = _RemeshArrays(res)
+    return dict(row_ptr=owner.view(res.row_ptr, C.c_int64, res.n + 1, np.int64),
+                col=owner.view(res.col, C.c_int32, res.nnz, np.int32),
+                volume=owner.view(res.volume, C.c_double, res.n, np.float64),
+                tets=owner.view(res.tets, C.c_int32, 4 * res.ntet, np.int32, (res.ntet, 4)),
+                old_of_new=owner.view(res.old_of_new, C.c_int32, res.n, np.int32))
 
 
 def sx_sync(ctx):

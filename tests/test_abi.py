@@ -148,3 +148,33 @@ def test_remesh_argument_errors(libpath):
         assert e.value.code == S.SX_EINVAL and e.value.vertex == -1
     r = S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [])
     assert np.array_equal(r["col"], p.col) and np.array_equal(r["old_of_new"], np.arange(p.n))
+
+
+def test_remesh_arrays_own_the_library_memory(libpath):
+    """sx_remesh_remove's arrays are numpy views of the memory the library
+    allocated: any one of them keeps the whole result alive, and the result
+    is freed (sx_remesh_free) when the last one is gone."""
+    import gc
+    import weakref
+
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    p = I.stromgren_problem(500, seed=4)
+    v = int(np.flatnonzero(p.interior)[3])
+    ref = S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [v])
+    ref = {k: np.array(a) for k, a in ref.items()}  # copies
+    r = S.sx_remesh_remove(p.pos, p.row_ptr, p.col, p.simplices, p.volume, [v])
+    b = r["tets"]
+    while not hasattr(b, "_owner"):
+        b = b.base
+    owner = weakref.ref(b._owner)
+    del b
+    tets = r["tets"][5:9]  # a view of a view
+    del r
+    gc.collect()
+    assert owner() is not None
+    assert np.array_equal(tets, ref["tets"][5:9])
+    del tets
+    gc.collect()
+    assert owner() is None

@@ -1,7 +1,8 @@
 """The host re-triangulation (Sect. 2.1.4) built with ThreadSanitizer and with
-AddressSanitizer + UndefinedBehaviorSanitizer, on enough cavities that they
-are filled by several threads: no report, and the same grid as a full QHull
-rebuild of the survivors.  Skipped where g++ has no sanitizer runtime."""
+AddressSanitizer + UndefinedBehaviorSanitizer, on a grid large enough that
+its passes and its cavity fill run on several threads: no report, and the
+same grid as a full QHull rebuild of the survivors.  Skipped where g++ has
+no sanitizer runtime."""
 import os
 import shutil
 import subprocess
@@ -17,8 +18,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def case(tmp_path_factory):
-    p = I.stromgren_problem(1 << 14, seed=3)
-    rem = _independent_interior(p, 1200, seed=1).astype(np.int32)  # 1200 cavities: 8+ threads' worth
+    # 2^16 points (about 450k tetrahedra, 1M edges) and 1200 cavities: the
+    # passes over the arrays and the cavity fill all run on several threads
+    p = I.stromgren_problem(1 << 16, seed=3)
+    rem = _independent_interior(p, 1200, seed=1).astype(np.int32)
     d = tmp_path_factory.mktemp("remesh")
     np.array([p.n, len(p.simplices), len(rem)], dtype=np.int64).tofile(d / "hdr")
     np.ascontiguousarray(p.pos, dtype=np.float64).tofile(d / "pos")
