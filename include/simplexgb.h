@@ -156,8 +156,10 @@ int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes
      d_workspace, workspace_bytes: caller-owned device memory, >= sx_workspace_bytes,
              256-byte aligned.
    Resets the step counter, the sources and the budget.  Errors: SX_EINVAL
-   (asymmetric/unsorted CSR, id out of range, self loop, non-sink degree >
-   SX_MAX_DEGREE, nnz >= 2^31), SX_ENOMEM (workspace too small), SX_ECUDA. */
+   (row_ptr not starting at 0 or decreasing -- checked on the host before
+   anything runs on the device --, asymmetric/unsorted CSR, id out of range,
+   self loop, non-sink degree > SX_MAX_DEGREE, n or nnz >= 2^31), SX_ENOMEM
+   (workspace too small), SX_ECUDA. */
 int sx_load_grid(sx_ctx *ctx, int64_t n, const double *pos, const int64_t *row_ptr,
                  const int32_t *col, const double *nH, const double *volume,
                  const uint8_t *flags, const double *y0, void *d_workspace,

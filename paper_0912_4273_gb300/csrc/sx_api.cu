@@ -149,8 +149,10 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
                       int64_t workspace_bytes, sx::DevGrid &g, sx::Layout &L, double **bins_dev) {
   if (n < 1 || !pos || !row_ptr || !nH || !volume || !flags || !d_workspace)
     return fail(c, SX_EINVAL, "n < 1 or a required pointer is NULL");
+  if (n >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "n must be < 2^31");
   const int64_t nnz = row_ptr[n];
-  if (row_ptr[0] != 0 || nnz < 0) return fail(c, SX_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+  if (!sx::row_ptr_nondecreasing(n, row_ptr))
+    return fail(c, SX_EINVAL, "row_ptr must start at 0 and must not decrease");
   if (nnz > 0 && !col) return fail(c, SX_EINVAL, "col is NULL");
   if (nnz >= (int64_t)1 << 31) return fail(c, SX_EINVAL, "nnz must be < 2^31");
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)

@@ -270,6 +270,17 @@ struct Layout {
 Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transport = 0);
 void bind_layout(DevGrid &g, void *base, const Layout &L);
 
+// Host check of a row_ptr in host memory (n + 1 entries): it starts at 0 and
+// never decreases, so every row lies inside [0, row_ptr[n]).  The setup
+// kernels index col and the edge tables by it before their own checks are
+// read back, so it runs before any of them.
+inline bool row_ptr_nondecreasing(int64_t n, const int64_t *row_ptr) {
+  if (row_ptr[0] != 0) return false;
+  for (int64_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return false;
+  return true;
+}
+
 cudaError_t launch_setup(DevGrid &g, cudaStream_t st);
 cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double sigma,
                                     double alpha_B, double kappa_cfg, const double *y0_dev,

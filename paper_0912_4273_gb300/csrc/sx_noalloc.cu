@@ -81,8 +81,8 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   if (!pos || !row_ptr || !flags || !bin_dirs || !kappa_out) return fail(SX_EINVAL, "NULL argument");
   if (n < 1 || n > kNv) return fail(SX_EINVAL, "n must be in 1..SX_NOALLOC_MAX_VERTICES");
   const int64_t nnz = row_ptr[n];
-  if (row_ptr[0] != 0 || nnz < 0 || nnz > kNe)
-    return fail(SX_EINVAL, "row_ptr[0] must be 0 and nnz <= SX_NOALLOC_MAX_EDGES");
+  if (!sx::row_ptr_nondecreasing(n, row_ptr) || nnz > kNe)
+    return fail(SX_EINVAL, "row_ptr must start at 0, must not decrease, and nnz <= SX_NOALLOC_MAX_EDGES");
   if (nnz > 0 && !col) return fail(SX_EINVAL, "col is NULL");
   if (nbins < 1 || nbins > SX_MAX_BINS) return fail(SX_EINVAL, "nbins must be in 1..SX_MAX_BINS");
   if (device < 0 || device >= 64) return fail(SX_EINVAL, "device ordinal out of range");

@@ -178,3 +178,23 @@ def test_remesh_arrays_own_the_library_memory(libpath):
     del tets
     gc.collect()
     assert owner() is None
+
+
+def test_noalloc_refuses_a_decreasing_row_ptr(libpath):
+    """A row_ptr that decreases is refused on the host, before any device
+    work: its rows would index col out of range."""
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    p = I.stromgren_problem(300, seed=2)
+    rp = p.row_ptr.copy()
+    rp[7] = rp[9] + 5  # row 6 overshoots, row 7 decreases
+    out = ctypes.c_double(0.0)
+    bins = np.ascontiguousarray(I.fibonacci_bins(21))
+    P = ctypes.POINTER
+    rc = S.lib().sx_kappa_noalloc(p.n, p.pos.ctypes.data_as(P(ctypes.c_double)),
+                                  rp.ctypes.data_as(P(ctypes.c_int64)),
+                                  p.col.ctypes.data_as(P(ctypes.c_int32)),
+                                  p.flags.ctypes.data_as(P(ctypes.c_uint8)), 21,
+                                  bins.ctypes.data_as(P(ctypes.c_double)), 0, None, ctypes.byref(out))
+    assert rc == S.SX_EINVAL and "decrease" in S.sx_kappa_noalloc_last_error()

@@ -196,6 +196,12 @@ def test_invalid_grids_are_rejected():
     with pytest.raises(S.SimplexError) as e:
         s.load(pos=prob.pos, row_ptr=rp, col=col, nH=prob.nH, volume=prob.volume, flags=prob.flags)
     assert e.value.code == S.SX_EINVAL and "symmetric" in str(e.value)
+    # a row_ptr that decreases: refused on the host before any device work
+    rp = prob.row_ptr.copy()
+    rp[7] = rp[9] + 5
+    with pytest.raises(S.SimplexError) as e:
+        s.load(pos=prob.pos, row_ptr=rp, col=prob.col, nH=prob.nH, volume=prob.volume, flags=prob.flags)
+    assert e.value.code == S.SX_EINVAL and "decrease" in str(e.value)
     # a non-sink star centre with more than SX_MAX_DEGREE neighbours
     n = 80
     pos = np.random.default_rng(0).normal(size=(n, 3))
