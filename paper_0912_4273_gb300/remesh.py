@@ -13,8 +13,10 @@ tetrahedron holds two of them, the cavities have disjoint interiors and each
 is filled on its own.
 
 The paper's QHull cannot delete points and rebuilds the whole grid after a
-removal; here only the cavities are re-triangulated (QHull on each vertex's
-neighbours) and the graph, the cell volumes and the tetrahedra are patched.
+removal; here only the cavities are re-triangulated and the graph, the cell
+volumes and the tetrahedra are patched: by the library's native code
+(Bowyer-Watson on each vertex's neighbours, threaded; the default), or with
+QHull per cavity and numpy patches (``method="qhull"``, the cross-check).
 Each cavity's new tetrahedra must fill its volume; a vertex on the convex
 hull (whose removal changes the hull) fails that check, and the grid is then
 rebuilt from scratch.
