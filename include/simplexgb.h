@@ -15,7 +15,9 @@
  *     a one-line reason.  A failed call leaves the context usable unless it
  *     returns SX_ECUDA (a CUDA error; the CUDA context may be lost).
  *   - Host pointers are read during the call (or, for sx_step, not at all);
- *     the library keeps no reference to them.  Device memory is the caller's:
+ *     the library keeps no reference to them, except the budgets array of
+ *     sx_step_budgets, which is written behind the queued steps and must stay
+ *     valid until the stream has reached them.  Device memory is the caller's:
  *     the per-grid state lives in one device workspace the caller allocates
  *     (size from sx_workspace_bytes) and keeps alive until sx_destroy.
  *   - Vertex ids are the caller's order 0..n-1.  The CSR is symmetric, each
@@ -221,7 +223,9 @@ int sx_get_info(sx_ctx *ctx, sx_info *info);
    SX_EINVAL with out->bad_vertex set: the caller rebuilds the grid instead.
    Errors: SX_EINVAL (bad arguments, a row_ptr that decreases, a col or tets
    entry outside [0, n), adjacent removed vertices: bad_vertex -1),
-   SX_ENOMEM.  No device memory or GPU is used. */
+   SX_ENOMEM.  No device memory or GPU is used.  The call runs on up to 16
+   host threads (fewer for small grids), joined before it returns; its
+   result does not depend on their number. */
 typedef struct {
     int64_t n, nnz, ntet;
     int64_t *row_ptr;     /* n + 1 */
