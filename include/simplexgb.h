@@ -19,7 +19,8 @@
  *     sx_step_budgets, which is written behind the queued steps and must stay
  *     valid until the stream has reached them.  Device memory is the caller's:
  *     the per-grid state lives in one device workspace the caller allocates
- *     (size from sx_workspace_bytes) and keeps alive until sx_destroy.
+ *     (size from sx_workspace_bytes) and keeps alive until sx_destroy and
+ *     until the work queued on the context's stream has run.
  *   - Vertex ids are the caller's order 0..n-1.  The CSR is symmetric, each
  *     row sorted strictly ascending, no self loops (a Delaunay graph).
  *   - Work is queued on the stream given in sx_config (NULL = the legacy
@@ -293,8 +294,12 @@ int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz);
    workspace (>= sx_workspace_bytes for the checkpoint's n and nnz, 256-byte
    aligned).  The context must have the checkpoint's bins (directions) and
    precision; the run parameters (seed, sigma, alpha_B, kappa, chemistry)
-   are the checkpoint's.  Errors: SX_EINVAL (not a checkpoint, other bins or
-   precision, truncated file), SX_ENOMEM (workspace too small), SX_ECUDA. */
+   are the checkpoint's.  The file's body is trusted once the header, layout
+   and size checks pass: it carries no checksum, so restore only files this
+   library wrote.  A call that fails after the checks leaves the context
+   without a grid (SX_ESTATE until the next load).  Errors: SX_EINVAL (not a
+   checkpoint, other bins or precision, truncated file), SX_ENOMEM
+   (workspace too small), SX_ECUDA. */
 int sx_restore(sx_ctx *ctx, const char *path, void *d_workspace, int64_t workspace_bytes);
 
 /* ---------------------------------------------------------------------------
@@ -386,7 +391,9 @@ int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row_ptr, const
                      void *stream, double *kappa_out);
 const char *sx_kappa_noalloc_last_error(void);
 
-/* Release the context (not the caller's workspace). */
+/* Release the context (not the caller's workspace).  It does not wait for
+   the context's stream: free the workspace after sx_sync, or in stream order
+   behind the queued work. */
 void sx_destroy(sx_ctx *ctx);
 
 /* Reason for the last failure of a call on ctx (or of sx_create if ctx is NULL). */
