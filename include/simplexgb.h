@@ -277,8 +277,8 @@ int sx_profile(sx_ctx *ctx, int enable);
  * checkpoint holds a loaded grid's tables and state -- positions, CSR,
  * per-edge and per-vertex tables, neutral fractions, the photons in flight
  * and their routing, budget, sources, step counters -- in one little-endian
- * file; restoring it and stepping on gives bit-identical results to stepping
- * on from the save.
+ * file that ends with a checksum of all its other bytes; restoring it and
+ * stepping on gives bit-identical results to stepping on from the save.
  * ------------------------------------------------------------------------- */
 
 /* Write the context's grid and state to path (overwritten).  Waits for the
@@ -287,18 +287,25 @@ int sx_profile(sx_ctx *ctx, int enable);
 int sx_save(sx_ctx *ctx, const char *path);
 
 /* Vertex and directed-edge counts of the grid in a checkpoint, to size the
-   workspace (sx_workspace_bytes).  Errors: SX_EINVAL (not a checkpoint). */
+   workspace (sx_workspace_bytes).  Reads the header only.  Errors: SX_EINVAL
+   (not a checkpoint). */
 int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz);
+
+/* Read a checkpoint through and check it against its checksum (host only, no
+   GPU).  SX_OK, or SX_EINVAL (not a checkpoint, no checksum, damaged or
+   truncated) with the reason from sx_last_error(NULL). */
+int sx_checkpoint_verify(const char *path);
 
 /* Replace the context's grid and state by the checkpoint's, in the caller's
    workspace (>= sx_workspace_bytes for the checkpoint's n and nnz, 256-byte
    aligned).  The context must have the checkpoint's bins (directions) and
    precision; the run parameters (seed, sigma, alpha_B, kappa, chemistry)
-   are the checkpoint's.  The file's body is trusted once the header, layout
-   and size checks pass: it carries no checksum, so restore only files this
-   library wrote.  A call that fails after the checks leaves the context
-   without a grid (SX_ESTATE until the next load).  Errors: SX_EINVAL (not a
-   checkpoint, other bins or precision, truncated file), SX_ENOMEM
+   are the checkpoint's.  The whole file is first checked against its
+   checksum (as sx_checkpoint_verify), so a damaged file is refused before
+   the context is touched; the file is then read a second time to restore
+   it.  A call that fails after those checks leaves the context without a
+   grid (SX_ESTATE until the next load).  Errors: SX_EINVAL (not a
+   checkpoint, damaged, other bins or precision, truncated file), SX_ENOMEM
    (workspace too small), SX_ECUDA. */
 int sx_restore(sx_ctx *ctx, const char *path, void *d_workspace, int64_t workspace_bytes);
 

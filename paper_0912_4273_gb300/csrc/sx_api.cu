@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "simplexgb.h"
+#include "sx_ckpt_io.h"
 #include "sx_internal.cuh"
 
 #include <nvtx3/nvToolsExt.h>
@@ -623,7 +624,7 @@ int sx_read_neutral_fraction(sx_ctx *c, double *y_out) {
 // host state, in one little-endian file.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr char kCkptMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr char kCkptMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '2'};
 
 struct CkptHeader {
   char magic[8];
@@ -640,15 +641,7 @@ struct CkptHeader {
   uint64_t bytes_a, bytes_p, bytes_m, bytes_b, bytes_col;
 };
 
-struct File {
-  FILE *f = nullptr;
-  explicit File(const char *path, const char *mode) : f(std::fopen(path, mode)) {}
-  ~File() {
-    if (f) std::fclose(f);
-  }
-  bool write(const void *p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
-  bool read(void *p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
-};
+using sx::File;  // checksummed writes (sx_ckpt_io.h)
 
 // The workspace regions a checkpoint holds, for a grid of this layout whose
 // next step is `step`: [offset, bytes] of the tables and y, the photons and
@@ -688,6 +681,16 @@ int sx_checkpoint_info(const char *path, int64_t *n, int64_t *nnz) {
   if (!f.f || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0) return SX_EINVAL;
   *n = h.n;
   *nnz = h.nnz;
+  return SX_OK;
+}
+
+int sx_checkpoint_verify(const char *path) {
+  if (!path) return SX_EINVAL;
+  std::string why;
+  if (!sx::verify_checkpoint_file(path, kCkptMagic, why)) {
+    g_create_err = std::string(path) + ": " + why;
+    return SX_EINVAL;
+  }
   return SX_OK;
 }
 
@@ -743,7 +746,7 @@ int sx_save(sx_ctx *c, const char *path) {
     SX_CUDA(c, cudaStreamSynchronize(c->stream));
     ok = f.write(buf.data(), r.bytes[k]);
   }
-  if (!ok) return fail(c, SX_EINVAL, std::string("write to ") + path + " failed");
+  if (!ok || !sx::write_trailer(f)) return fail(c, SX_EINVAL, std::string("write to ") + path + " failed");
   return SX_OK;
 }
 
@@ -754,6 +757,11 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   if (!path || !d_workspace) return fail(c, SX_EINVAL, "NULL argument");
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
     return fail(c, SX_EINVAL, "workspace not 256-byte aligned");
+  {  // the whole file against its checksum, before anything of it is used
+    std::string why;
+    if (!sx::verify_checkpoint_file(path, kCkptMagic, why))
+      return fail(c, SX_EINVAL, std::string(path) + ": " + why);
+  }
   File f(path, "rb");
   CkptHeader h;
   if (!f.f || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)

@@ -97,6 +97,7 @@ _SIGS = [
     ("sx_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("sx_checkpoint_info", C.c_int, [C.c_char_p, _P(C.c_int64), _P(C.c_int64)]),
     ("sx_restore", C.c_int, [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64]),
+    ("sx_checkpoint_verify", C.c_int, [C.c_char_p]),
     ("sx_set_variant", C.c_int, [C.c_void_p, C.c_int32]),
     ("sx_get_variant", C.c_int, [C.c_void_p, _P(C.c_int32)]),
     ("sx_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_size_t,
@@ -312,6 +313,14 @@ def sx_checkpoint_info(path: str):
     if rc != SX_OK:
         raise SimplexError(rc, f"{path} is not a checkpoint")
     return n.value, nnz.value
+
+
+def sx_checkpoint_verify(path: str):
+    """Check a checkpoint file against its checksum (no GPU); raises
+    SimplexError with the reason if it is not an intact checkpoint."""
+    rc = lib().sx_checkpoint_verify(os.fsencode(path))
+    if rc != SX_OK:
+        raise SimplexError(rc, sx_last_error(None))
 
 
 def sx_restore(ctx, path: str, ws_ptr: int, ws_bytes: int):

@@ -94,6 +94,18 @@ def test_restore_refuses_other_bins_and_non_checkpoints(tmp_path):
     with pytest.raises(S.SimplexError) as e:
         s.restore(str(bad))
     assert e.value.code == S.SX_EINVAL
+    # the file sx_save wrote verifies; a copy with one byte changed in its
+    # body is refused before the context is touched, which keeps its grid
+    S.sx_checkpoint_verify(path)
+    data = bytearray(open(path, "rb").read())
+    data[len(data) // 2] ^= 0x10
+    damaged = tmp_path / "damaged.sxck"
+    damaged.write_bytes(bytes(data))
+    y = s.y
+    with pytest.raises(S.SimplexError) as e:
+        s.restore(str(damaged))
+    assert e.value.code == S.SX_EINVAL and "damaged" in str(e.value)
+    assert np.array_equal(s.y, y)
     s.close()
     other.close()
 
