@@ -42,7 +42,10 @@ def build(force: bool = False) -> str:
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
            "-o", tmp] + srcs + ["-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP for the threaded sweep (OracleSim(threads=...)); without it the
+    # same code runs on one thread
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 
@@ -75,6 +78,7 @@ def lib():
             L.ox_add_source.argtypes = [C.c_void_p, i32, d]
             L.ox_add_source.restype = C.c_int
             L.ox_step.argtypes = [C.c_void_p, d, C.c_int]
+            L.ox_set_threads.argtypes = [C.c_void_p, C.c_int]
             for name in ("ox_get_y", "ox_set_y", "ox_get_I", "ox_set_I", "ox_get_budget"):
                 getattr(L, name).argtypes = [C.c_void_p, P(d)]
             L.ox_get_kappa.argtypes = [C.c_void_p]
@@ -206,7 +210,9 @@ class OracleSim:
     """FP64 SimpleX2 simulation of one grid on the CPU: direction-conserving,
     ballistic or combined transport (``Params.transport``)."""
 
-    def __init__(self, problem, params: Params, bins: np.ndarray, y0=None):
+    def __init__(self, problem, params: Params, bins: np.ndarray, y0=None, threads: int = 1):
+        """threads > 1: the direction-conserving sweep runs on that many
+        threads, with the serial sweep's results bit for bit."""
         L = lib()
         self.p = params
         self.n = problem.n
@@ -235,6 +241,7 @@ class OracleSim:
                              _p(k["bins"], C.c_double))
         if not self.h:
             raise ValueError("diffuse radiation needs alpha_A >= alpha_B")
+        L.ox_set_threads(self.h, int(threads))
         for v, r in zip(problem.src_vertex, problem.src_rate):
             if L.ox_add_source(self.h, int(v), float(r)) != 0:
                 raise ValueError("bad source vertex")

@@ -465,6 +465,7 @@ typedef struct {
     double ground;          /* (alpha_A - alpha_B) / alpha_A */
     double *D;              /* n, or NULL: recombination photons of the last step, emitted next */
     double diffuse_emitted; /* photons emitted by recombining cells so far */
+    int threads;            /* > 1: the direction-conserving sweep on that many threads */
 } ox_sim;
 
 typedef struct {
@@ -561,6 +562,96 @@ int ox_add_source(ox_sim *s, int32_t v, double rate) {
     return 0;
 }
 
+/* The interaction and transport of one direction-conserving step on
+   s->threads threads, with the results of the serial loop of ox_one_step bit
+   for bit (the tests hold it to that).  Only what is independent per vertex
+   runs in parallel, and every sum keeps the serial order:
+     1. per vertex i (parallel): N_in, the chemistry, and for every bin b the
+        transmitted O_i[b] and the straight set S(i, b) it goes to;
+     2. the budget (serial, i then b ascending, as the serial loop adds it);
+     3. the transport, as its definition reads: I'_j[b] = sum over the
+        vertices i with j in S(i, b), in ascending i, of O_i[b] / |S(i, b)|.
+        Each j (parallel) walks its own neighbours, which are the only
+        candidates and come in ascending order, so every bin adds its terms in
+        the order of the serial push. */
+static void sweep_threaded(ox_sim *s, double dt, const int32_t *qb) {
+    const int nb = s->nbins;
+    const int64_t n = s->n;
+    const size_t nI = (size_t)n * (size_t)nb;
+    double *nin = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *O = (double *)malloc(sizeof(double) * (nI ? nI : 1));       /* O_i[b] */
+    int64_t *sset = (int64_t *)malloc(sizeof(int64_t) * (nI ? nI : 1)); /* edge of S(i,b), -1: escapes */
+    int *nsub = (int *)calloc((size_t)n + 1, sizeof(int));
+    int *capped = (int *)calloc((size_t)n + 1, sizeof(int));
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->threads)
+    for (int64_t i = 0; i < n; ++i) {
+        const double *Ii = s->I + (size_t)i * nb;
+        double N_in = 0.0;
+        for (int b = 0; b < nb; ++b) N_in += Ii[b];
+        nin[i] = N_in;
+        if (s->flags[i] & 1) continue;
+        double rec = 0.0;
+        double f = ox_chem_rec(&s->y[i], N_in, dt, s->A[i], s->tau_max[i], s->R0[i], s->fc, s->tol,
+                               s->max_sub, &nsub[i], &capped[i], &rec);
+        if (s->D) s->D[i] = s->ground * (s->A[i] * rec);
+        int64_t r0 = s->row_ptr[i], r1 = s->row_ptr[i + 1];
+        for (int b = 0; b < nb; ++b) {
+            O[(size_t)i * nb + b] = Ii[b] * f;
+            int64_t e = -1;
+            if (r1 > r0) {
+                int k = associate(qb + 3 * b, s->qedge, r0, r1);
+                if (s->straight[4 * (r0 + k) + 3] > 0) e = r0 + k;
+            }
+            sset[(size_t)i * nb + b] = e;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        s->total_sub += nsub[i];
+        s->total_capped += capped[i];
+        if (s->flags[i] & 1) {
+            s->budget[2] += nin[i];
+            continue;
+        }
+        double out_sum = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const double Ob = O[(size_t)i * nb + b];
+            out_sum += Ob;
+            if (sset[(size_t)i * nb + b] < 0) s->budget[2] += Ob;
+        }
+        s->budget[1] += nin[i] - out_sum;
+    }
+#pragma omp parallel for schedule(dynamic, 64) num_threads(s->threads)
+    for (int64_t j = 0; j < n; ++j) {
+        double *Ij = s->Inew + (size_t)j * nb;
+        for (int b = 0; b < nb; ++b) Ij[b] = 0.0;
+        for (int64_t ej = s->row_ptr[j]; ej < s->row_ptr[j + 1]; ++ej) {
+            const int64_t i = s->col[ej];
+            if (s->flags[i] & 1) continue;  /* a sink sends nothing */
+            const int64_t r0 = s->row_ptr[i];
+            for (int b = 0; b < nb; ++b) {
+                const int64_t e = sset[(size_t)i * nb + b];
+                if (e < 0) continue;
+                const uint8_t *st = s->straight + 4 * e;
+                const int cnt = st[3];
+                for (int m = 0; m < cnt; ++m) {
+                    if (s->col[r0 + st[m]] == j) {
+                        Ij[b] += O[(size_t)i * nb + b] / cnt;
+                        break;
+                    }
+                }
+            }
+        }
+    }
+    free(nin); free(O); free(sset); free(nsub); free(capped);
+    double *t = s->I;
+    s->I = s->Inew;
+    s->Inew = t;
+    double inflight = 0.0;
+    for (size_t e = 0; e < nI; ++e) inflight += s->I[e];
+    s->budget[3] = inflight;
+    s->step++;
+}
+
 /* One radiative-transfer step of length dt (Sect. 4.6). */
 static void ox_one_step(ox_sim *s, double dt) {
     const int nb = s->nbins;
@@ -580,11 +671,26 @@ static void ox_one_step(ox_sim *s, double dt) {
         double *tmp = (double *)malloc(sizeof(double) * (size_t)nb);
         ox_rotated_bins(Rp, nb, s->bins, qp);
         ox_bin_map(nb, qp, qb, map);
-        for (int64_t i = 0; i < n; ++i) {
-            double *Ii = s->I + (size_t)i * nb;
-            for (int b = 0; b < nb; ++b) tmp[b] = 0.0;
-            for (int b = 0; b < nb; ++b) tmp[map[b]] += Ii[b];
-            for (int b = 0; b < nb; ++b) Ii[b] = tmp[b];
+        if (s->threads > 1) {  /* the same loop, vertices split over threads */
+#pragma omp parallel num_threads(s->threads)
+            {
+                double *t = (double *)malloc(sizeof(double) * (size_t)nb);
+#pragma omp for schedule(static)
+                for (int64_t i = 0; i < n; ++i) {
+                    double *Ii = s->I + (size_t)i * nb;
+                    for (int b = 0; b < nb; ++b) t[b] = 0.0;
+                    for (int b = 0; b < nb; ++b) t[map[b]] += Ii[b];
+                    for (int b = 0; b < nb; ++b) Ii[b] = t[b];
+                }
+                free(t);
+            }
+        } else {
+            for (int64_t i = 0; i < n; ++i) {
+                double *Ii = s->I + (size_t)i * nb;
+                for (int b = 0; b < nb; ++b) tmp[b] = 0.0;
+                for (int b = 0; b < nb; ++b) tmp[map[b]] += Ii[b];
+                for (int b = 0; b < nb; ++b) Ii[b] = tmp[b];
+            }
         }
         free(qp); free(map); free(tmp);
     }
@@ -612,6 +718,11 @@ static void ox_one_step(ox_sim *s, double dt) {
         }
     }
 
+    if (s->threads > 1) {
+        sweep_threaded(s, dt, qb);
+        free(qb);
+        return;
+    }
     memset(s->Inew, 0, sizeof(double) * (size_t)n * nb);
     for (int64_t i = 0; i < n; ++i) {
         double *Ii = s->I + (size_t)i * nb;
@@ -837,6 +948,9 @@ static void ox_one_step_ballistic(ox_sim *s, double dt) {
     free(map);
     free(tmp);
 }
+
+/* Threads of the direction-conserving sweep (1: the serial loop). */
+void ox_set_threads(ox_sim *s, int threads) { s->threads = threads > 1 ? threads : 1; }
 
 void ox_step(ox_sim *s, double dt, int nsteps) {
     for (int k = 0; k < nsteps; ++k) {
