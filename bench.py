@@ -3,10 +3,13 @@
 
 Metric: DCT vertex-direction updates per second (interior vertices x bins x
 steps / time) on the Test-1 Stromgren workload at 2^20 interior vertices and
-84 bins, FP32 transport (the configuration the headline metric is quoted on;
-the chemistry evaluates its rates in FP32 and keeps y in FP64).  One step is
-one pass of the whole hot path: rotation and bin remap, gather, sources,
-chemistry, association and routing, budget.
+84 bins: photons and transport in FP32 (compensated per-bin gathers), the
+neutral fraction and the recombination subcycling in FP64, the budget's
+global reduction in FP64.  One step is one pass of the whole hot path:
+rotation and bin remap, gather, sources, chemistry, association and routing,
+budget.  The grid is first advanced, untimed, to a fixed mid-run state
+(--state-step, default step 300 of the 1000-step run), so that the timed
+steps cost what the run's steps cost on average whatever --steps is.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,14 +42,14 @@ UNIT = "updates/s"
 
 WORKLOADS = {
     # 2^20 interior vertices of the Test-1 grid (Sect. 5.1), 84 bins, 1000 steps over 500 Myr
-    "c1": dict(n=1 << 20, nbins=84, precision="fp32", dt_myr=0.5, seed=0,
-               name="Test-1 Stromgren grid, 2^20 interior Poisson-Delaunay vertices + sink shell, "
-                    "84 direction bins, FP32 transport (FP32 chemistry rates, FP64 neutral fraction), "
-                    "dt = 0.5 Myr"),
+    "c1": dict(n=1 << 20, nbins=84, precision="fp32", dt_myr=0.5, seed=0, run_steps=1000,
+               name="Test-1 Stromgren problem: 2^20 interior Poisson-Delaunay vertices in the "
+                    "13.2 kpc mirror box of the 6.6 kpc corner-source cube (source at the centre) "
+                    "+ sink shell, 84 direction bins, 1000 steps of 0.5 Myr"),
     # the small FP64 case
-    "c0": dict(n=8192, nbins=42, precision="fp64", dt_myr=2.5, seed=0,
-               name="Test-1 Stromgren grid, 8192 interior vertices + sink shell, 42 bins, FP64, "
-                    "dt = 2.5 Myr"),
+    "c0": dict(n=8192, nbins=42, precision="fp64", dt_myr=2.5, seed=0, run_steps=200,
+               name="Test-1 Stromgren problem: 8192 interior vertices in the 13.2 kpc mirror box "
+                    "+ sink shell, 42 bins, FP64, 200 steps of 2.5 Myr"),
 }
 
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
@@ -202,6 +205,14 @@ def make_problem(wl: dict, seed: int):
     return I.cached(I.stromgren_problem, wl["n"], seed=seed)
 
 
+def chemistry_label(fp64: bool, chem_fp32: bool) -> str:
+    if fp64:
+        return "FP64 throughout"
+    if chem_fp32:
+        return "FP32 transport, FP32 subcycle rates with FP64 neutral fraction (the faster, less exact mode)"
+    return "FP32 transport (compensated per-bin gathers), FP64 neutral fraction and recombination subcycling"
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
 
@@ -218,10 +229,15 @@ def run_ours(args, wl, rank, world, local_rank):
     fp64 = wl["precision"] == "fp64"
     prec = S.SX_FP64 if fp64 else S.SX_FP32_TRANSPORT
     stream = torch.cuda.Stream(device)
-    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream).load(prob)
+    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream,
+                      chem_fp32=args.chem_fp32).load(prob)
     n_int = int(prob.interior.sum())
-    solver.step(dt, args.warmup)
+    # untimed: the grid is advanced to the fixed state the timed steps start
+    # from, then the warm-up steps
+    state_step = min(args.state_step, max(wl["run_steps"] - args.steps - args.warmup, 0))
+    solver.step(dt, state_step + args.warmup)
     solver.sync()
+    t_first = state_step + args.warmup
 
     clocks = ClockSampler(local_rank)
     clocks.start()
@@ -247,12 +263,14 @@ def run_ours(args, wl, rank, world, local_rank):
     value = aggregate(n_int * wl["nbins"] * args.steps, world, max_ms)
     kernel_ms = info["step_kernel_ms"] / max(info["step_kernel_launches"], 1)
     mean_deg = prob.nnz / prob.n
-    bytes_launch = algorithmic_bytes_per_vertex(wl["nbins"], fp64, mean_deg) * prob.n
+    per_vertex = algorithmic_bytes_per_vertex(wl["nbins"], fp64, mean_deg)
+    bytes_launch = per_vertex * prob.n
     achieved = bytes_launch / (kernel_ms * 1e-3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic = None
-    if NCU_TRAFFIC["sx_step.cu_sha256"] == kernel_source_sha() and NCU_TRAFFIC["workload"] == args.config:
+    if (NCU_TRAFFIC["sx_step.cu_sha256"] == kernel_source_sha() and NCU_TRAFFIC["workload"] == args.config
+            and NCU_TRAFFIC.get("chem_fp32", False) == bool(args.chem_fp32)):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     budget = solver.budget
     solver.close()
@@ -262,7 +280,7 @@ def run_ours(args, wl, rank, world, local_rank):
         barrier(world, device)
         e2e = run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream)
         max_s = reduce_max(e2e["seconds"], world, device)
-        e2e.update(value=aggregate(n_int * wl["nbins"] * args.steps, world, max_s * 1e3),
+        e2e.update(value=aggregate(n_int * wl["nbins"] * e2e["steps"], world, max_s * 1e3),
                    seconds=max_s, h2d_bytes_per_step=e2e["h2d_bytes_per_step"] * world,
                    d2h_bytes_per_step=e2e["d2h_bytes_per_step"] * world)
     cpu = None
@@ -274,9 +292,13 @@ def run_ours(args, wl, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32",
         "data": "synthetic (seeded Poisson-Delaunay Test-1 grid)",
-        "config": {"workload": wl["name"], "n_interior": n_int, "n_vertices": prob.n,
-                   "nnz": prob.nnz, "nbins": wl["nbins"],
-                   "chemistry": "f64" if fp64 else "f32 rates, f64 y", "transport": "f64" if fp64 else "f32",
+        "config": {"workload": wl["name"] + f"; timed steps {t_first}..{t_first + args.steps - 1} "
+                                            f"after an untimed advance to step {state_step}",
+                   "state_step": state_step, "timed_steps": [t_first, t_first + args.steps],
+                   "n_interior": n_int, "n_vertices": prob.n,
+                   "nnz": prob.nnz, "nbins": wl["nbins"], "precision": chemistry_label(fp64, args.chem_fp32),
+                   "chemistry": "f64" if (fp64 or not args.chem_fp32) else "f32 rates, f64 y",
+                   "transport": "f64" if fp64 else "f32, compensated gathers",
                    "l2": (f"no flush: per-grid state {info['workspace_bytes'] / 1e9:.2f} GB > 129 MB L2"
                           if info["workspace_bytes"] > 129e6 else
                           f"no flush: per-grid state {info['workspace_bytes'] / 1e6:.0f} MB fits in the "
@@ -285,8 +307,9 @@ def run_ours(args, wl, rank, world, local_rank):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_step", "kernel_ms": kernel_ms,
+                     "algorithmic_bytes_per_vertex": per_vertex,
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback"},
         "clocks": clk,
         # the step kernels and one rotation launch per block of steps
         "gpu_launches": args.steps + -(-args.steps // S.SX_STEP_BLOCK),
@@ -304,10 +327,11 @@ def run_ours(args, wl, rank, world, local_rank):
 
 
 def run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream):
-    """The whole solve through the C ABI from pinned host buffers: load the grid
-    (host->device), every step read the photon budget back into pinned memory
-    (sx_step_budgets: queued behind its step, nothing waits), at the end read
-    the neutral fraction."""
+    """The whole job through the C ABI from pinned host buffers: load the grid
+    (host->device), run the workload's full run (1000 steps for C1), every
+    step reading the photon budget back into pinned memory (sx_step_budgets:
+    queued behind its step, nothing waits), and read the neutral fraction at
+    the end."""
     import torch
 
     from paper_0912_4273_gb300 import simplex as S
@@ -319,10 +343,11 @@ def run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream):
     host = dict(pos=pinned(prob.pos), row_ptr=pinned(prob.row_ptr), col=pinned(prob.col),
                 nH=pinned(prob.nH), volume=pinned(prob.volume), flags=pinned(prob.flags))
     y_out = pinned(np.zeros(prob.n))
-    K = args.steps
+    K = wl["run_steps"]
     budgets = pinned(np.zeros((K, 4)))
     h2d = sum(a.nbytes for a in host.values())
-    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream)
+    solver = S.Solver(bins, precision=prec, seed=seed, device=local_rank, stream=stream,
+                      chem_fp32=args.chem_fp32)
     nbytes = solver.workspace_bytes(prob.n, prob.nnz)
     ws = torch.empty(nbytes, dtype=torch.uint8, device=torch.device("cuda", local_rank))
     torch.cuda.synchronize()
@@ -336,55 +361,82 @@ def run_e2e(args, wl, prob, bins, dt, prec, seed, local_rank, stream):
     assert budgets[-1, 0] > 0.0 and np.all(np.diff(budgets[:, 0]) > 0.0)  # every row arrived
     solver.close()
     n_int = int(prob.interior.sum())
-    return {"value": n_int * wl["nbins"] * K / (t1 - t0), "unit": UNIT,
+    return {"value": n_int * wl["nbins"] * K / (t1 - t0), "unit": UNIT, "steps": K,
+            "what": f"the whole {K}-step run from pinned host inputs: grid load, a budget read "
+                    "per step, the neutral fraction at the end",
             "h2d_bytes_per_step": (h2d + 12 * len(prob.src_rate)) / K,
             "d2h_bytes_per_step": (y_out.nbytes + budgets.nbytes) / K,
             "seconds": t1 - t0}
 
 
-def run_cpu_baseline(wl, prob, bins, dt, seed, budget_s: float = 12.0, max_steps: int = 4):
+def time_oracle(prob, bins, dt, seed, threads, budget_s, max_steps):
+    """Oracle steps from the start of the run, timed one by one until
+    budget_s seconds or max_steps steps; returns (steps, seconds, setup
+    seconds).  The oracle sweeps every bin of every vertex, so a step costs
+    the same at any state of the run."""
     import oracle as O
 
-    sim = O.OracleSim(prob, O.Params(nbins=wl["nbins"], seed=seed), bins)
-    n_int = int(prob.interior.sum())
-    done = 0
     t0 = time.perf_counter()
-    while done < max_steps and (time.perf_counter() - t0) < budget_s:
+    sim = O.OracleSim(prob, O.Params(nbins=len(bins), seed=seed), bins, threads=threads)
+    setup = time.perf_counter() - t0
+    done, el = 0, 0.0
+    while done < max_steps and el < budget_s:
+        t0 = time.perf_counter()
         sim.step(dt, 1)
+        el += time.perf_counter() - t0
         done += 1
-    el = time.perf_counter() - t0
-    return {"value": n_int * wl["nbins"] * done / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} oracle steps (single thread, FP64) of the same grid"}
+    return done, el, setup
+
+
+def run_cpu_baseline(wl, prob, bins, dt, seed):
+    """The oracle (FP64, as it stands) on the same grid, on every host core
+    (its threaded sweep, bit-identical to the serial one) and on one thread."""
+    cores = os.cpu_count() or 1
+    n_int = int(prob.interior.sum())
+    steps_all, s_all, _ = time_oracle(prob, bins, dt, seed, cores, 12.0, 6)
+    steps_one, s_one, _ = time_oracle(prob, bins, dt, seed, 1, 12.0, 3)
+    v_all = n_int * wl["nbins"] * steps_all / s_all
+    v_one = n_int * wl["nbins"] * steps_one / s_one
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps_all} FP64 oracle steps of the same grid from its start on {cores} "
+                      f"threads (the oracle's cost per step does not depend on the state)",
+            "single_thread": {"value": v_one, "cores": 1,
+                              "sample": f"{steps_one} oracle steps, one thread"}}
 
 
 def run_reference(args, wl, rank, world):
-    """The oracle as the reference arm: each step is one FP64 oracle step of a
-    2^14-vertex grid built with the same recipe (a bounded sample)."""
+    """The oracle as the reference arm, on the workload's own grid: --warmup
+    untimed steps, then --steps timed FP64 oracle steps on every host core
+    (the threaded sweep).  Its cost per step does not depend on the state of
+    the run, so the steps are taken from its start."""
     if rank != 0:
         return
     import oracle as O
     from paper_0912_4273_gb300 import inputs as I
 
-    n_sample = 1 << 14
-    prob = I.stromgren_problem(n_sample, seed=wl["seed"])
+    cores = os.cpu_count() or 1
+    prob = make_problem(wl, wl["seed"])
     bins = I.fibonacci_bins(wl["nbins"])
     dt = wl["dt_myr"] * I.MYR_S
-    sim = O.OracleSim(prob, O.Params(nbins=wl["nbins"], seed=wl["seed"]), bins)
+    sim = O.OracleSim(prob, O.Params(nbins=wl["nbins"], seed=wl["seed"]), bins, threads=cores)
     sim.step(dt, args.warmup)
     t0 = time.perf_counter()
     sim.step(dt, args.steps)
     el = time.perf_counter() - t0
     n_int = int(prob.interior.sum())
     value = n_int * wl["nbins"] * args.steps / el
-    sample = (f"each step one FP64 oracle step of a {n_sample}-vertex grid of the same recipe "
-              f"({wl['nbins']} bins), single thread")
+    sample = (f"steps {args.warmup}..{args.warmup + args.steps - 1} of the FP64 oracle on the "
+              f"workload's own grid ({prob.n} vertices, {wl['nbins']} bins), {cores} threads")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Poisson-Delaunay Test-1 grid)",
-        "config": {"workload": wl["name"], "nbins": wl["nbins"], "sample_vertices": n_sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": wl["name"], "n_interior": n_int, "n_vertices": prob.n,
+                   "nbins": wl["nbins"], "same_config": True,
+                   "note": "the oracle sweeps every bin of every vertex: its cost per step does "
+                           "not depend on the state, so it is timed from the start of the run"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -712,6 +764,10 @@ def main(argv=None):
     ap.add_argument("--config", choices=sorted(WORKLOADS), default="c1")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--state-step", type=int, default=300,
+                    help="untimed steps before the warm-up (the state the timed steps start from)")
+    ap.add_argument("--chem-fp32", action="store_true",
+                    help="FP32 subcycle rates (the faster, less exact mode) instead of FP64 subcycles")
     ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport", "shadow"],
                     default="step")
     ap.add_argument("--shadow-res", type=int, default=128)

@@ -50,10 +50,16 @@ enum {
 
 enum {
     SX_FP64 = 0,           /* photons, transport and chemistry in FP64 */
-    SX_FP32_TRANSPORT = 1  /* photons and transport in FP32 (sums in a fixed
-                              order); chemistry rates in FP32 with the neutral
-                              fraction accumulated in FP64; the photon budget
-                              in float-float and FP64 */
+    SX_FP32_TRANSPORT = 1  /* photons and transport in FP32: every bin's
+                              packets are summed in a fixed order with a
+                              compensated (Kahan-Babuska) addition; N_in and
+                              the per-tile budget terms in float-float.  The
+                              chemistry -- the neutral fraction y and the
+                              recombination subcycling (Sect. 4.5) -- runs in
+                              FP64 unless sx_config.chem_fp32 = 1, which
+                              evaluates the subcycle rates, lengths and
+                              exponentials in FP32 and keeps only y in FP64.
+                              The budget's global reduction is FP64. */
 };
 
 /* Transport of the photons that a vertex passes on (Sect. 2.2):
@@ -86,6 +92,7 @@ enum {
 #define SX_MAX_DEGREE 64      /* per non-sink vertex */
 #define SX_MAX_SOURCES 4096
 #define SX_FLAG_SINK 1u
+#define SX_FLAG_GHOST 2u      /* a copy of a vertex another shard steps (see the halo exchange) */
 
 typedef struct sx_ctx sx_ctx;
 
@@ -104,6 +111,21 @@ typedef struct {
     int32_t transport;      /* SX_TRANSPORT_DCT (default), _BALLISTIC or _COMBINED */
     double tau_switch;      /* combined: ballistic where y tau_max >= tau_switch (default 1,
                                Sect. 5.1.3) */
+    int32_t chem_fp32;      /* SX_FP32_TRANSPORT only: 0 (default) = FP64 subcycles;
+                               1 = subcycle rates in FP32, y in FP64 (faster, less exact);
+                               ignored in SX_FP64.  Other values: SX_EINVAL */
+    double alpha_A;         /* diffuse recombination radiation (Sect. 2.2.1, 4.5; the paper's
+                               tests leave it out): 0 (default) = the on-the-spot
+                               approximation, recombination at alpha_B; > 0 = the case-A
+                               coefficient (cm^3/s, >= alpha_B; 4.18e-13 at 1e4 K):
+                               recombination runs at alpha_A, and the fraction
+                               (alpha_A - alpha_B) / alpha_A of a cell's recombinations in a
+                               step (summed over its subcycles) become ionising photons that
+                               the cell emits in the next step as a source does -- an equal
+                               share in every bin of its incoming photons, after the sources'
+                               (a ballistic vertex sends them with its own photons to all its
+                               neighbours).  They count as emitted when they enter.  The
+                               dynamic grid update refuses alpha_A > 0. */
 } sx_config;
 
 typedef struct {
@@ -128,9 +150,9 @@ typedef struct {
                                 range and skipped; always 0 in release builds, which do not check */
 } sx_info;
 
-/* Fill cfg with the Test-1 defaults of Sect. 5.1 (42 bins, FP32 transport,
-   sigma 6.3e-18, alpha_B 2.59e-13, chem_frac 0.5, chem_tol 1e-5,
-   chem_max_sub 1000, seed 0, device 0, NULL stream). */
+/* Fill cfg with the Test-1 defaults of Sect. 5.1 (42 bins, FP32 transport
+   with FP64 chemistry, sigma 6.3e-18, alpha_B 2.59e-13, chem_frac 0.5,
+   chem_tol 1e-5, chem_max_sub 1000, seed 0, device 0, NULL stream). */
 void sx_config_default(sx_config *cfg);
 
 /* Create a context.  bin_dirs: nbins x 3 unit vectors (row-major, FP64) --
@@ -154,7 +176,8 @@ int sx_workspace_bytes(const sx_ctx *ctx, int64_t n, int64_t nnz, int64_t *bytes
      pos     n x 3 FP64 positions (cm)
      row_ptr n + 1 int64 CSR offsets; col nnz int32 neighbour ids
      nH      n FP64 hydrogen densities (cm^-3); volume n FP64 cell volumes (cm^3)
-     flags   n bytes, bit 0 = sink (absorbs everything into "escaped")
+     flags   n bytes, bit 0 = sink (absorbs everything into "escaped"), bit 1 = ghost
+             (a shard's copy of another shard's vertex: SX_FLAG_GHOST below)
      y0      n FP64 initial neutral fractions, or NULL for 1 (neutral)
      d_workspace, workspace_bytes: caller-owned device memory, >= sx_workspace_bytes,
              256-byte aligned.
@@ -389,14 +412,71 @@ const char *sx_batch_last_error(const sx_batch *batch);
    this library holds until exit, so n <= SX_NOALLOC_MAX_VERTICES and nnz <=
    SX_NOALLOC_MAX_EDGES (SX_EINVAL beyond).  The first call on a device looks
    up that array's address there; make it before any stream capture.  Calls
-   share the array: the call waits for its stream before returning, and calls
-   whose GPU work overlaps would race (the calls of one process are serialised
-   on the host).  Errors: SX_EINVAL, SX_ECUDA; reason from
+   share the array: the call waits for its stream before returning (also
+   when it fails after queuing work), and calls whose GPU work overlaps would
+   race (the calls of one process are serialised on the host).  `device` is
+   current during the call; the caller's current device is current again when
+   it returns.  Errors: SX_EINVAL, SX_ECUDA; reason from
    sx_kappa_noalloc_last_error(). */
 int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row_ptr, const int32_t *col,
                      const uint8_t *flags, int32_t nbins, const double *bin_dirs, int32_t device,
                      void *stream, double *kappa_out);
 const char *sx_kappa_noalloc_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * One grid split into shards (the paper's domain decomposition for
+ * distributed memory, Sect. 3.1-3.2: every vertex depends only on its
+ * neighbours' photons of the previous step, so the subdomains exchange their
+ * boundary once per step).  A shard is an ordinary grid whose vertices are a
+ * range of the whole grid's vertices plus, flagged SX_FLAG_GHOST, their
+ * neighbours owned by other shards; its CSR holds every local neighbour of
+ * every local vertex (for a ghost: those of its neighbours that are local).
+ * A ghost is not stepped, sends nothing and counts in no budget term, and is
+ * not part of kappa; sources go on the owning shard only.  After every step
+ * each shard packs, for each other shard, what that shard's gather will read
+ * from this shard's vertices -- the routing masks at the receivers' in-edge
+ * indices and the senders' transmitted photons -- and the other shard
+ * unpacks them at its own indices (the ghosts' out-edges' masks and the
+ * ghosts' photon rows) before its next step.  With the local vertices in
+ * the whole grid's order (ghosts below, owned, ghosts above) every vertex
+ * gathers in the same order as in the whole grid, so the neutral fractions
+ * equal the whole grid's bit for bit; the budget, summed over the shards, to
+ * its rounding.  Direction-conserving transport only (SX_EINVAL otherwise);
+ * the dynamic grid update refuses a shard.
+ * ------------------------------------------------------------------------- */
+
+/* kappa's two sums (Sect. 2.2.3) over the loaded grid's interior, non-ghost
+   vertices: progress along the unrotated bins and path length of their
+   straight moves (each a mean over the straight set), summed per vertex in
+   FP32 and across vertices in FP64.  kappa of the whole grid is the sum of
+   the shards' num over the sum of their den; pass it as sx_config.kappa.
+   Waits for the stream.  Errors: SX_ESTATE (no grid, or after sx_restore or
+   sx_grid_update_mark, which reuse the load-time tables), SX_ECUDA. */
+int sx_kappa_sums(sx_ctx *ctx, double *num, double *den);
+
+/* Bytes of one halo buffer of n_edges masks and n_rows photon rows: the
+   masks (the grid's mask words per edge: 1, 2 or 4 x 32 bits), then, at the
+   next 16-byte boundary, the rows (nbins rounded up to 4 values of the
+   photon type: FP64, or FP32 in SX_FP32_TRANSPORT). */
+int sx_halo_bytes(const sx_ctx *ctx, int64_t n_edges, int64_t n_rows, int64_t *bytes);
+
+/* Queue, on the context's stream, the gather of the buffers the last step
+   wrote into d_buf (device memory, 16-byte aligned, >= sx_halo_bytes):
+   mask k = the mask at in-edge index d_edge_idx[k] (0 <= k < n_edges), row
+   k = the transmitted photons of vertex d_row_idx[k] (local ids; both index
+   arrays in device memory, read when the work runs).  An index out of range
+   is skipped and counted in sx_info.index_errors.  Errors: SX_EINVAL (counts,
+   NULL pointers, alignment, not direction conserving), SX_ESTATE (no grid or
+   no step taken), SX_ECUDA. */
+int sx_halo_pack(sx_ctx *ctx, int64_t n_edges, const int32_t *d_edge_idx, int64_t n_rows,
+                 const int32_t *d_row_idx, void *d_buf);
+
+/* The inverse: queue the scatter of d_buf into the buffers the last step
+   wrote, so that the next step's gather reads them (mask k to in-edge index
+   d_edge_idx[k], row k to vertex d_row_idx[k]).  Same arguments and errors
+   as sx_halo_pack; d_buf must stay valid until the work has run. */
+int sx_halo_unpack(sx_ctx *ctx, int64_t n_edges, const int32_t *d_edge_idx, int64_t n_rows,
+                   const int32_t *d_row_idx, const void *d_buf);
 
 /* Release the context (not the caller's workspace).  It does not wait for
    the context's stream: free the workspace after sx_sync, or in stream order

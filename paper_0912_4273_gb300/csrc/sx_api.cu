@@ -44,6 +44,8 @@ struct sx_ctx {
   std::unordered_map<int32_t, int> src_slot;
   int32_t max_degree = 0;
   bool punit_set = false;  // FP32 photons are stored in units of g.punit photons
+  bool has_ghosts = false;  // the grid is a shard of a larger one (vertices flagged SX_FLAG_GHOST)
+  bool staging_ok = false;  // the load-time staging (flags, edge vectors) still holds the grid's
   bool profiling = false;
   // dynamic grid update
   bool marked = false;
@@ -173,6 +175,9 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   g.nbp = (g.nbins + 3) / 4 * 4;
   g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
   g.precision = c->cfg.precision;
+  g.chem_fp32 = c->cfg.precision == SX_FP32_TRANSPORT && c->cfg.chem_fp32 ? 1 : 0;
+  g.diffuse = c->cfg.alpha_A > 0.0 ? 1 : 0;
+  g.ground = g.diffuse ? (c->cfg.alpha_A - c->cfg.alpha_B) / c->cfg.alpha_A : 0.0;
   g.punit = 1.0;
   g.transport = c->cfg.transport;
   g.tau_switch = c->cfg.tau_switch;
@@ -181,6 +186,7 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   c->ws_used = L.total + sizeof(double) * 3 * (size_t)c->cfg.nbins;
   char *base = static_cast<char *>(d_workspace);
   // zero the state that must start at zero
+  SX_CUDA(c, cudaMemsetAsync(base + L.off_dif, 0, L.off_P0 - L.off_dif, st));
   SX_CUDA(c, cudaMemsetAsync(base + L.off_P0, 0, L.off_M0 - L.off_P0, st));
   SX_CUDA(c, cudaMemsetAsync(base + L.off_M0, 0, L.off_partials - L.off_M0, st));
   SX_CUDA(c, cudaMemsetAsync(base + L.off_partials, 0, L.off_tabs - L.off_partials, st));
@@ -205,8 +211,11 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
     SX_CUDA(c, sx::launch_ballistic_tables(g, st));
   }
   SX_CUDA(c, sx::launch_rotation(g, *bins_dev, c->cfg.seed, 1, 1, 1.0, st));
-  SX_CUDA(c, sx::launch_kappa_and_consts(g, *bins_dev, c->cfg.sigma, c->cfg.alpha_B, c->cfg.kappa,
-                                          y0 ? g.s_y0 : nullptr, st));
+  // recombination at case A where the cells re-emit the ground-level photons
+  // (diffuse radiation), else at case B (on the spot)
+  SX_CUDA(c, sx::launch_kappa_and_consts(g, *bins_dev, c->cfg.sigma,
+                                          c->cfg.alpha_A > 0.0 ? c->cfg.alpha_A : c->cfg.alpha_B,
+                                          c->cfg.kappa, y0 ? g.s_y0 : nullptr, st));
   unsigned long long diag[sx::kDiagCount];
   SX_CUDA(c, cudaMemcpyAsync(diag, g.diag, sizeof(diag), cudaMemcpyDeviceToHost, st));
   SX_CUDA(c, cudaStreamSynchronize(st));
@@ -235,6 +244,7 @@ static sx::BudgetScale budget_scale(const sx_ctx *c) {
   sc.carry_esc = c->carry_esc;
   sc.carry_fly = c->carry_fly;
   sc.fly_mode = c->fresh_update ? 1 : (c->step > 0 ? 2 : 0);
+  sc.diffuse = c->g.diffuse;
   return sc;
 }
 
@@ -263,6 +273,8 @@ void sx_config_default(sx_config *cfg) {
   cfg->stream = nullptr;
   cfg->transport = SX_TRANSPORT_DCT;
   cfg->tau_switch = 1.0;
+  cfg->chem_fp32 = 0;
+  cfg->alpha_A = 0.0;
 }
 
 int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
@@ -298,6 +310,9 @@ int sx_create(const sx_config *cfg, const double *bin_dirs, sx_ctx **out) {
       cfg->transport != SX_TRANSPORT_COMBINED)
     return fail(nullptr, SX_EINVAL, "transport must be SX_TRANSPORT_DCT, _BALLISTIC or _COMBINED");
   if (std::isnan(cfg->tau_switch)) return fail(nullptr, SX_EINVAL, "tau_switch is NaN");
+  if (cfg->chem_fp32 != 0 && cfg->chem_fp32 != 1) return fail(nullptr, SX_EINVAL, "chem_fp32 must be 0 or 1");
+  if (!(cfg->alpha_A == 0.0 || (cfg->alpha_A >= cfg->alpha_B && std::isfinite(cfg->alpha_A))))
+    return fail(nullptr, SX_EINVAL, "alpha_A must be 0 (on the spot) or a finite value >= alpha_B");
   for (int b = 0; b < cfg->nbins; ++b) {
     const double *d = bin_dirs + 3 * b;
     const double l2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -346,6 +361,9 @@ int sx_load_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *row_ptr
   c->src_rate.clear();
   c->src_slot.clear();
   c->g.nsrc = 0;
+  c->has_ghosts = false;
+  for (int64_t i = 0; i < n; ++i) c->has_ghosts |= (flags[i] & SX_FLAG_GHOST) != 0;
+  c->staging_ok = true;
   c->loaded = true;
   return SX_OK;
 }
@@ -355,10 +373,14 @@ int sx_grid_update_mark(sx_ctx *c, double y_thresh, double min_spacing, int32_t 
   NvtxRange nvtx_range_("sx_grid_update_mark");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "the dynamic grid update")) return rc;
+  if (c->cfg.alpha_A > 0.0)
+    return fail(c, SX_EINVAL, "the dynamic grid update does not hand over diffuse photons (alpha_A > 0)");
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (c->has_ghosts) return fail(c, SX_EINVAL, "the dynamic grid update takes a whole grid, not a shard");
   if (!removed || !n_removed) return fail(c, SX_EINVAL, "NULL argument");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
   sx::DevGrid &g = c->g;
+  c->staging_ok = false;
   // load-time scratch regions are free after the load
   uint8_t *cand = g.s_flags;
   uint8_t *rem = reinterpret_cast<uint8_t *>(g.s_y0);
@@ -386,6 +408,8 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
   NvtxRange nvtx_range_("sx_grid_update_apply");
   if (!c) return SX_EINVAL;
   if (int rc = dct_only(c, "the dynamic grid update")) return rc;
+  if (c->cfg.alpha_A > 0.0)
+    return fail(c, SX_EINVAL, "the dynamic grid update does not hand over diffuse photons (alpha_A > 0)");
   if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
   if (!c->marked || c->mark_step != c->step)
     return fail(c, SX_ESTATE, "sx_grid_update_mark must come right before sx_grid_update_apply");
@@ -477,6 +501,7 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
   c->bins_dev = bins_new;
   c->marked = false;
   c->removed.clear();
+  c->staging_ok = true;  // the new grid's flags and edge vectors
   return SX_OK;
 }
 
@@ -624,7 +649,7 @@ int sx_read_neutral_fraction(sx_ctx *c, double *y_out) {
 // host state, in one little-endian file.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr char kCkptMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '2'};
+constexpr char kCkptMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '3'};
 
 struct CkptHeader {
   char magic[8];
@@ -639,6 +664,8 @@ struct CkptHeader {
   double carry_abs, carry_esc, carry_fly;
   int32_t group, max_degree;
   uint64_t bytes_a, bytes_p, bytes_m, bytes_b, bytes_col;
+  int32_t chem_fp32, has_ghosts;
+  double alpha_A;
 };
 
 using sx::File;  // checksummed writes (sx_ckpt_io.h)
@@ -733,20 +760,36 @@ int sx_save(sx_ctx *c, const char *path) {
   h.bytes_m = r.bytes[2];
   h.bytes_b = r.bytes[3];
   h.bytes_col = r.bytes[4];
+  h.chem_fp32 = c->cfg.chem_fp32;
+  h.alpha_A = c->cfg.alpha_A;
+  h.has_ghosts = c->has_ghosts ? 1 : 0;
+  // written to path.tmp, synced and renamed over path: a save that fails
+  // part-way leaves the previous file at path as it was
+  const std::string tmp = std::string(path) + ".tmp";
   std::vector<char> buf;
-  File f(path, "wb");
-  if (!f.f) return fail(c, SX_EINVAL, std::string("cannot open ") + path + " for writing");
+  File f(tmp.c_str(), "wb");
+  if (!f.f) return fail(c, SX_EINVAL, "cannot open " + tmp + " for writing");
   bool ok = f.write(&h, sizeof(h)) && f.write(c->bins.data(), sizeof(double) * c->bins.size()) &&
             f.write(c->src_vertex.data(), sizeof(int32_t) * c->src_vertex.size()) &&
             f.write(c->src_rate.data(), sizeof(double) * c->src_rate.size());
   const char *base = static_cast<const char *>(c->ws_base);
   for (int k = 0; k < kCkptRegions && ok; ++k) {
     buf.resize(r.bytes[k]);
-    SX_CUDA(c, cudaMemcpyAsync(buf.data(), base + r.off[k], r.bytes[k], cudaMemcpyDeviceToHost, c->stream));
-    SX_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaError_t e = cudaMemcpyAsync(buf.data(), base + r.off[k], r.bytes[k], cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+      f.close();
+      std::remove(tmp.c_str());
+      return fail(c, SX_ECUDA, std::string("cuda: ") + cudaGetErrorString(e));
+    }
     ok = f.write(buf.data(), r.bytes[k]);
   }
-  if (!ok || !sx::write_trailer(f)) return fail(c, SX_EINVAL, std::string("write to ") + path + " failed");
+  ok = ok && sx::write_trailer(f);
+  ok = f.close() && ok;
+  if (!ok || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return fail(c, SX_EINVAL, std::string("write to ") + path + " failed");
+  }
   return SX_OK;
 }
 
@@ -757,18 +800,27 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   if (!path || !d_workspace) return fail(c, SX_EINVAL, "NULL argument");
   if (reinterpret_cast<uintptr_t>(d_workspace) % 256 != 0)
     return fail(c, SX_EINVAL, "workspace not 256-byte aligned");
-  {  // the whole file against its checksum, before anything of it is used
+  // One handle for the check and the restore: the whole file is read
+  // against its checksum before anything of it is used, then read again from
+  // its start.  (A file replaced by a rename in between is not seen: the
+  // handle keeps the file it opened.)
+  File f(path, "rb");
+  {
     std::string why;
-    if (!sx::verify_checkpoint_file(path, kCkptMagic, why))
+    if (!sx::verify_checkpoint_stream(f, kCkptMagic, why))
       return fail(c, SX_EINVAL, std::string(path) + ": " + why);
   }
-  File f(path, "rb");
   CkptHeader h;
-  if (!f.f || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)
+  if (fseeko(f.f, 0, SEEK_SET) != 0 || !f.read(&h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)
     return fail(c, SX_EINVAL, std::string(path) + " is not a checkpoint");
   if (h.nbins != c->cfg.nbins || h.precision != c->cfg.precision)
     return fail(c, SX_EINVAL, "checkpoint bins or precision differ from the context's");
-  if (h.n < 1 || h.nnz < 0 || h.nsrc < 0 || h.nsrc > sx::kMaxSources)
+  // the bounds sx_load_grid applies (the checksum finds damage only: a
+  // checkpoint is trusted input)
+  if (h.n < 1 || h.n >= ((int64_t)1 << 31) || h.nnz < 0 || h.nnz >= ((int64_t)1 << 31) ||
+      h.nsrc < 0 || h.nsrc > sx::kMaxSources || h.step < 0 || (h.group != 0 && h.group != 2 && h.group != 4) ||
+      h.max_degree < 0 || h.max_degree > SX_MAX_DEGREE || !(h.punit > 0.0) || (h.chem_fp32 != 0 && h.chem_fp32 != 1) ||
+      !(h.alpha_A == 0.0 || (h.alpha_A >= h.alpha_B && std::isfinite(h.alpha_A))))
     return fail(c, SX_EINVAL, "corrupt checkpoint header");
   std::vector<double> bins(3 * (size_t)h.nbins);
   std::vector<int32_t> srcv(h.nsrc);
@@ -811,6 +863,9 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   g.nbp = (h.nbins + 3) / 4 * 4;
   g.mw = h.nbins <= 32 ? 1 : (h.nbins <= 64 ? 2 : 4);
   g.precision = h.precision;
+  g.chem_fp32 = h.precision == SX_FP32_TRANSPORT && h.chem_fp32 ? 1 : 0;
+  g.diffuse = h.alpha_A > 0.0 ? 1 : 0;
+  g.ground = g.diffuse ? (h.alpha_A - h.alpha_B) / h.alpha_A : 0.0;
   g.punit = h.punit;
   g.nsrc = h.nsrc;
   g.group = h.group;
@@ -829,6 +884,10 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   c->cfg.chem_frac = h.chem_frac;
   c->cfg.chem_tol = h.chem_tol;
   c->cfg.chem_max_sub = h.chem_max_sub;
+  c->cfg.chem_fp32 = h.chem_fp32;
+  c->cfg.alpha_A = h.alpha_A;
+  c->has_ghosts = h.has_ghosts != 0;
+  c->staging_ok = false;  // the load-time staging is not in a checkpoint
   c->step = h.step;
   c->emitted = h.emitted;
   c->punit_set = h.punit_set != 0;
@@ -845,6 +904,71 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   for (int32_t k = 0; k < h.nsrc; ++k) c->src_slot[srcv[k]] = k;
   c->loaded = true;
   return SX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Shards of one grid: kappa's sums and the halo exchange
+// ---------------------------------------------------------------------------
+int sx_kappa_sums(sx_ctx *c, double *num, double *den) {
+  NvtxRange nvtx_range_("sx_kappa_sums");
+  if (!c) return SX_EINVAL;
+  if (!num || !den) return fail(c, SX_EINVAL, "NULL argument");
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (!c->staging_ok)
+    return fail(c, SX_ESTATE, "the load-time tables are gone (after a restore or a grid update mark)");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  SX_CUDA(c, sx::launch_kappa_parts(c->g, c->bins_dev, c->stream));
+  std::vector<double> part(2 * (size_t)c->g.nblocks_kappa);
+  SX_CUDA(c, cudaMemcpyAsync(part.data(), c->g.kappa_part, sizeof(double) * part.size(),
+                             cudaMemcpyDeviceToHost, c->stream));
+  SX_CUDA(c, cudaStreamSynchronize(c->stream));
+  double a = 0.0, b = 0.0;
+  for (int64_t k = 0; k < c->g.nblocks_kappa; ++k) {  // ascending blocks
+    a += part[2 * k];
+    b += part[2 * k + 1];
+  }
+  *num = a;
+  *den = b;
+  return SX_OK;
+}
+
+int sx_halo_bytes(const sx_ctx *c, int64_t n_edges, int64_t n_rows, int64_t *bytes) {
+  if (!c || !bytes || n_edges < 0 || n_rows < 0) return fail(const_cast<sx_ctx *>(c), SX_EINVAL, "bad arguments");
+  const int nbp = (c->cfg.nbins + 3) / 4 * 4;
+  const int mw = c->cfg.nbins <= 32 ? 1 : (c->cfg.nbins <= 64 ? 2 : 4);
+  const size_t tsz = c->cfg.precision == SX_FP64 ? sizeof(double) : sizeof(float);
+  *bytes = (int64_t)(sx::halo_rows_offset(n_edges, mw) + (size_t)n_rows * nbp * tsz);
+  return SX_OK;
+}
+
+static int halo(sx_ctx *c, bool pack, int64_t n_edges, const int32_t *d_edge_idx, int64_t n_rows,
+                const int32_t *d_row_idx, void *d_buf) {
+  if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "the halo exchange")) return rc;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (c->step < 1) return fail(c, SX_ESTATE, "no step taken yet: nothing to exchange");
+  if (n_edges < 0 || n_rows < 0 || n_edges >= ((int64_t)1 << 31) || n_rows >= ((int64_t)1 << 31))
+    return fail(c, SX_EINVAL, "bad counts");
+  if ((n_edges && !d_edge_idx) || (n_rows && !d_row_idx) || ((n_edges || n_rows) && !d_buf))
+    return fail(c, SX_EINVAL, "NULL argument");
+  if (reinterpret_cast<uintptr_t>(d_buf) % 16 != 0) return fail(c, SX_EINVAL, "buffer not 16-byte aligned");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  // the buffers the last step wrote, which the next step reads
+  const int buf = (int)((c->step - 1) & 1);
+  SX_CUDA(c, sx::launch_halo(c->g, buf, pack, n_edges, d_edge_idx, n_rows, d_row_idx, d_buf, c->stream));
+  return SX_OK;
+}
+
+int sx_halo_pack(sx_ctx *c, int64_t n_edges, const int32_t *d_edge_idx, int64_t n_rows,
+                 const int32_t *d_row_idx, void *d_buf) {
+  NvtxRange nvtx_range_("sx_halo_pack");
+  return halo(c, true, n_edges, d_edge_idx, n_rows, d_row_idx, d_buf);
+}
+
+int sx_halo_unpack(sx_ctx *c, int64_t n_edges, const int32_t *d_edge_idx, int64_t n_rows,
+                   const int32_t *d_row_idx, const void *d_buf) {
+  NvtxRange nvtx_range_("sx_halo_unpack");
+  return halo(c, false, n_edges, d_edge_idx, n_rows, d_row_idx, const_cast<void *>(d_buf));
 }
 
 int sx_read_photons(sx_ctx *c, double *per_vertex, sx_budget *b) {

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <string>
 #include <sys/types.h>
+#include <unistd.h>
 #include <vector>
 
 namespace sx {
@@ -63,6 +64,12 @@ struct File {
     return std::fwrite(p, 1, n, f) == n;
   }
   bool read(void *p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+  bool close() {  // true if the file closed cleanly
+    if (!f) return false;
+    const int r = std::fclose(f);
+    f = nullptr;
+    return r == 0;
+  }
 };
 
 constexpr char kCkptSumMagic[8] = {'S', 'X', 'C', 'K', 'S', 'U', 'M', '1'};
@@ -72,19 +79,21 @@ struct CkptTrailer {
 };
 static_assert(sizeof(CkptTrailer) == 16, "trailer layout");
 
-// Ends a file written through f: appends the trailer (not hashed) and flushes.
+// Ends a file written through f: appends the trailer (not hashed), flushes
+// it and asks the system to put it on storage (fsync).
 inline bool write_trailer(File &f) {
   CkptTrailer t;
   std::memcpy(t.magic, kCkptSumMagic, 8);
   t.checksum = f.hash.digest();
-  return std::fwrite(&t, 1, sizeof(t), f.f) == sizeof(t) && std::fflush(f.f) == 0;
+  return std::fwrite(&t, 1, sizeof(t), f.f) == sizeof(t) && std::fflush(f.f) == 0 &&
+         fsync(fileno(f.f)) == 0;
 }
 
-// Reads the file at path through and checks that it starts with magic
-// (8 bytes) and ends with a trailer whose checksum matches the bytes before
-// it.  Returns true, or false with the reason in why.
-inline bool verify_checkpoint_file(const char *path, const char magic[8], std::string &why) {
-  File f(path, "rb");
+// Reads the open file f through from its start and checks that it starts
+// with magic (8 bytes) and ends with a trailer whose checksum matches the
+// bytes before it.  Returns true, or false with the reason in why; the file
+// position is left anywhere (seek before reading on).
+inline bool verify_checkpoint_stream(File &f, const char magic[8], std::string &why) {
   if (!f.f) {
     why = "cannot open";
     return false;
@@ -126,6 +135,12 @@ inline bool verify_checkpoint_file(const char *path, const char magic[8], std::s
     return false;
   }
   return true;
+}
+
+// The same check of the file at path.
+inline bool verify_checkpoint_file(const char *path, const char magic[8], std::string &why) {
+  File f(path, "rb");
+  return verify_checkpoint_stream(f, magic, why);
 }
 
 }  // namespace sx

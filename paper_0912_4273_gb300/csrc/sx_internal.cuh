@@ -14,6 +14,10 @@ constexpr int kMaxDeg = 64;        // largest non-sink degree the step kernel st
 enum Transport { kTransportDct = 0, kTransportBallistic = 1, kTransportCombined = 2 };
 constexpr int kTile = 32;          // vertices per CTA in the step kernel (one chemistry warp)
 constexpr int kMaxSources = 4096;
+// vertex flags: a sink absorbs everything into "escaped"; a ghost is a copy of
+// a vertex that another shard of the grid steps (the halo exchange fills in
+// what it sends), so it is neither stepped nor counted here
+constexpr int kFlagSink = 1, kFlagGhost = 2;
 constexpr uint32_t kRotTag = 0x53583252u;  // Philox counter word 3 of the rotation draws
 constexpr int kRotMaxAttempts = 64;
 // Step tables are made kRotAhead steps at a time (one rotation launch for up
@@ -80,6 +84,7 @@ struct StepArgs {
   double punit;      // photons per stored unit (a power of two; 1 in FP64 mode)
   double fc, tol;
   int max_sub;
+  int chem_fp32;     // FP32 transport: 1 = subcycle rates in FP32, 0 = FP64 subcycles
   const int32_t *row_ptr;
   const Edge *edges;
   const VConst *vc;
@@ -102,6 +107,10 @@ struct StepArgs {
   double src_scale;        // dt / punit: a source's photons of the step in stored units
   int transport;
   double tau_switch;
+  // diffuse recombination radiation (Sect. 2.2.1, 4.5)
+  int diffuse;             // 1: the cells re-emit their ground-level recombination photons
+  double ground;           // (alpha_A - alpha_B) / alpha_A: photons per recombination
+  double *dif;             // n: photons (stored units) each vertex made in the last step
 };
 
 enum Diag { kDiagSubcycles = 0, kDiagCapped = 1, kDiagError = 2, kDiagMaxDeg = 3, kDiagIndex = 4,
@@ -218,6 +227,7 @@ struct DevGrid {
   int64_t n, nnz;
   int nbins, nbp, mw;   // bins, bins padded to 4, mask words per edge (1, 2 or 4)
   int precision;        // 0 FP64, 1 FP32 transport
+  int chem_fp32;        // FP32 transport: subcycle rates in FP32 (1) or FP64 subcycles (0)
   double punit;         // photons per stored unit (power of two; stored = photons / punit)
   double *pos;          // n*3
   int32_t *row_ptr;     // n+1
@@ -225,9 +235,12 @@ struct DevGrid {
   VConst *vc;           // n
   double *mean_len;     // n
   double *y;            // n
+  double *dif;          // n: diffuse recombination photons made in the last step, stored units
+  int diffuse;          // 1: diffuse recombination radiation on
+  double ground;        // (alpha_A - alpha_B) / alpha_A
   void *P[2];           // n*nbp photons (T), ping-pong
   uint32_t *M[2];       // nnz*mw masks, ping-pong
-  double *partials;     // nblocks*4: absorbed (acc), escaped (acc), in flight (last), spare
+  double *partials;     // nblocks*4: absorbed, escaped (acc), in flight (last), diffuse emitted (acc)
   int64_t nblocks;      // tiles of kTile vertices
   int group;            // step kernel variant: vertices per warp (2 or 4; 0 = 4)
   StepTables *tabs;     // [kTabCount]: the next steps' tables, then the unrotated one (kappa)
@@ -260,7 +273,7 @@ struct DevGrid {
 };
 
 struct Layout {
-  size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_P0, off_P1, off_M0,
+  size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_dif, off_P0, off_P1, off_M0,
       off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       off_B0, off_B1, off_mode0, off_mode1, off_stb, off_bpos, off_binv, total;
@@ -307,6 +320,7 @@ cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, 
 struct BudgetScale {
   double emitted, punit, carry_abs, carry_esc, carry_fly;
   int fly_mode;
+  int diffuse;  // 1: add the diffuse photons the cells emitted (the tiles' fourth partial)
 };
 cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st);
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
@@ -327,5 +341,13 @@ cudaError_t launch_sum_rows(int precision, int64_t n, int nbins, int nbp, const 
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
 // ballistic straight sets of every in-edge (after the edge tables)
 cudaError_t launch_ballistic_tables(DevGrid &g, cudaStream_t st);
+// kappa's per-block sums (numerator, denominator) into g.kappa_part, from the
+// unrotated table (the context's kappa is not touched)
+cudaError_t launch_kappa_parts(DevGrid &g, const double *bins_dev, cudaStream_t st);
+// halo exchange (sx_halo.cu): pack (or unpack) the masks at ne in-edge
+// indices and the photon rows of nr vertices of buffer `buf` into (from) data
+size_t halo_rows_offset(int64_t n_edges, int mw);
+cudaError_t launch_halo(DevGrid &g, int buf, bool pack, int64_t ne, const int32_t *eidx, int64_t nr,
+                        const int32_t *ridx, void *data, cudaStream_t st);
 
 }  // namespace sx

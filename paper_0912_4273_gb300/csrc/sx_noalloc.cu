@@ -22,6 +22,10 @@
 //     serialised on the host by a mutex.
 //   - what must start at zero (the error and degree counters) is cleared on
 //     every call; the rest of the array keeps the last call's contents.
+//   - the call makes `device` current while it runs and the caller's current
+//     device current again before it returns; a call that fails after it
+//     queued work waits for its stream first, so that no work of it still
+//     uses the array when the next call starts.
 // The kernels are the ones sx_load_grid runs; only their buffers differ.
 #include <cstring>
 #include <mutex>
@@ -72,6 +76,19 @@ int fail(int code, const std::string &m) {
   return code;
 }
 
+// Runs when the call returns (while the lock is still held): waits for the
+// stream if the call queued work and failed, then makes the caller's device
+// current again.
+struct CallScope {
+  int prev_device = -1;
+  cudaStream_t st = nullptr;
+  bool queued = false, ok = false;
+  ~CallScope() {
+    if (queued && !ok) cudaStreamSynchronize(st);  // best effort: the error is already reported
+    if (prev_device >= 0) cudaSetDevice(prev_device);
+  }
+};
+
 }  // namespace
 
 extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row_ptr,
@@ -87,7 +104,12 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   if (nbins < 1 || nbins > SX_MAX_BINS) return fail(SX_EINVAL, "nbins must be in 1..SX_MAX_BINS");
   if (device < 0 || device >= 64) return fail(SX_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_mu);
-  cudaError_t e = cudaSetDevice(device);
+  CallScope scope;
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return fail(SX_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  scope.prev_device = prev;
+  e = cudaSetDevice(device);
   if (e != cudaSuccess) return fail(SX_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   if (!g_base[device]) {
     void *p = nullptr;
@@ -98,6 +120,7 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   }
   char *b = static_cast<char *>(g_base[device]);
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  scope.st = st;
   sx::DevGrid g{};
   g.n = n;
   g.nnz = nnz;
@@ -125,6 +148,7 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
     if (e_ != cudaSuccess) return fail(SX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
   // what must start at zero: the error and degree counters
+  scope.queued = true;
   NA_CUDA(cudaMemsetAsync(g.diag, 0, sizeof(unsigned long long) * sx::kDiagCount, st));
   NA_CUDA(cudaMemcpyAsync(g.pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
   NA_CUDA(cudaMemcpyAsync(g.s_row_ptr, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
@@ -139,6 +163,7 @@ extern "C" int sx_kappa_noalloc(int64_t n, const double *pos, const int64_t *row
   NA_CUDA(cudaMemcpyAsync(diag, g.diag, sizeof(diag), cudaMemcpyDeviceToHost, st));
   NA_CUDA(cudaMemcpyAsync(&kappa, g.kappa_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
   NA_CUDA(cudaStreamSynchronize(st));
+  scope.ok = true;  // nothing of the call is left on the stream
 #undef NA_CUDA
   if (diag[sx::kDiagError])
     return fail(SX_EINVAL, "malformed grid (as sx_load_grid would refuse it)");

@@ -29,6 +29,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transpo
   L.off_vc = take(sizeof(VConst) * n);
   L.off_mean_len = take(sizeof(double) * n);
   L.off_y = take(sizeof(double) * n);
+  L.off_dif = take(sizeof(double) * n);
   L.off_P0 = take(tsz * nbp * n);
   L.off_P1 = take(tsz * nbp * n);
   L.off_M0 = take(sizeof(uint32_t) * mw * nnz);
@@ -73,6 +74,7 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.vc = reinterpret_cast<VConst *>(b + L.off_vc);
   g.mean_len = reinterpret_cast<double *>(b + L.off_mean_len);
   g.y = reinterpret_cast<double *>(b + L.off_y);
+  g.dif = reinterpret_cast<double *>(b + L.off_dif);
   g.P[0] = b + L.off_P0;
   g.P[1] = b + L.off_P1;
   g.M[0] = reinterpret_cast<uint32_t *>(b + L.off_M0);
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(256) k_kappa(int64_t n, int nbins, const int32
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double num = 0.0, den = 0.0;
-  if (i < n && !(flags[i] & 1u)) {
+  if (i < n && !(flags[i] & (kFlagSink | kFlagGhost))) {  // interior vertices this grid steps
     const int32_t r0 = rp[i], r1 = rp[i + 1];
     if (r1 > r0) {
       float fn = 0.f, fd = 0.f;
@@ -431,6 +433,13 @@ cudaError_t launch_kappa_and_consts(DevGrid &g, const double *bins_dev, double s
   k_vconst<<<(unsigned)((n + T - 1) / T), T, 0, st>>>(n, g.s_nH, g.s_vol, g.s_flags, y0_dev,
                                                       g.mean_len, g.kappa_dev, sigma, alpha_B,
                                                       g.vc, g.y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_parts(DevGrid &g, const double *bins_dev, cudaStream_t st) {
+  const int T = 256;
+  k_kappa<<<(unsigned)g.nblocks_kappa, T, 0, st>>>(g.n, g.nbins, g.row_ptr, g.edges, g.s_ev,
+                                                   g.s_flags, g.tabs + kTabUnrotated, bins_dev, g.kappa_part);
   return cudaGetLastError();
 }
 

@@ -246,6 +246,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
 
   __shared__ int s_incoming;
   __shared__ long long s_step;
+  // diffuse radiation: the photons each tile vertex emits in this step (made
+  // in the last one), for the budget
+  __shared__ double s_D[kTile];
   // BAL: thick vertices' photons per in-edge and their sources' photons of
   // the step, and every tile vertex's mode (one element each without BAL)
   __shared__ T s_E[BAL ? kTile : 1][BAL ? kMaxDeg : 1];
@@ -253,9 +256,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   __shared__ unsigned char s_thick[BAL ? kTile : 1];
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
-  constexpr int kScr1 = 0;
+  // phase 1 (FP32) keeps the compensation words of the group's rows there
+  constexpr int kScr1 = sizeof(T) == 4 ? kGroup * (32 * MW + 1) * (int)sizeof(T) : 0;
   constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
-  constexpr int kScrB = 96 * (int)sizeof(typename Bud<T>::type);  // the budget terms of a warp
+  constexpr int kScrB = 128 * (int)sizeof(typename Bud<T>::type);  // the budget terms of a warp
   constexpr int kScr13 = kScr1 > kScr3 ? kScr1 : kScr3;
   constexpr int kScr = ((kScr13 > kScrB ? kScr13 : kScrB) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
@@ -274,29 +278,38 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     }
   }
   const int64_t v0 = tile * kTile;
-  if (warp < kTile / 32) {  // the chemistry warps fetch their vertices' constants and y
-    const int64_t nv = min((int64_t)32, a.n - v0 - 32 * warp);
-    const int64_t vw = v0 + 32 * warp;
+  // the chemistry warp (lane per tile vertex)
+  constexpr int cw = 0;
+  static_assert(kTile == 32 && kWarps >= 4, "one chemistry warp of 32 lanes, among >= 4 warps");
+  if (warp == cw) {  // the chemistry warp fetches its vertices' constants and y
+    const int64_t nv = min((int64_t)32, a.n - v0);
     for (int i = lane; i < 2 * nv; i += 32)
-      cp_async16(reinterpret_cast<char *>(s_vc + 32 * warp) + 16 * i,
-                 reinterpret_cast<const char *>(a.vc + vw) + 16 * i);
-    if (lane < nv) cp_async8(s_y + 32 * warp + lane, a.y + vw + lane);
+      cp_async16(reinterpret_cast<char *>(s_vc) + 16 * i, reinterpret_cast<const char *>(a.vc + v0) + 16 * i);
+    if (lane < nv) cp_async8(s_y + lane, a.y + v0 + lane);
     cp_async_commit();
   }
   const int g0 = warp * kGroup;          // first tile vertex of the warp's group
   const int64_t vg = v0 + g0;            // its grid index
   T *grow = s_I + (size_t)g0 * nbs;      // the group's rows
   uint32_t(*gocc)[MW] = s_occ + g0;      // and occupancy
-  // the group's rows, kGroup * nbs * sizeof(T) bytes at an offset that is a
-  // multiple of the same, are cleared with 16-byte stores when G sizeof(T)
-  // is a multiple of 16, else 8-byte ones (G even)
+  // FP32: the rows' compensation words during phase 1 (bin_add), in the
+  // warp's scratch; FP64 sums plainly and never touches them
+  T *gcomp = reinterpret_cast<T *>(s_scr[warp]);
+  // the group's rows (and FP32 compensation words), kGroup * nbs *
+  // sizeof(T) bytes at an offset that is a multiple of the same, are
+  // cleared with 16-byte stores when G sizeof(T) is a multiple of 16, else
+  // 8-byte ones (G even)
   if constexpr (kGroup * sizeof(T) % 16 == 0) {
-    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 16; i += 32)
+    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 16; i += 32) {
       reinterpret_cast<uint4 *>(grow)[i] = make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (sizeof(T) == 4) reinterpret_cast<uint4 *>(gcomp)[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
   } else {
     static_assert(kGroup * sizeof(T) % 8 == 0, "rows cleared in 8-byte words");
-    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 8; i += 32)
+    for (int i = lane; i < kGroup * nbs * (int)sizeof(T) / 8; i += 32) {
       reinterpret_cast<uint2 *>(grow)[i] = make_uint2(0u, 0u);
+      if constexpr (sizeof(T) == 4) reinterpret_cast<uint2 *>(gcomp)[i] = make_uint2(0u, 0u);
+    }
   }
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
@@ -305,7 +318,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       bool thick = false;
       if (vg + lane < a.n) {
         const VConst c = a.vc[vg + lane];
-        thick = !(c.flags & 1) && (a.transport == kTransportBallistic ||
+        thick = !(c.flags & (kFlagSink | kFlagGhost)) && (a.transport == kTransportBallistic ||
                                    __dmul_rn(a.y[vg + lane], c.tau_max) >= a.tau_switch);
       }
       s_thick[g0 + lane] = thick ? 1 : 0;
@@ -316,6 +329,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // overlaps the tile, by the lanes that write it back
   double run_part = 0.0;
   if (lane == 0 && (warp == 1 || warp == 2)) run_part = a.partials[4 * tile + (warp == 1 ? 1 : 0)];
+  if (lane == 0 && warp == 3 && a.diffuse) run_part = a.partials[4 * tile + 3];
   if (reload) __syncthreads(); else __syncwarp();  // the rest of the prologue is the warp's own
 
   const int cur = (int)(s_step & 1);
@@ -339,7 +353,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           const int b = b0 + lane;
           const T val = b < nbins ? Pin[b] : T(0);
           const bool on = val != T(0);
-          add_round<T, MW>(grow, nbs, gocc, on, on ? ((g << 7) | s_fwd[b]) : 0, val, lt_mask);
+          add_round<T, MW>(grow, gcomp, nbs, gocc, on, on ? ((g << 7) | s_fwd[b]) : 0, val, lt_mask);
         }
       }
     }
@@ -364,18 +378,19 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           if (s_thick[g0 + g]) {
             // a thick receiver keeps the edge's photons together: the
             // sender's bins ascending, then the edge packet
-            T acc = T(0);
+            CSum<T> acc;
 #pragma unroll
             for (int w = 0; w < MW; ++w) {
               uint32_t m = my_m[w];
               while (m) {
                 const int i = __ffs(m) - 1;
                 m &= m - 1u;
-                acc += Pp[(size_t)my_src * nbp + 32 * w + i];
+                acc.add(Pp[(size_t)my_src * nbp + 32 * w + i]);
               }
               my_m[w] = 0u;
             }
-            if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc + edge_val;
+            acc.add(edge_val);
+            if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc.value();
             edge_val = T(0);
           }
         } else {
@@ -427,7 +442,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           val = Pp[(size_t)src * nbp + bo];
           key = (gk << 7) | s_fwd[bo];
         }
-        add_round<T, MW>(grow, nbs, gocc, on, key, val, lt_mask);
+        add_round<T, MW>(grow, gcomp, nbs, gocc, on, key, val, lt_mask);
       }
       if constexpr (BAL) {
         // packets from thick senders at thin receivers: into the bin closest
@@ -449,7 +464,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           }
           key = (g << 7) | best;
         }
-        add_round<T, MW>(grow, nbs, gocc, on, key, edge_val, lt_mask);
+        add_round<T, MW>(grow, gcomp, nbs, gocc, on, key, edge_val, lt_mask);
       }
     }
     // a source puts its share in every bin (BAL: a thick source keeps its
@@ -471,9 +486,44 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       T share;
       if constexpr (sizeof(T) == 8) share = a.src_share[slot]; else share = a.src_share_f[slot];
       T *row = grow + (size_t)g * nbs;
-      for (int b = lane; b < nbins; b += 32) row[b] += share;
+      T *crow = gcomp + (size_t)g * nbs;
+      for (int b = lane; b < nbins; b += 32) bin_add(row + b, crow + b, share);
       if (lane < MW) gocc[g][lane] = word_bins(nbins, lane);
       __syncwarp();
+    }
+    if (a.diffuse) {
+      // diffuse radiation: the ground-level recombination photons each vertex
+      // made in the last step enter now, after the sources' and as a
+      // source's do: D / n in every bin (BAL, thick: with its own photons)
+      double dv = 0.0;
+      if (lane < kGroup && vg + lane < a.n) dv = a.dif[vg + lane];
+      if (lane < kGroup) s_D[g0 + lane] = dv;
+      uint32_t ds = __ballot_sync(0xffffffffu, dv > 0.0);
+      while (ds) {
+        const int g = __ffs(ds) - 1;
+        ds &= ds - 1u;
+        const double d = __shfl_sync(0xffffffffu, dv, g);
+        if constexpr (BAL) {
+          if (s_thick[g0 + g]) {
+            if (lane == 0) s_S[g0 + g] += (T)d;
+            __syncwarp();
+            continue;
+          }
+        }
+        const T share = (T)__ddiv_rn(d, (double)nbins);
+        T *row = grow + (size_t)g * nbs;
+        T *crow = gcomp + (size_t)g * nbs;
+        for (int b = lane; b < nbins; b += 32) bin_add(row + b, crow + b, share);
+        if (lane < MW) gocc[g][lane] = word_bins(nbins, lane);
+        __syncwarp();
+      }
+    }
+    if constexpr (sizeof(T) == 4) {  // fold the compensation words into the bins
+      __syncwarp();
+      for (int i = lane; i < kGroup * nbs; i += 32) {
+        const float c = gcomp[i];
+        if (c != 0.f) grow[i] = __fadd_rn(grow[i], c);
+      }
     }
   }
   __syncthreads();
@@ -484,10 +534,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   double bud_abs = 0.0, bud_sink = 0.0;
   FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f};
   unsigned diag_nsub = 0, diag_capped = 0;  // subcycle counters, summed after phase 3
-  if (warp < kTile / 32) {
+  if (warp == cw) {
     cp_async_wait_all();
     __syncwarp();
-    const int vl = warp * 32 + lane;
+    const int vl = lane;
     const int64_t v = v0 + vl;
     T f = T(0);
     int nsub = 0, capped = 0;
@@ -529,26 +579,39 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       }
       if constexpr (sizeof(T) == 8) {
         const double nin = nin_acc;
-        if (c.flags & 1) {
+        if (c.flags & kFlagGhost) {
+          // another shard's vertex: stepped and counted there
+        } else if (c.flags & kFlagSink) {
           bud_sink = nin;  // a sink passes nothing on
         } else {
           double yv = s_y[vl];
+          double d_new = 0.0;  // diffuse radiation: photons made in this step
           if (nin == 0.0 && yv == 1.0) {
             f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
+          } else if (a.diffuse) {
+            double rec = 0.0;
+            f = chem_cell<true>(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
+                                a.fc, a.tol, a.max_sub, nsub, capped, &rec);
+            a.y[v] = yv;
+            if (c.invA != 0.0) d_new = __dmul_rn(a.ground, __ddiv_rn(rec, c.invA)) / a.punit;
           } else {
             f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
                           a.fc, a.tol, a.max_sub, nsub, capped);
             a.y[v] = yv;
           }
+          if (a.diffuse && d_new != s_D[vl]) a.dif[v] = d_new;
           bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
         }
       } else {
         const FF nin = nin_acc;
-        if (c.flags & 1) {
+        if (c.flags & kFlagGhost) {
+          // another shard's vertex: stepped and counted there
+        } else if (c.flags & kFlagSink) {
           bud_sink_ff = nin;  // a sink passes nothing on
         } else {
           double yv = s_y[vl];
           float absf = 0.f;
+          double rec = 0.0;  // diffuse radiation: recombinations per atom in this step
           if (nin.hi == 0.f && yv == 1.0) {
             f = 1.f;  // no photons and nothing to recombine: the state is a fixed point
           } else {
@@ -556,17 +619,28 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
                                         __dmul_rn(c.invA, a.inv_dt));
             if (c.invA == 0.0) {
               f = 1.f;  // no atoms: transparent, nothing to ionise
-            } else if (Fa < 1e30 && c.tau_max < 1e30 && c.R0 < 1e30 && a.dt < 1e30) {
+            } else if (a.chem_fp32 && Fa < 1e30 && c.tau_max < 1e30 && c.R0 < 1e30 && a.dt < 1e30) {
+              float recf = 0.f;
               f = chem_cell_f(yv, (float)Fa, (float)a.dt, (float)c.tau_max, (float)c.R0,
-                              (float)a.fc, (float)a.tol, a.max_sub, nsub, capped, absf);
-            } else {  // rates beyond the FP32 range: the FP64 subcycles
-              const double fd = chem_cell(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
-                                          c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub,
-                                          capped);
+                              (float)a.fc, (float)a.tol, a.max_sub, nsub, capped, absf, recf);
+              rec = recf;
+            } else {  // the FP64 subcycles (by default, and where rates leave the FP32 range)
+              double fd;
+              if (a.diffuse)
+                fd = chem_cell<true>(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
+                                     c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub,
+                                     capped, &rec);
+              else
+                fd = chem_cell(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
+                               c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub, capped);
               f = (float)fd;
               absf = (float)(1.0 - fd);
             }
             a.y[v] = yv;
+          }
+          if (a.diffuse) {
+            const double d_new = c.invA != 0.0 ? __dmul_rn(a.ground, rec / c.invA) / a.punit : 0.0;
+            if (d_new != s_D[vl]) a.dif[v] = d_new;
           }
           bud_abs_ff = ff_mul(nin, absf);
         }
@@ -587,6 +661,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * 32 * MW]
     int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
     if (lane < kGroup && vg + lane < a.n) vflags = s_vc[g0 + lane].flags;
+    if (vflags & kFlagGhost) vflags |= kFlagSink;  // a ghost sends nothing (its owner does)
     if constexpr (BAL) {  // thick vertices send no bins either
       if (lane < kGroup && s_thick[g0 + lane]) vflags |= 1;
     }
@@ -743,20 +818,20 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           const unsigned ent = a.bpos[e];
           const uint8_t *lst = a.binv + 3 * (int64_t)r0 + (ent & 0xFFu);
           const T *Eg = s_E[g0 + g];
-          T acc = T(0);
+          CSum<T> acc;
           for (unsigned i = 0; i < (ent >> 8); ++i)
-            if (SX_INDEX_OK(lst[i] < dg, a.diag)) acc += Eg[lst[i]];
+            if (SX_INDEX_OK(lst[i] < dg, a.diag)) acc.add(Eg[lst[i]]);
           const T S = s_S[g0 + g];
-          if (S != T(0)) acc += (S * s_f[g0 + g]) / (T)dg;
+          if (S != T(0)) acc.add((S * s_f[g0 + g]) / (T)dg);
           const int32_t tw = a.edges[e].twin;
-          if (SX_INDEX_OK((unsigned)tw < (unsigned)a.row_ptr[a.n], a.diag)) Bn[tw] = acc;
+          if (SX_INDEX_OK((unsigned)tw < (unsigned)a.row_ptr[a.n], a.diag)) Bn[tw] = acc.value();
         }
       }
       // every vertex's mode of this step, for its receivers in the next
       if (lane < kGroup && vg + lane < a.n) a.mode[cur][vg + lane] = s_thick[g0 + lane];
     }
   }
-  if (warp < kTile / 32) {  // the chemistry lanes' subcycle counters
+  if (warp == cw) {  // the chemistry lanes' subcycle counters
     unsigned ns = diag_nsub, nc = diag_capped;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -778,28 +853,35 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     if constexpr (sizeof(T) == 8) {
       s_b[lane] = fly.v;
       s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink);
-      if (warp == 0) s_b[64 + lane] = bud_abs;
+      if (warp == cw) s_b[64 + lane] = bud_abs;
+      if (warp == cw && a.diffuse) s_b[96 + lane] = v0 + lane < a.n ? s_D[lane] : 0.0;
     } else {
       s_b[lane] = fly.v;
       s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink_ff);
-      if (warp == 0) s_b[64 + lane] = bud_abs_ff;
+      if (warp == cw) s_b[64 + lane] = bud_abs_ff;
+      if (warp == cw && a.diffuse) {  // the photons emitted as double: hi + lo in float-float
+        const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
+        const float hi = (float)d;
+        s_b[96 + lane] = FF{hi, (float)(d - (double)hi)};
+      }
     }
     __syncthreads();
-    if (warp < 3) {
+    if (warp < 3 || (warp == 3 && a.diffuse)) {
       BT acc;
       if (warp < 2) {
         acc = reinterpret_cast<const BT *>(s_scr[0])[32 * warp + lane];
 #pragma unroll
         for (int w = 1; w < kWarps; ++w)
           acc = Bud<T>::add(acc, reinterpret_cast<const BT *>(s_scr[w])[32 * warp + lane]);
-      } else {
-        acc = reinterpret_cast<const BT *>(s_scr[0])[64 + lane];
+      } else {  // the chemistry warp's terms
+        acc = reinterpret_cast<const BT *>(s_scr[cw])[32 * warp + lane];
       }
       acc = Bud<T>::warp_sum(acc);
       if (lane == 0) {
         double *p = a.partials + 4 * tile;
         const double t = Bud<T>::to_double(acc);
         if (warp == 0) p[2] = t;
+        else if (warp == 3) p[3] = run_part + t;  // diffuse photons emitted, accumulated
         else p[warp == 1 ? 1 : 0] = run_part + t;
       }
     }
@@ -866,6 +948,7 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
   a.fc = fc;
   a.tol = tol;
   a.max_sub = max_sub;
+  a.chem_fp32 = g.chem_fp32;
   a.row_ptr = g.row_ptr;
   a.edges = g.edges;
   a.vc = g.vc;
@@ -891,6 +974,9 @@ StepArgs make_step_args(DevGrid &g, double dt, double fc, double tol, int max_su
   a.src_scale = dt / g.punit;
   a.transport = g.transport;
   a.tau_switch = g.tau_switch;
+  a.diffuse = g.diffuse;
+  a.ground = g.ground;
+  a.dif = g.dif;
   return a;
 }
 
@@ -1029,27 +1115,32 @@ cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, 
 // (emitted, absorbed, escaped, in flight in photons, carries included).
 __global__ void k_budget(int64_t nb, const double *__restrict__ part, double *__restrict__ out,
                          BudgetScale sc) {
-  __shared__ double s[3][256];
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  __shared__ double s[4][256];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   for (int64_t k = threadIdx.x; k < nb; k += blockDim.x) {
     a0 += part[4 * k];
     a1 += part[4 * k + 1];
     a2 += part[4 * k + 2];
+    if (sc.diffuse) a3 += part[4 * k + 3];
   }
   s[0][threadIdx.x] = a0;
   s[1][threadIdx.x] = a1;
   s[2][threadIdx.x] = a2;
+  s[3][threadIdx.x] = a3;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if (threadIdx.x < h)
-      for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
+      for (int c = 0; c < 4; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     out[0] = s[0][0];
     out[1] = s[1][0];
     out[2] = s[2][0];
-    out[4] = sc.emitted;
+    out[3] = s[3][0];
+    // the sources' photons (host) and, with diffuse radiation, the photons
+    // the recombining cells emitted
+    out[4] = sc.diffuse ? __dadd_rn(sc.emitted, __dmul_rn(s[3][0], sc.punit)) : sc.emitted;
     out[5] = __dadd_rn(__dmul_rn(s[0][0], sc.punit), sc.carry_abs);
     out[6] = __dadd_rn(__dmul_rn(s[1][0], sc.punit), sc.carry_esc);
     out[7] = sc.fly_mode == 2 ? __dmul_rn(s[2][0], sc.punit) : (sc.fly_mode == 1 ? sc.carry_fly : 0.0);

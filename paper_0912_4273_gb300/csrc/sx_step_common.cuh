@@ -18,17 +18,23 @@ namespace sx {
 // 1 + expm1(-tau) (its absolute error, 1e-16 of N_in, is what matters for the
 // transmitted photons), and f_c / (Gamma + R) = f_c y / (ion + R0 x y).
 // Returns the transmitted fraction f = (1/dt) sum e^-tau_k h_k.
+// kRec: rec_int receives the recombinations per atom over the step,
+// sum R0 x_k^2 h_k (the hold after equilibrium at the last subcycle's rate),
+// for diffuse recombination radiation.
 // ----------------------------------------------------------------------------
+template <bool kRec = false>
 static __device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt, double invA,
                             double tau_max, double R0, double fc, double tol, int max_sub,
-                            int &nsub, int &capped) {
+                            int &nsub, int &capped, double *rec_int = nullptr) {
   double y = y_io;
   nsub = 0;
   capped = 0;
+  if constexpr (kRec) *rec_int = 0.0;
   if (invA == 0.0) return 1.0;  // no atoms: transparent, nothing to ionise
   const double F = __dmul_rn(N_in, inv_dt);
   double t_left = dt;
   double trans_int = 0.0;
+  double rec_sum = 0.0;
   while (t_left > 0.0) {
     const double em = expm1(-__dmul_rn(tau_max, y));
     const double ab = -em;                   // absorbed fraction
@@ -53,6 +59,7 @@ static __device__ double chem_cell(double &y_io, double N_in, double dt, double 
     }
     const double y_new = __dadd_rn(y, __dmul_rn(__dsub_rn(rec, ion), h));
     trans_int = __dadd_rn(trans_int, __dmul_rn(tr, h));
+    if constexpr (kRec) rec_sum = __dadd_rn(rec_sum, __dmul_rn(rec, h));
     t_left = (h == t_left) ? 0.0 : __dsub_rn(t_left, h);
     nsub++;
     const bool eq = fabs(__dsub_rn(y_new, y)) <= __dmul_rn(tol, y_new);
@@ -60,10 +67,12 @@ static __device__ double chem_cell(double &y_io, double N_in, double dt, double 
     if (t_left > 0.0 && (eq || nsub >= max_sub)) {
       if (!eq) capped = 1;
       trans_int = __dadd_rn(trans_int, __dmul_rn(tr, t_left));
+      if constexpr (kRec) rec_sum = __dadd_rn(rec_sum, __dmul_rn(rec, t_left));
       t_left = 0.0;
     }
   }
   y_io = y;
+  if constexpr (kRec) *rec_int = rec_sum;
   return __dmul_rn(trans_int, inv_dt);
 }
 
@@ -77,13 +86,15 @@ static __device__ double chem_cell(double &y_io, double N_in, double dt, double 
 // in thin ones; *absf is the absorbed fraction, f + absf = 1 up to rounding.
 // Fa = F / A, photoionisations per atom per second at full absorption.
 // ----------------------------------------------------------------------------
+// recf: the recombinations per atom over the step (as rec_int of chem_cell).
 static __device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau, float R0, float fc,
-                             float tol, int max_sub, int &nsub, int &capped, float &absf) {
+                             float tol, int max_sub, int &nsub, int &capped, float &absf,
+                             float &recf) {
   double y = y_io;
   float yf = (float)y, xf = (float)(1.0 - y);
   nsub = 0;
   capped = 0;
-  float t_left = dt, trans = 0.f, absd = 0.f;
+  float t_left = dt, trans = 0.f, absd = 0.f, recd = 0.f;
   while (t_left > 0.f) {
     const float ty = tau * yf;
     const float ab = -expm1f(-ty);  // absorbed fraction
@@ -105,6 +116,7 @@ static __device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau,
     xf -= dy;
     trans += tr * h;
     absd += ab * h;
+    recd += rec * h;
     t_left = (h == t_left) ? 0.f : t_left - h;
     nsub++;
     const bool eq = fabsf(dy) <= tol * yf;
@@ -112,10 +124,12 @@ static __device__ float chem_cell_f(double &y_io, float Fa, float dt, float tau,
       if (!eq) capped = 1;
       trans += tr * t_left;
       absd += ab * t_left;
+      recd += rec * t_left;
       t_left = 0.f;
     }
   }
   y_io = y;
+  recf = recd;
   const float inv_dt = 1.f / dt;
   const float fa = absd * inv_dt, ft = trans * inv_dt;
   if (fa < ft) {
@@ -215,20 +229,53 @@ struct Shape {
   static constexpr int kLanesPerVertex = 32 / G;
 };
 
+// Adds x to the photons of one bin.  FP64: a plain addition.  FP32: a
+// compensated (Kahan-Babuska) addition -- the rounding error of s + x,
+// exact by Knuth's two-sum, is accumulated in the bin's compensation word
+// *c, which the caller folds into the bin once every packet has arrived.
+template <typename T>
+__device__ __forceinline__ void bin_add(T *s, T *c, T x) {
+  if constexpr (sizeof(T) == 8) {
+    *s += x;
+  } else {
+    const float a = *s;
+    const float t = __fadd_rn(a, x);
+    const float xb = __fsub_rn(t, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, xb)), __fsub_rn(x, xb));
+    *s = t;
+    *c = __fadd_rn(*c, err);
+  }
+}
+
+// A sum in registers: FP64 plainly, FP32 compensated as bin_add.
+template <typename T>
+struct CSum {
+  T s = T(0);
+  __device__ void add(T x) { s += x; }
+  __device__ T value() const { return s; }
+};
+template <>
+struct CSum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ void add(float x) { bin_add(&s, &c, x); }
+  __device__ float value() const { return __fadd_rn(s, c); }
+};
+
 // One round of photon packets arriving at the vertices of a warp's group:
 // lane i adds `val` to bin `key & 127` of group vertex `key >> 7` (if `on`).
 // Lanes of equal key add in lane order, one rank at a time, so every bin
-// sums its packets in list order.  The rows start at zero.
+// sums its packets in list order.  The rows start at zero; gcomp holds the
+// rows' compensation words (FP32, see bin_add), laid out as the rows.
 template <typename T, int MW>
-__device__ __forceinline__ void add_round(T *grow, int nbs, uint32_t (*gocc)[MW], bool on,
+__device__ __forceinline__ void add_round(T *grow, T *gcomp, int nbs, uint32_t (*gocc)[MW], bool on,
                                           int key, T val, uint32_t lt_mask) {
   const int k = on ? key : (1 << 12) + (int)(threadIdx.x & 31);  // idle lanes: unique keys
   const uint32_t grp = __match_any_sync(0xffffffffu, k);
   const unsigned rank = __popc(grp & lt_mask);
   const unsigned maxr = __reduce_max_sync(0xffffffffu, on ? rank : 0u);
-  T *dst = grow + (k >> 7) * nbs + (k & 127);
+  const int at = (k >> 7) * nbs + (k & 127);
   for (unsigned r = 0; r <= maxr; ++r) {
-    if (on && rank == r) *dst += val;
+    if (on && rank == r) bin_add(grow + at, gcomp + at, val);
     __syncwarp();
   }
   if (on) atomicOr(&gocc[k >> 7][(k & 127) >> 5], 1u << (k & 31));

@@ -24,6 +24,7 @@ SX_TRANSPORT_DCT, SX_TRANSPORT_BALLISTIC, SX_TRANSPORT_COMBINED = 0, 1, 2
 SX_MAX_BINS = 128
 SX_MAX_DEGREE = 64
 SX_FLAG_SINK = 1
+SX_FLAG_GHOST = 2
 SX_STEP_BLOCK = 16  # steps whose rotation tables one launch makes
 
 
@@ -38,7 +39,8 @@ class sx_config(C.Structure):
                 ("sigma", C.c_double), ("alpha_B", C.c_double), ("kappa", C.c_double),
                 ("chem_frac", C.c_double), ("chem_tol", C.c_double),
                 ("chem_max_sub", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
-                ("transport", C.c_int32), ("tau_switch", C.c_double)]
+                ("transport", C.c_int32), ("tau_switch", C.c_double), ("chem_fp32", C.c_int32),
+                ("alpha_A", C.c_double)]
 
 
 class sx_budget(C.Structure):
@@ -124,6 +126,12 @@ _SIGS = [
                                    C.c_int64, _P(C.c_int32), _P(C.c_double), C.c_int64,
                                    _P(C.c_int32), _P(sx_remesh_result)]),
     ("sx_remesh_free", None, [_P(sx_remesh_result)]),
+    ("sx_kappa_sums", C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double)]),
+    ("sx_halo_bytes", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _P(C.c_int64)]),
+    ("sx_halo_pack", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                               C.c_void_p]),
+    ("sx_halo_unpack", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_void_p]),
 ]
 
 
@@ -361,6 +369,30 @@ def sx_grid_update_apply(ctx, n_new, pos, row_ptr, col, nH, volume, flags, old_o
                                            C.c_void_p(d_workspace), workspace_bytes))
 
 
+def sx_kappa_sums(ctx):
+    """(num, den) of kappa over the loaded grid's interior, non-ghost vertices."""
+    a, b = C.c_double(), C.c_double()
+    _check(ctx, lib().sx_kappa_sums(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def sx_halo_bytes(ctx, n_edges: int, n_rows: int) -> int:
+    out = C.c_int64()
+    _check(ctx, lib().sx_halo_bytes(ctx, n_edges, n_rows, C.byref(out)))
+    return out.value
+
+
+def sx_halo_pack(ctx, n_edges: int, d_edge_idx: int, n_rows: int, d_row_idx: int, d_buf: int):
+    """Device pointers (ints): int32 in-edge and vertex indices, the buffer."""
+    _check(ctx, lib().sx_halo_pack(ctx, n_edges, C.c_void_p(d_edge_idx), n_rows,
+                                   C.c_void_p(d_row_idx), C.c_void_p(d_buf)))
+
+
+def sx_halo_unpack(ctx, n_edges: int, d_edge_idx: int, n_rows: int, d_row_idx: int, d_buf: int):
+    _check(ctx, lib().sx_halo_unpack(ctx, n_edges, C.c_void_p(d_edge_idx), n_rows,
+                                     C.c_void_p(d_row_idx), C.c_void_p(d_buf)))
+
+
 def sx_destroy(ctx):
     lib().sx_destroy(ctx)
 
@@ -481,7 +513,7 @@ class Solver:
                  device: int = 0, stream=None, sigma: float = 6.3e-18, alpha_B: float = 2.59e-13,
                  kappa: float = 0.0, chem_frac: float = 0.5, chem_tol: float = 1e-5,
                  chem_max_sub: int = 1000, transport: int = SX_TRANSPORT_DCT,
-                 tau_switch: float = 1.0):
+                 tau_switch: float = 1.0, chem_fp32: bool = False, alpha_A: float = 0.0):
         import torch
 
         self._torch = torch
@@ -499,6 +531,8 @@ class Solver:
         cfg.chem_max_sub = chem_max_sub
         cfg.transport = transport
         cfg.tau_switch = tau_switch
+        cfg.chem_fp32 = 1 if chem_fp32 else 0
+        cfg.alpha_A = alpha_A
         cfg.device = device
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -14,7 +14,7 @@
 
 int main(int argc, char **argv) {
   if (argc < 4) return 2;
-  static const char kMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '2'};
+  static const char kMagic[8] = {'S', 'X', 'C', 'K', 'P', 'T', '0', '3'};
   uint64_t state = std::strtoull(argv[2], nullptr, 10) * 2 + 1;
   {
     sx::File f(argv[1], "wb");

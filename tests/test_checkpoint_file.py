@@ -11,11 +11,11 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-MAGIC = b"SXCKPT02"
+MAGIC = b"SXCKPT03"
 
 # the write sizes of sx_save for 42 bins and one source (header, bins,
 # source vertices, source rates), then regions of odd sizes
-SAVE_LIKE = [192 - 8, 24 * 42, 4, 8, 1_000_003, 77, 5, 4_194_311]
+SAVE_LIKE = [208 - 8, 24 * 42, 4, 8, 1_000_003, 77, 5, 4_194_311]
 
 
 def _fnv_lanes(data: bytes) -> int:

@@ -7,9 +7,10 @@ Tolerances (element by element):
     the budget as reductions) and exp/expm1 from another library (1-2 ulp)
     -> |dy| <= 1e-9, budget 1e-9 relative.
   * SX_FP32_TRANSPORT: photons are rounded to FP32 at every hop (2^-24
-    relative) and the chemistry's rates, subcycle lengths and exponentials
-    are FP32 (y accumulated in FP64) -> |dy| <= 1e-4 per vertex and 1e-5 of
-    the emitted photons for each budget term.
+    relative; every bin's packets summed with compensation), the chemistry
+    in FP64 (or, with chem_fp32, its rates, subcycle lengths and
+    exponentials in FP32 with y accumulated in FP64) -> |dy| <= 1e-4 per
+    vertex and 1e-5 of the emitted photons for each budget term.
 Routing decisions (association, straight table, bin remap) are integer on
 both sides and therefore identical.
 """
@@ -48,11 +49,12 @@ def c0():
 
 
 @pytest.mark.parametrize("variant", [4, 2])
-@pytest.mark.parametrize("precision,ytol,btol", [(S.SX_FP64, 1e-9, 1e-9),
-                                                 (S.SX_FP32_TRANSPORT, 1e-4, 1e-5)])
-def test_c0_parity(c0, precision, ytol, btol, variant):
+@pytest.mark.parametrize("precision,chem_fp32,ytol,btol", [(S.SX_FP64, False, 1e-9, 1e-9),
+                                                           (S.SX_FP32_TRANSPORT, False, 1e-4, 1e-5),
+                                                           (S.SX_FP32_TRANSPORT, True, 1e-4, 1e-5)])
+def test_c0_parity(c0, precision, chem_fp32, ytol, btol, variant):
     prob, bins, ref, snaps = c0
-    s = S.Solver(bins, precision=precision, seed=0, kappa=ref.kappa).load(prob)
+    s = S.Solver(bins, precision=precision, seed=0, kappa=ref.kappa, chem_fp32=chem_fp32).load(prob)
     s.variant = variant
     assert s.variant == variant
     for k in range(4):
