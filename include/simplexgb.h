@@ -454,6 +454,16 @@ const char *sx_kappa_noalloc_last_error(void);
    sx_grid_update_mark, which reuse the load-time tables), SX_ECUDA. */
 int sx_kappa_sums(sx_ctx *ctx, double *num, double *den);
 
+/* SX_FP32_TRANSPORT stores photons in units of a power of two, by default
+   the power of two just above the photons the sources emit in the first
+   step (so that packets stay near 1 and the scaling is exact).  Shards of
+   one grid exchange stored values, so they must share the unit: set it, on
+   every shard, to the whole grid's (frexp of the sum over all its sources of
+   rate x dt, as 2^exponent) after the load and before the first step.
+   SX_FP64 ignores it.  Errors: SX_EINVAL (not a positive power of two),
+   SX_ESTATE (no grid, or a step has run). */
+int sx_set_photon_unit(sx_ctx *ctx, double unit);
+
 /* Bytes of one halo buffer of n_edges masks and n_rows photon rows: the
    masks (the grid's mask words per edge: 1, 2 or 4 x 32 bits), then, at the
    next 16-byte boundary, the rows (nbins rounded up to 4 values of the

@@ -932,6 +932,19 @@ int sx_kappa_sums(sx_ctx *c, double *num, double *den) {
   return SX_OK;
 }
 
+int sx_set_photon_unit(sx_ctx *c, double unit) {
+  if (!c) return SX_EINVAL;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (c->step != 0) return fail(c, SX_ESTATE, "the photon unit is fixed once a step has run");
+  int ex = 0;
+  if (!(unit > 0.0) || !std::isfinite(unit) || std::frexp(unit, &ex) != 0.5)
+    return fail(c, SX_EINVAL, "the photon unit must be a positive power of two");
+  if (c->cfg.precision == SX_FP64) return SX_OK;  // FP64 stores photons as they are
+  c->g.punit = unit;
+  c->punit_set = true;
+  return SX_OK;
+}
+
 int sx_halo_bytes(const sx_ctx *c, int64_t n_edges, int64_t n_rows, int64_t *bytes) {
   if (!c || !bytes || n_edges < 0 || n_rows < 0) return fail(const_cast<sx_ctx *>(c), SX_EINVAL, "bad arguments");
   const int nbp = (c->cfg.nbins + 3) / 4 * 4;

@@ -27,6 +27,7 @@ group differently).  Direction-conserving transport only.
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 
@@ -151,6 +152,17 @@ def build_plans(prob: I.Problem, nparts: int, bounds: np.ndarray | None = None) 
     return plans
 
 
+def photon_unit(src_rate, dt: float) -> float:
+    """The FP32 photon unit a whole grid with these sources takes at a first
+    step of dt: the power of two just above the photons of one step."""
+    tot = 0.0
+    for r in np.asarray(src_rate, dtype=np.float64):
+        tot += float(r) * dt
+    if not tot > 0.0:
+        return 1.0
+    return math.ldexp(1.0, math.frexp(tot)[1])
+
+
 def global_kappa(sums) -> float:
     """kappa of the whole grid from the shards' (num, den) (sx_kappa_sums)."""
     num = sum(s[0] for s in sums)
@@ -174,6 +186,8 @@ class ShardedSolver:
         self._torch, self._S = torch, S
         self.plans = build_plans(prob, nparts, bounds)
         self.n = prob.n
+        self.src_rate = np.asarray(prob.src_rate, dtype=np.float64)
+        self.started = False
         devs = [torch.device("cuda", d) for d in devices]
         self.devices = [devs[r % len(devs)] for r in range(nparts)]
         self.streams = [torch.cuda.Stream(d) for d in self.devices]
@@ -204,6 +218,11 @@ class ShardedSolver:
 
     def step(self, dt: float, nsteps: int = 1):
         S, torch = self._S, self._torch
+        if not self.started:  # every shard stores photons in the whole grid's unit
+            u = photon_unit(self.src_rate, dt)
+            for s in self.solvers:
+                S.sx_set_photon_unit(s.ctx, u)
+            self.started = True
         for _ in range(nsteps):
             for s in self.solvers:
                 s.step(dt, 1)

@@ -128,6 +128,7 @@ _SIGS = [
     ("sx_remesh_free", None, [_P(sx_remesh_result)]),
     ("sx_kappa_sums", C.c_int, [C.c_void_p, _P(C.c_double), _P(C.c_double)]),
     ("sx_halo_bytes", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, _P(C.c_int64)]),
+    ("sx_set_photon_unit", C.c_int, [C.c_void_p, C.c_double]),
     ("sx_halo_pack", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                C.c_void_p]),
     ("sx_halo_unpack", C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
@@ -374,6 +375,10 @@ def sx_kappa_sums(ctx):
     a, b = C.c_double(), C.c_double()
     _check(ctx, lib().sx_kappa_sums(ctx, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def sx_set_photon_unit(ctx, unit: float):
+    _check(ctx, lib().sx_set_photon_unit(ctx, float(unit)))
 
 
 def sx_halo_bytes(ctx, n_edges: int, n_rows: int) -> int:
