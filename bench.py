@@ -755,6 +755,46 @@ def run_clumpy(args):
         "grid_updates": updates, "budget_residual": res}), flush=True)
 
 
+def run_accuracy(args):
+    """The error of every result against the FP64 oracle on the small Test-1
+    case (C0: 8192 interior vertices, 42 bins, 200 steps of 2.5 Myr), for
+    each precision mode, with on-the-spot and with diffuse recombination
+    radiation: neutral fraction per vertex (max and mean |dy|), each budget
+    term and the photons in flight per vertex (relative to the emitted
+    photons), and the ionised-volume radius."""
+    import oracle as O
+    from paper_0912_4273_gb300 import inputs as I
+    from paper_0912_4273_gb300 import simplex as S
+
+    prob = I.stromgren_problem(8192, seed=0)
+    bins = I.fibonacci_bins(42)
+    dt, steps = 2.5 * I.MYR_S, 200
+    modes = (("fp64", S.SX_FP64, False), ("fp32_transport_fp64_chemistry", S.SX_FP32_TRANSPORT, False),
+             ("fp32_transport_fp32_rates", S.SX_FP32_TRANSPORT, True))
+    out = {}
+    for rad, alpha_A in (("on_the_spot", 0.0), ("diffuse_case_A", 4.18e-13)):
+        ref = O.OracleSim(prob, O.Params(nbins=42, seed=0, alpha_A=alpha_A), bins,
+                          threads=os.cpu_count() or 1)
+        ref.step(dt, steps)
+        ry, rb, rph = ref.y, ref.budget, ref.photons()
+        r_ref = O.ionised_radius_sphere(ry, prob.volume, prob.interior)
+        for name, prec, f32 in modes:
+            s = S.Solver(bins, precision=prec, seed=0, kappa=ref.kappa, chem_fp32=f32,
+                         alpha_A=alpha_A).load(prob)
+            s.step(dt, steps)
+            y, b, ph = s.y, s.budget, s.photons()
+            s.close()
+            dy = np.abs(y - ry)
+            out[f"{rad}/{name}"] = {
+                "max_abs_dy": float(dy.max()), "mean_abs_dy": float(dy.mean()),
+                "budget_rel_err": {k: abs(b[k] - rb[k]) / rb["emitted"] for k in rb},
+                "photons_per_vertex_max_err_rel": float(np.abs(ph - rph).max() / rb["emitted"]),
+                "ionised_radius_rel_err": abs(O.ionised_radius_sphere(y, prob.volume, prob.interior)
+                                              / r_ref - 1.0)}
+    print(json.dumps({"mode": "accuracy", "workload": WORKLOADS["c0"]["name"], "results": out}),
+          flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -768,8 +808,8 @@ def main(argv=None):
                     help="untimed steps before the warm-up (the state the timed steps start from)")
     ap.add_argument("--chem-fp32", action="store_true",
                     help="FP32 subcycle rates (the faster, less exact mode) instead of FP64 subcycles")
-    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport", "shadow"],
-                    default="step")
+    ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport", "shadow",
+                                       "accuracy"], default="step")
     ap.add_argument("--shadow-res", type=int, default=128)
     ap.add_argument("--clumpy-n", type=int, default=1 << 22)
     ap.add_argument("--clumpy-steps", type=int, default=200)
@@ -800,6 +840,9 @@ def main(argv=None):
         return
     if args.mode == "shadow":
         run_shadow(args)
+        return
+    if args.mode == "accuracy":
+        run_accuracy(args)
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -249,6 +249,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // diffuse radiation: the photons each tile vertex emits in this step (made
   // in the last one), for the budget
   __shared__ double s_D[kTile];
+  // each warp's sum of the photons its pairs let escape in phase 3, and the
+  // chemistry lanes' absorbed, sink-bound and transmitted photons (kept here
+  // through phase 3)
+  __shared__ typename Bud<T>::type s_esc[kWarps];
+  __shared__ typename Bud<T>::type s_bud[3][kTile];
   // BAL: thick vertices' photons per in-edge and their sources' photons of
   // the step, and every tile vertex's mode (one element each without BAL)
   __shared__ T s_E[BAL ? kTile : 1][BAL ? kMaxDeg : 1];
@@ -258,13 +263,14 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // phase 3 (the group's staged out-edges and masks, its occupied bins).
   // phase 1 (FP32) keeps the compensation words of the group's rows there
   constexpr int kScr1 = sizeof(T) == 4 ? kGroup * (32 * MW + 1) * (int)sizeof(T) : 0;
-  constexpr int kScr3 = kGroupCap * 8 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
-  constexpr int kScrB = 128 * (int)sizeof(typename Bud<T>::type);  // the budget terms of a warp
-  constexpr int kScr13 = kScr1 > kScr3 ? kScr1 : kScr3;
-  constexpr int kScr = ((kScr13 > kScrB ? kScr13 : kScrB) + 15) / 16 * 16;
+  constexpr int kScr3 = kGroupCap * 12 + kGroupCap * MW * 4 + kGroup * 32 * MW * 2;
+  constexpr int kScr = ((kScr1 > kScr3 ? kScr1 : kScr3) + 15) / 16 * 16;
   __shared__ __align__(16) unsigned char s_scr[kWarps][kScr];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the chemistry warp (lane per tile vertex)
+  constexpr int cw = 0;
+  static_assert(kTile == 32 && kWarps >= 4, "one chemistry warp of 32 lanes, among >= 4 warps");
   const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
   const uint32_t lt_mask = (1u << lane) - 1u;
   if (reload) {  // this step's tables (a CTA keeps them from tile to tile of one grid)
@@ -278,9 +284,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     }
   }
   const int64_t v0 = tile * kTile;
-  // the chemistry warp (lane per tile vertex)
-  constexpr int cw = 0;
-  static_assert(kTile == 32 && kWarps >= 4, "one chemistry warp of 32 lanes, among >= 4 warps");
+
   if (warp == cw) {  // the chemistry warp fetches its vertices' constants and y
     const int64_t nv = min((int64_t)32, a.n - v0);
     for (int i = lane; i < 2 * nv; i += 32)
@@ -327,9 +331,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   }
   // the tile's running budget (escaped, absorbed), read now so that the load
   // overlaps the tile, by the lanes that write it back
-  double run_part = 0.0;
-  if (lane == 0 && (warp == 1 || warp == 2)) run_part = a.partials[4 * tile + (warp == 1 ? 1 : 0)];
-  if (lane == 0 && warp == 3 && a.diffuse) run_part = a.partials[4 * tile + 3];
+
   if (reload) __syncthreads(); else __syncwarp();  // the rest of the prologue is the warp's own
 
   const int cur = (int)(s_step & 1);
@@ -531,8 +533,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // ---------------- phase 2: N_in and chemistry, lane per vertex ----------------
   // photons absorbed in the tile's cells and passed to sinks, in stored units
   // (FP64 sums, or float-float in FP32 mode)
-  double bud_abs = 0.0, bud_sink = 0.0;
-  FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f};
+  // and transmitted (N_in f: in flight, but for what phase 3 finds no edge for)
+  double bud_abs = 0.0, bud_sink = 0.0, bud_tr = 0.0;
+  FF bud_abs_ff{0.f, 0.f}, bud_sink_ff{0.f, 0.f}, bud_tr_ff{0.f, 0.f};
   unsigned diag_nsub = 0, diag_capped = 0;  // subcycle counters, summed after phase 3
   if (warp == cw) {
     cp_async_wait_all();
@@ -601,6 +604,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           }
           if (a.diffuse && d_new != s_D[vl]) a.dif[v] = d_new;
           bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
+          bud_tr = __dmul_rn(nin, f);
         }
       } else {
         const FF nin = nin_acc;
@@ -643,21 +647,32 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
             if (d_new != s_D[vl]) a.dif[v] = d_new;
           }
           bud_abs_ff = ff_mul(nin, absf);
+          bud_tr_ff = ff_mul(nin, f);
         }
       }
     }
     s_f[vl] = f;
     diag_nsub = (unsigned)nsub;
     diag_capped = (unsigned)capped;
+    if constexpr (sizeof(T) == 8) {
+      s_bud[0][vl] = bud_abs;
+      s_bud[1][vl] = bud_sink;
+      s_bud[2][vl] = bud_tr;
+    } else {
+      s_bud[0][vl] = bud_abs_ff;
+      s_bud[1][vl] = bud_sink_ff;
+      s_bud[2][vl] = bud_tr_ff;
+    }
   }
   __syncthreads();
 
   // ---------------- phase 3: transmit, associate, route ----------------
-  Acc<T> fly, esc;
+  Acc<T> esc;  // photons this lane's pairs let escape
   {
     uint32_t *s_q = reinterpret_cast<uint32_t *>(s_scr[warp]);                   // [kGroupCap] q bytes
     uint32_t *s_st = s_q + kGroupCap;                                             // [kGroupCap] straight sets
-    uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_st + kGroupCap);  // [kGroupCap][MW]
+    int32_t *s_tw = reinterpret_cast<int32_t *>(s_st + kGroupCap);               // [kGroupCap] reverse edges
+    uint32_t(*s_am)[MW] = reinterpret_cast<uint32_t(*)[MW]>(s_tw + kGroupCap);  // [kGroupCap][MW]
     uint16_t *s_pair = reinterpret_cast<uint16_t *>(s_am + kGroupCap);          // [kGroup * 32 * MW]
     int vflags = 1;  // lanes < kGroup: flags of group vertex `lane` (past the grid: a sink)
     if (lane < kGroup && vg + lane < a.n) vflags = s_vc[g0 + lane].flags;
@@ -680,6 +695,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           memcpy(&stw, &E.st, 4);
           s_q[idx] = qw;
           s_st[idx] = stw;
+          s_tw[idx] = E.twin;
 #pragma unroll
           for (int w = 0; w < MW; ++w) s_am[idx][w] = 0u;
         }
@@ -751,7 +767,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
                 } else {
                   P = O * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
                 }
-                fly.add(O);
                 Pn[(size_t)(vg + g) * nbp + b] = P;
                 const uint32_t bit = 1u << (b & 31);
                 for (int m = 0; m < cnt; ++m) {
@@ -769,7 +784,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         uint32_t m[MW];
 #pragma unroll
         for (int w = 0; w < MW; ++w) m[w] = idx < kGroupCap ? s_am[idx][w] : 0u;
-        const int32_t tw = a.edges[e].twin;
+        const int32_t tw = idx < kGroupCap ? s_tw[idx] : a.edges[e].twin;
         if (SX_INDEX_OK((unsigned)tw < (unsigned)a.row_ptr[a.n], a.diag))
           store_mask<MW>(M_next, (int64_t)tw, m);  // at the receiver's in-edge index
       }
@@ -796,7 +811,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
             esc.add(o);  // no neighbour within 90 degrees: escaped
             E = T(0);
           } else {
-            fly.add(o);
             if constexpr (sizeof(T) == 8) E = o / (T)cnt;
             else E = o * (cnt == 1 ? 1.f : (cnt == 2 ? 0.5f : (1.f / 3.f)));
           }
@@ -804,7 +818,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       }
       if (lane < kGroup && s_thick[g0 + lane] && s_S[g0 + lane] != T(0)) {
         const T os = s_S[g0 + lane] * s_f[g0 + lane];  // a source sends to all its neighbours
-        (s_R[warp][lane + 1] > s_R[warp][lane] ? fly : esc).add(os);
+        if (s_R[warp][lane + 1] == s_R[warp][lane]) esc.add(os);  // ... if it has any
       }
       __syncwarp();
       T *__restrict__ Bn = static_cast<T *>(a.B[cur]);
@@ -844,46 +858,47 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     }
   }
   // ---------------- budget partials of the tile ----------------
-  // every lane's terms go to its warp's scratch; then warp 0 sums the photons
-  // in flight, warp 1 the escaped ones (and those passed to sinks), warp 2
-  // the absorbed ones, each in a fixed order
+  // The chemistry warp's lanes hold each tile vertex's absorbed, transmitted
+  // and sink-bound photons; phase 3 adds the transmitted photons that found
+  // no edge (rare) to "escaped" and takes them from "in flight".  Each sum
+  // runs in a fixed order: lanes by a shuffle tree, warps ascending.
   {
-    using BT = typename Bud<T>::type;
-    BT *s_b = reinterpret_cast<BT *>(s_scr[warp]);  // [0..31] in flight, [32..63] escaped, [64..95] absorbed
-    if constexpr (sizeof(T) == 8) {
-      s_b[lane] = fly.v;
-      s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink);
-      if (warp == cw) s_b[64 + lane] = bud_abs;
-      if (warp == cw && a.diffuse) s_b[96 + lane] = v0 + lane < a.n ? s_D[lane] : 0.0;
-    } else {
-      s_b[lane] = fly.v;
-      s_b[32 + lane] = Bud<T>::add(esc.v, bud_sink_ff);
-      if (warp == cw) s_b[64 + lane] = bud_abs_ff;
-      if (warp == cw && a.diffuse) {  // the photons emitted as double: hi + lo in float-float
-        const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
-        const float hi = (float)d;
-        s_b[96 + lane] = FF{hi, (float)(d - (double)hi)};
+    using B = Bud<T>;
+    using BT = typename B::type;
+    {  // this warp's escapes
+      BT e = esc.v;
+      bool nz;
+      if constexpr (sizeof(T) == 8) nz = e != 0.0; else nz = e.hi != 0.f;
+      if (__any_sync(0xffffffffu, nz)) e = B::warp_sum(e); else e = BT{};
+      if (lane == 0) s_esc[warp] = e;
+    }
+    BT sum_tr{}, sum_esc{}, sum_abs{}, sum_dif{};
+    if (warp == cw) {
+      sum_abs = B::warp_sum(s_bud[0][lane]);
+      sum_esc = B::warp_sum(s_bud[1][lane]);
+      sum_tr = B::warp_sum(s_bud[2][lane]);
+      if constexpr (sizeof(T) == 8) {
+        if (a.diffuse) sum_dif = B::warp_sum(v0 + lane < a.n ? s_D[lane] : 0.0);
+      } else {
+        if (a.diffuse) {  // the photons emitted, as double: hi + lo in float-float
+          const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
+          const float hi = (float)d;
+          sum_dif = B::warp_sum(FF{hi, (float)(d - (double)hi)});
+        }
       }
     }
     __syncthreads();
-    if (warp < 3 || (warp == 3 && a.diffuse)) {
-      BT acc;
-      if (warp < 2) {
-        acc = reinterpret_cast<const BT *>(s_scr[0])[32 * warp + lane];
+    if (warp == cw && lane == 0) {
+      BT e3 = s_esc[0];
 #pragma unroll
-        for (int w = 1; w < kWarps; ++w)
-          acc = Bud<T>::add(acc, reinterpret_cast<const BT *>(s_scr[w])[32 * warp + lane]);
-      } else {  // the chemistry warp's terms
-        acc = reinterpret_cast<const BT *>(s_scr[cw])[32 * warp + lane];
-      }
-      acc = Bud<T>::warp_sum(acc);
-      if (lane == 0) {
-        double *p = a.partials + 4 * tile;
-        const double t = Bud<T>::to_double(acc);
-        if (warp == 0) p[2] = t;
-        else if (warp == 3) p[3] = run_part + t;  // diffuse photons emitted, accumulated
-        else p[warp == 1 ? 1 : 0] = run_part + t;
-      }
+      for (int w = 1; w < kWarps; ++w) e3 = B::add(e3, s_esc[w]);
+      BT neg;
+      if constexpr (sizeof(T) == 8) neg = -e3; else neg = FF{-e3.hi, -e3.lo};
+      double *p = a.partials + 4 * tile;
+      p[0] += B::to_double(sum_abs);
+      p[1] += B::to_double(B::add(sum_esc, e3));
+      p[2] = B::to_double(B::add(sum_tr, neg));  // in flight after this step
+      if (a.diffuse) p[3] += B::to_double(sum_dif);  // diffuse photons emitted
     }
   }
   if (more) __syncthreads();  // shared state is reused by the next tile of a persistent CTA

@@ -14,14 +14,32 @@ namespace sx {
 // (one ionisation each) and transmits F h e^-tau; its length is
 // h = min(t_left, f_c / (Gamma + R)) with Gamma + R = ion / y + alpha_B n_e;
 // equilibrium (|dy| <= tol y) keeps the last subcycle's rates for the rest of
-// the step.  FP64.  One expm1 and one division per subcycle: e^-tau is
-// 1 + expm1(-tau) (its absolute error, 1e-16 of N_in, is what matters for the
-// transmitted photons), and f_c / (Gamma + R) = f_c y / (ion + R0 x y).
-// Returns the transmitted fraction f = (1/dt) sum e^-tau_k h_k.
+// the step.  FP64.  One expm1 per subcycle: e^-tau is 1 + expm1(-tau) (its
+// absolute error, 1e-16 of N_in, is what matters for the transmitted
+// photons).  f_c / (Gamma + R) = f_c y / (ion + R0 x y) is taken (only where
+// it limits the subcycle) with a Newton-Raphson reciprocal, to 1e-15, and
+// the products and sums fuse into FMAs: GB300 issues an FP64 warp
+// instruction in 16 cycles per SM, and the chemistry's FP64 instructions
+// are a large share of a step.  Returns the transmitted fraction
+// f = (1/dt) sum e^-tau_k h_k.
 // kRec: rec_int receives the recombinations per atom over the step,
 // sum R0 x_k^2 h_k (the hold after equilibrium at the last subcycle's rate),
 // for diffuse recombination radiation.
 // ----------------------------------------------------------------------------
+// f_c y / den by a Newton-Raphson reciprocal: an FP32 seed refined twice
+// in FP64 (each step squares the relative error: 2^-23 -> 2^-46 -> below an
+// ulp); the division itself where den is outside the normal FP32 range.
+static __device__ __forceinline__ double fast_quot(double num, double den) {
+  const float df = (float)den;
+  if (!(df > 1e-37f && df < 1e37f)) return num / den;
+  double r = (double)(1.0f / df);
+  double e = fma(-den, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-den, r, 1.0);
+  r = fma(r, e, r);
+  return num * r;
+}
+
 template <bool kRec = false>
 static __device__ double chem_cell(double &y_io, double N_in, double dt, double inv_dt, double invA,
                             double tau_max, double R0, double fc, double tol, int max_sub,
@@ -31,49 +49,45 @@ static __device__ double chem_cell(double &y_io, double N_in, double dt, double 
   capped = 0;
   if constexpr (kRec) *rec_int = 0.0;
   if (invA == 0.0) return 1.0;  // no atoms: transparent, nothing to ionise
-  const double F = __dmul_rn(N_in, inv_dt);
+  const double F = N_in * inv_dt;
+  const double Fa = F * invA;
   double t_left = dt;
   double trans_int = 0.0;
   double rec_sum = 0.0;
   while (t_left > 0.0) {
-    const double em = expm1(-__dmul_rn(tau_max, y));
+    const double em = expm1(-(tau_max * y));
     const double ab = -em;                   // absorbed fraction
-    const double tr = __dadd_rn(1.0, em);    // transmitted fraction
-    const double ion = __dmul_rn(__dmul_rn(F, ab), invA);  // photoionisations per atom per s
-    const double x = __dsub_rn(1.0, y);
-    const double r0x = __dmul_rn(R0, x);
-    const double rec = __dmul_rn(r0x, x);    // recombinations per atom per s
+    const double tr = 1.0 + em;              // transmitted fraction
+    const double ion = Fa * ab;              // photoionisations per atom per s
+    const double x = 1.0 - y;
+    const double r0x = R0 * x;
+    const double rec = r0x * x;              // recombinations per atom per s
     double h = t_left;
     if (y > 0.0) {
-      const double den = __dadd_rn(ion, __dmul_rn(r0x, y));
-      if (den > 0.0) {
-        const double hc = __ddiv_rn(__dmul_rn(fc, y), den);
-        if (hc < h) h = hc;
-      }
+      const double den = fma(r0x, y, ion);
+      const double fy = fc * y;
+      if (den > 0.0 && fy < den * t_left) h = fast_quot(fy, den);
     } else {
-      const double rate = __dadd_rn(__dmul_rn(__dmul_rn(F, tau_max), invA), r0x);
-      if (rate > 0.0) {
-        const double hc = __ddiv_rn(fc, rate);
-        if (hc < h) h = hc;
-      }
+      const double rate = fma(Fa, tau_max, r0x);
+      if (rate > 0.0 && fc < rate * t_left) h = fast_quot(fc, rate);
     }
-    const double y_new = __dadd_rn(y, __dmul_rn(__dsub_rn(rec, ion), h));
-    trans_int = __dadd_rn(trans_int, __dmul_rn(tr, h));
-    if constexpr (kRec) rec_sum = __dadd_rn(rec_sum, __dmul_rn(rec, h));
-    t_left = (h == t_left) ? 0.0 : __dsub_rn(t_left, h);
+    const double y_new = fma(rec - ion, h, y);
+    trans_int = fma(tr, h, trans_int);
+    if constexpr (kRec) rec_sum = fma(rec, h, rec_sum);
+    t_left = (h == t_left) ? 0.0 : t_left - h;
     nsub++;
-    const bool eq = fabs(__dsub_rn(y_new, y)) <= __dmul_rn(tol, y_new);
+    const bool eq = fabs(y_new - y) <= tol * y_new;
     y = y_new;
     if (t_left > 0.0 && (eq || nsub >= max_sub)) {
       if (!eq) capped = 1;
-      trans_int = __dadd_rn(trans_int, __dmul_rn(tr, t_left));
-      if constexpr (kRec) rec_sum = __dadd_rn(rec_sum, __dmul_rn(rec, t_left));
+      trans_int = fma(tr, t_left, trans_int);
+      if constexpr (kRec) rec_sum = fma(rec, t_left, rec_sum);
       t_left = 0.0;
     }
   }
   y_io = y;
   if constexpr (kRec) *rec_int = rec_sum;
-  return __dmul_rn(trans_int, inv_dt);
+  return trans_int * inv_dt;
 }
 
 // ----------------------------------------------------------------------------
