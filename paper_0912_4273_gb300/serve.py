@@ -17,9 +17,13 @@ count, a time step and a number of steps.  The server
     first keeps the median latency low); requests that have waited longer
     than ``max_wait_s`` since arrival go first, oldest first, so that large
     ones are not held back indefinitely;
-  * loads newly admitted grids on their own stream while the others step;
-  * reads a finished request's neutral fraction and photon budget, releases
-    its workspace and records its latency (finish - arrival).
+  * loads newly admitted grids on a host thread and their own stream while
+    the others step, and reads a finished request's neutral fraction and
+    photon budget on another host thread once its last chunk has run, then
+    releases its workspace and records its latency (results in hand -
+    arrival); the main loop only queues chunks, at most ``max_inflight``
+    ahead of the device, so the GPU is not left idle while the host loads or
+    reads.
 
 Failures are handled on the host: a request larger than the whole budget is
 rejected, a load error fails that request only and returns its memory, a
@@ -34,6 +38,7 @@ CPU with a fake backend.
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import dataclasses
 import time
 from typing import Callable, Dict, List, Optional
@@ -103,12 +108,29 @@ class GpuBackend:
         s.load(req.problem)
         return s
 
+    def load_async(self, req: Request) -> cf.Future:
+        """The load on the loader thread (sx_load_grid waits for its own
+        stream only, so the batches keep running)."""
+        return self._loader().submit(self.load, req)
+
     def step(self, key, solvers: List, dts: List[float], nsteps: int):
+        """Queue a chunk; returns an event that completes with it."""
         if key not in self.batches:
             st = self.torch.cuda.Stream(self.torch.device("cuda", self.device))
             self.streams[key] = st
             self.batches[key] = self.S.Batch(self.max_grids, device=self.device, stream=st)
         self.batches[key].step(solvers, dts, nsteps)
+        ev = self.torch.cuda.Event()
+        ev.record(self.streams[key])
+        return ev
+
+    @staticmethod
+    def done(event) -> bool:
+        return event.query()
+
+    @staticmethod
+    def wait(event):
+        event.synchronize()
 
     def finish(self, solver):
         y = solver.y
@@ -116,13 +138,43 @@ class GpuBackend:
         solver.close()
         return y, b
 
+    def finish_async(self, solver) -> cf.Future:
+        """The reads on the reader thread: they wait for the context's own
+        stream, which waits for the chunks that stepped it, not for later
+        chunks of other grids."""
+        return self._reader().submit(self.finish, solver)
+
     def release(self, solver):
         solver.close()
 
+    def _loader(self):
+        if getattr(self, "_load_pool", None) is None:
+            self._load_pool = cf.ThreadPoolExecutor(max_workers=1, thread_name_prefix="sx-load")
+        return self._load_pool
+
+    def _reader(self):
+        if getattr(self, "_read_pool", None) is None:
+            self._read_pool = cf.ThreadPoolExecutor(max_workers=1, thread_name_prefix="sx-read")
+        return self._read_pool
+
     def close(self):
+        for pool in (getattr(self, "_load_pool", None), getattr(self, "_read_pool", None)):
+            if pool is not None:
+                pool.shutdown(wait=True)
+        self._load_pool = self._read_pool = None
         for b in self.batches.values():
             b.close()
         self.batches.clear()
+
+
+def _done_future(fn, *args) -> cf.Future:
+    """fn(*args) run now, as a completed future (backends without threads)."""
+    f: cf.Future = cf.Future()
+    try:
+        f.set_result(fn(*args))
+    except Exception as e:  # noqa: BLE001 -- handed to the caller through the future
+        f.set_exception(e)
+    return f
 
 
 # Vertices that keep the step kernel busy: about four waves of its resident
@@ -138,7 +190,8 @@ class Server:
     def __init__(self, backend, hbm_budget: int, chunk_steps: int = 8, max_grids: int = 256,
                  clock: Callable[[], float] = time.perf_counter, first_fit: bool = True,
                  fill_vertices: Optional[int] = DEFAULT_FILL_VERTICES,
-                 max_wait_s: Optional[float] = DEFAULT_MAX_WAIT_S, max_retries: int = 1):
+                 max_wait_s: Optional[float] = DEFAULT_MAX_WAIT_S, max_retries: int = 1,
+                 max_inflight: int = 2):
         self.backend = backend
         self.budget = int(hbm_budget)
         self.chunk = int(chunk_steps)
@@ -148,8 +201,12 @@ class Server:
         self.fill = None if fill_vertices is None else int(fill_vertices)
         self.max_wait = None if max_wait_s is None else float(max_wait_s)
         self.max_retries = int(max_retries)
+        self.max_inflight = max(1, int(max_inflight))
         self.pending: collections.deque = collections.deque()
         self.active: Dict[tuple, List[list]] = collections.defaultdict(list)  # key -> [[req, solver, done, bytes]]
+        self.loading: List[list] = []    # [req, future of the solver, bytes]
+        self.reading: List[list] = []    # [req, future of (y, budget), bytes]
+        self.inflight: collections.deque = collections.deque()  # events of queued chunks
         self.used = 0
         self.peak_used = 0
         self.finished: List[Request] = []
@@ -166,6 +223,17 @@ class Server:
                 self.pending.remove(r)
                 r.status = "cancelled"
                 self.finished.append(r)
+                return True
+        for ent in list(self.loading):
+            if ent[0].rid == rid:  # its load runs to the end, then the grid is released
+                self.loading.remove(ent)
+                try:
+                    self.backend.release(ent[1].result())
+                except Exception:
+                    pass
+                self.used -= ent[2]
+                ent[0].status = "cancelled"
+                self.finished.append(ent[0])
                 return True
         for key, lst in self.active.items():
             for ent in lst:
@@ -190,6 +258,55 @@ class Server:
     def _n_active(self) -> int:
         return sum(len(v) for v in self.active.values())
 
+    def _n_resident(self) -> int:
+        return self._n_active() + len(self.loading) + len(self.reading)
+
+    def _load(self, req: Request) -> cf.Future:
+        if hasattr(self.backend, "load_async"):
+            return self.backend.load_async(req)
+        return _done_future(self.backend.load, req)
+
+    def _read(self, solver) -> cf.Future:
+        if hasattr(self.backend, "finish_async"):
+            return self.backend.finish_async(solver)
+        return _done_future(self.backend.finish, solver)
+
+    def _collect_loads(self):
+        keep = []
+        for req, fut, need in self.loading:
+            if not fut.done():
+                keep.append([req, fut, need])
+                continue
+            try:
+                solver = fut.result()
+            except Exception as e:  # load failed: this request only
+                self.used -= need
+                req.status = "failed"
+                req.error = str(e)
+                req.t_done = self.now()
+                self.finished.append(req)
+                continue
+            req.status = "running"
+            self.active[req.key].append([req, solver, 0, need])
+        self.loading = keep
+
+    def _collect_reads(self):
+        keep = []
+        for req, fut, need in self.reading:
+            if not fut.done():
+                keep.append([req, fut, need])
+                continue
+            try:
+                req.y, req.budget = fut.result()
+                req.status = "done"
+            except Exception as e:
+                req.status = "failed"
+                req.error = str(e)
+            req.t_done = self.now()
+            self.used -= need
+            self.finished.append(req)
+        self.reading = keep
+
     def _admit(self):
         now = self.now()
         i = 0
@@ -205,21 +322,13 @@ class Server:
                 req.t_done = now
                 self.finished.append(req)
                 continue
-            if self.used + need <= self.budget and self._n_active() < self.max_grids:
+            if self.used + need <= self.budget and self._n_resident() < self.max_grids:
                 del self.pending[i]
-                try:
-                    solver = self.backend.load(req)
-                except Exception as e:  # load failed: this request only
-                    req.status = "failed"
-                    req.error = str(e)
-                    req.t_done = self.now()
-                    self.finished.append(req)
-                    continue
                 self.used += need
                 self.peak_used = max(self.peak_used, self.used)
-                req.status = "running"
+                req.status = "loading"
                 req.t_admit = self.now()
-                self.active[req.key].append([req, solver, 0, need])
+                self.loading.append([req, self._load(req), need])
                 continue
             if not self.first_fit:
                 break  # strict arrival order: later requests wait behind this one
@@ -249,6 +358,14 @@ class Server:
             nv += ent[0].problem.n
         return picked
 
+    def _throttle(self):
+        """At most max_inflight chunks queued ahead of the device."""
+        while self.inflight and (len(self.inflight) >= self.max_inflight
+                                 or getattr(self.backend, "done", lambda e: True)(self.inflight[0])):
+            ev = self.inflight.popleft()
+            if hasattr(self.backend, "wait"):
+                self.backend.wait(ev)
+
     def _tick(self):
         for key in list(self.active.keys()):
             lst = self.active[key]
@@ -257,26 +374,21 @@ class Server:
             sel = self._select(lst)
             n = min(self.chunk, min(ent[0].steps - ent[2] for ent in sel))
             if n > 0:
+                self._throttle()
                 try:
-                    self.backend.step(key, [ent[1] for ent in sel], [ent[0].dt for ent in sel], n)
+                    ev = self.backend.step(key, [ent[1] for ent in sel], [ent[0].dt for ent in sel], n)
                 except Exception as e:  # the chunk failed: its requests start over
                     self._restart(lst, sel, str(e))
                     continue
+                if ev is not None:
+                    self.inflight.append(ev)
                 for ent in sel:
                     ent[2] += n
             done = [ent for ent in sel if ent[2] >= ent[0].steps]
-            for ent in done:
+            for ent in done:  # its results are read on the reader thread
                 lst.remove(ent)
-                req = ent[0]
-                try:
-                    req.y, req.budget = self.backend.finish(ent[1])
-                    req.status = "done"
-                except Exception as e:
-                    req.status = "failed"
-                    req.error = str(e)
-                req.t_done = self.now()
-                self.used -= ent[3]
-                self.finished.append(req)
+                ent[0].status = "reading"
+                self.reading.append([ent[0], self._read(ent[1]), ent[3]])
 
     def _restart(self, lst: List[list], sel: List[list], why: str):
         """Release the grids of a failed chunk; requeue their requests at the
@@ -307,14 +419,24 @@ class Server:
         for r in sorted(requests, key=lambda r: r.arrival):
             self.submit(r)
         self.t0 = self.clock()
-        while self.pending or self._n_active():
+        while self.pending or self._n_resident():
             self._admit()
+            self._collect_loads()
             if self._n_active():
                 self._tick()
-            elif self.pending:
-                wait = self.pending[0].arrival - self.now()
-                if wait > 0:
-                    time.sleep(min(wait, 0.05) if idle_sleep else 0)
+            self._collect_reads()
+            if not self._n_active():
+                if self.loading or self.reading:  # wait for the host threads
+                    futs = [f for _, f, _ in self.loading + self.reading]
+                    cf.wait(futs, timeout=0.05, return_when=cf.FIRST_COMPLETED)
+                elif self.pending:
+                    wait = self.pending[0].arrival - self.now()
+                    if wait > 0:
+                        time.sleep(min(wait, 0.05) if idle_sleep else 0)
+        while self.inflight:
+            ev = self.inflight.popleft()
+            if hasattr(self.backend, "wait"):
+                self.backend.wait(ev)
         return self.finished
 
     # ------------------------------------------------------------- metrics

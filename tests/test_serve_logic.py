@@ -184,3 +184,80 @@ def test_cancel_a_running_request_releases_its_memory():
     assert srv.used == 100 * 100
     assert srv.cancel(0)
     assert srv.used == 0 and be.released == [0]
+
+
+class FakeEvent:
+    def __init__(self, log):
+        self.log = log
+        self.waited = False
+
+    def query(self):
+        return self.waited
+
+
+class AsyncFakeBackend(FakeBackend):
+    """Loads and reads on host threads (with a delay), chunks as events that
+    complete when waited for; counts the chunks queued ahead of the device."""
+
+    def __init__(self, fail_rids=(), delay=0.002):
+        super().__init__(fail_rids)
+        import concurrent.futures as cf
+        self.pool = cf.ThreadPoolExecutor(max_workers=2)
+        self.delay = delay
+        self.queued = []
+        self.max_queued = 0
+
+    def load_async(self, req):
+        import time
+
+        def work():
+            time.sleep(self.delay)
+            return self.load(req)
+        return self.pool.submit(work)
+
+    def finish_async(self, s):
+        return self.pool.submit(self.finish, s)
+
+    def step(self, key, solvers, dts, n):
+        super().step(key, solvers, dts, n)
+        ev = FakeEvent(self)
+        self.queued.append(ev)
+        self.max_queued = max(self.max_queued, sum(not e.waited for e in self.queued))
+        return ev
+
+    @staticmethod
+    def done(ev):
+        return ev.query()
+
+    @staticmethod
+    def wait(ev):
+        ev.waited = True
+
+
+def test_async_loads_and_reads_complete_every_request():
+    be = AsyncFakeBackend(fail_rids=(3,))
+    srv = SV.Server(be, hbm_budget=100 * 5000, chunk_steps=4, max_inflight=2,
+                    clock=__import__("time").perf_counter)
+    rs = [req(i, 500 + 300 * i, 10 + 3 * i, nbins=42 if i % 2 else 84, arrival=0.001 * i)
+          for i in range(8)]
+    out = srv.run(rs)
+    by = {r.rid: r for r in out}
+    assert by[3].status == "failed" and "simulated" in by[3].error
+    for r in out:
+        if r.rid != 3:
+            assert r.status == "done" and r.y[0] == r.steps
+    assert srv.used == 0 and not srv.loading and not srv.reading
+    assert srv.peak_used <= srv.budget
+    assert be.max_queued <= 2  # never more than max_inflight chunks ahead of the device
+    assert sorted(be.released) == sorted(r.rid for r in out if r.status == "done")
+
+
+def test_cancel_while_loading_releases_the_grid():
+    be = AsyncFakeBackend(delay=0.05)
+    srv = SV.Server(be, hbm_budget=100 * 5000, clock=__import__("time").perf_counter)
+    srv.t0 = srv.clock()
+    srv.submit(req(7, 1000, 5))
+    srv._admit()
+    assert srv.loading and srv.used == 100 * 1000
+    assert srv.cancel(7)
+    assert srv.used == 0 and not srv.loading and be.released == [7]
