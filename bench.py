@@ -531,54 +531,85 @@ def run_batched(args):
 
 
 def run_served(args):
-    """Poisson request stream: sizes log-uniform in [1e4, n_max] on pooled
-    geometries, uniform or clumpy-free Test-1 media, 42 or 84 bins, steps
-    uniform in [100, steps_max]; continuous batching under an HBM budget
-    against serving one request at a time."""
+    """Serving (C4): a Poisson request stream (mean --rate per second) of
+    solves with vertex counts log-uniform in [1e4, --serve-nmax] and, by coin
+    flip, a uniform Test-1 medium (the C0/C1 generator) or the clumpy medium
+    (the C2 generator: lognormal density, 16 sources); 42 or 84 bins; steps
+    uniform in [100, --serve-steps-max].  Grids come from pools of prebuilt
+    geometries (a fresh triangulation per request would take minutes at
+    4e6 points); each request draws its own size (nearest pooled one),
+    source rates, bins, steps and rotation seed.  Continuous batching (the
+    server, default fill target, and with every resident grid in every
+    chunk) against one request at a time on the plain path (sx_step with
+    graphs); the results of every request are compared bit for bit across
+    the policies."""
     import torch
 
     from paper_0912_4273_gb300 import inputs as I
     from paper_0912_4273_gb300 import serve as SV
 
     rng = np.random.default_rng(args.seed)
-    pool_sizes = np.unique(np.round(np.geomspace(1e4, args.serve_nmax, args.pool)).astype(int))
-    pool = _grid_pool(pool_sizes, seed0=2000)
+    pool_sizes = np.unique(np.round(np.geomspace(1e4, args.serve_nmax, args.serve_pool)).astype(int))
+    t_pool = time.perf_counter()
+    uni = _grid_pool(pool_sizes, seed0=2000)
+    clumpy = {int(n): I.cached(I.clumpy_problem, int(n), seed=3000 + i) for i, n in enumerate(pool_sizes)}
+    t_pool = time.perf_counter() - t_pool
     t = 0.0
     reqs = []
     for rid in range(args.requests):
         t += rng.exponential(1.0 / args.rate)
         n = np.exp(rng.uniform(np.log(1e4), np.log(args.serve_nmax)))
         k = int(pool_sizes[np.argmin(np.abs(np.log(pool_sizes) - np.log(n)))])
-        nH = 1e-3
-        rate = 10 ** rng.uniform(47.5, 49)
-        prob = _sized_problem(pool[k], nH, rate)
         nb = int(rng.choice([42, 84]))
         steps = int(rng.integers(100, args.serve_steps_max + 1))
-        dt = 4.0 / (I.ALPHA_B * nH) / steps
+        if rng.random() < 0.5:  # uniform Test-1 medium, box of 2.5 Stromgren radii
+            nH = 1e-3
+            rate = 10 ** rng.uniform(47.5, 49)
+            prob = _sized_problem(uni[k], nH, rate)
+            dt = 4.0 / (I.ALPHA_B * nH) / steps
+            medium = "uniform"
+        else:  # clumpy medium: its 16 sources with fresh log-uniform rates, 0.5 Myr steps
+            import copy
+
+            prob = copy.copy(clumpy[k])
+            prob.src_rate = 10 ** rng.uniform(47, 49, len(prob.src_rate))
+            dt = 0.5 * I.MYR_S
+            medium = "clumpy"
         reqs.append(SV.Request(rid=rid, problem=prob, bins=I.fibonacci_bins(nb), steps=steps,
                                dt=dt, seed=rid, arrival=t))
+        reqs[-1].medium = medium
     free, total = torch.cuda.mem_get_info()
     stats, results = {}, {}
-    # continuous batching with the default fill target, then with every
-    # resident grid in every chunk
     max_wait = SV.DEFAULT_MAX_WAIT_S if args.max_wait is None else (
         None if args.max_wait < 0 else args.max_wait)
-    for name, fill in (("continuous_batching", SV.DEFAULT_FILL_VERTICES),
-                       ("continuous_batching_every_grid", None)):
+    fills = [None if f in ("none", "every") else int(float(f)) for f in args.serve_fills.split(",")]
+    for fill in fills:
+        name = "continuous_batching" if fill == fills[0] else (
+            "continuous_batching_every_grid" if fill is None else f"continuous_batching_fill_{fill}")
         be = SV.GpuBackend()
         srv = SV.Server(be, hbm_budget=int(0.6 * free), chunk_steps=args.chunk, fill_vertices=fill,
                         max_wait_s=max_wait)
         srv.run(reqs)
         be.close()
-        stats[name] = dict(srv.stats(), fill_vertices=fill, max_wait_s=srv.max_wait)
+        stats[name] = dict(srv.stats(), fill_vertices=fill, max_wait_s=srv.max_wait,
+                           chunk_steps=args.chunk)
         results[name] = {r.rid: r.y for r in reqs}
         for r in reqs:
             r.y = None
+            r.status = "pending"
     st_p = SV.serve_one_at_a_time(reqs)
     same = all(np.array_equal(res[r.rid], r.y) for res in results.values() for r in reqs)
+    work = float(sum(r.problem.n * len(r.bins) * r.steps for r in reqs))
+    for v in list(stats.values()) + [st_p]:
+        v["vertex_direction_updates_per_s"] = work / v["makespan_s"]
     print(json.dumps({"mode": "served", "requests": len(reqs), "rate_per_s": args.rate,
-                      "n_range": [1e4, args.serve_nmax], "pool_geometries": len(pool_sizes),
-                      **stats, "one_at_a_time": st_p, "identical_results": same}), flush=True)
+                      "n_range": [1e4, args.serve_nmax], "steps_range": [100, args.serve_steps_max],
+                      "pool_geometries_per_medium": len(pool_sizes), "pool_build_s": t_pool,
+                      "media": {m: sum(r.medium == m for r in reqs) for m in ("uniform", "clumpy")},
+                      **stats, "one_at_a_time": st_p,
+                      "speedup_solves_per_s": stats["continuous_batching"]["solves_per_s"]
+                      / st_p["solves_per_s"],
+                      "identical_results": same}), flush=True)
 
 
 def run_transport(args):
@@ -817,11 +848,15 @@ def main(argv=None):
     ap.add_argument("--grids", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=500)
     ap.add_argument("--pool", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=6, help="served: pooled geometries per medium")
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--rate", type=float, default=50.0)
-    ap.add_argument("--serve-nmax", type=float, default=4e5)
-    ap.add_argument("--serve-steps-max", type=int, default=400)
+    ap.add_argument("--serve-nmax", type=float, default=4e6)
+    ap.add_argument("--serve-steps-max", type=int, default=1000)
     ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--serve-fills", default="131072,none",
+                    help="served: fill targets in vertices to run (the first is the headline; "
+                         "none = every resident grid in every chunk)")
     ap.add_argument("--max-wait", type=float, default=None,
                     help="served: seconds after which a request goes first (< 0: never)")
     ap.add_argument("--seed", type=int, default=0)
