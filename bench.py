@@ -663,11 +663,14 @@ def run_transport(args):
                       "warmup": args.warmup, **rows}), flush=True)
 
 
-def shadow_depth_profile(p, y, max_cells: int = 20):
+def shadow_depth_profile(p, y, max_cells: int = 20, behind_cells=None, slice_cells=None):
     """Ionised fraction (y < 0.5) of the vertices in the slab's geometric
     shadow, behind it and inside 0.85 r_S, by their distance in cells from the
     shadow cone's edge (bins of one cell); and the depth, in cells, of the
-    first bin that is mostly neutral (the front's penetration)."""
+    first bin that is mostly neutral (the front's penetration).
+    behind_cells: only vertices within that many cells behind the slab's far
+    face; slice_cells: only vertices within that many cells of the source's
+    z plane (a slice like the paper's figures)."""
     from paper_0912_4273_gb300 import inputs as I
 
     lo, hi = np.array(p.meta["slab_lo"]), np.array(p.meta["slab_hi"])
@@ -681,6 +684,10 @@ def shadow_depth_profile(p, y, max_cells: int = 20):
     depth = np.minimum(0.5 * (hi[1] - lo[1]) * x / near - np.abs(d[:, 1]),
                        0.5 * (hi[2] - lo[2]) * x / near - np.abs(d[:, 2])) / cell
     sel &= depth > 0
+    if behind_cells is not None:
+        sel &= x < far + (1 + behind_cells) * cell
+    if slice_cells is not None:
+        sel &= np.abs(d[:, 2]) < slice_cells * cell
     prof, pen = [], None
     for k in range(max_cells):
         m = sel & (depth >= k) & (depth < k + 1)
@@ -693,11 +700,13 @@ def shadow_depth_profile(p, y, max_cells: int = 20):
 
 def run_shadow(args):
     """Test 2 (Sect. 5.2): a point source and a slab 200 times denser than its
-    surroundings, 500 Myr at dt = 0.5 Myr, FP32 transport, on the Test-1 grid
-    at --shadow-res^3 points; 42 and 84 bins, and ballistic transport.
-    Reports, by depth in cells into the slab's shadow, the ionised fraction,
-    and the penetration depth (the paper: about 5 cells at 64^3; 8 (84 bins)
-    and 15 (42 bins) at 128^3)."""
+    surroundings, 500 Myr at dt = --shadow-dt Myr (0.5 by default), FP32
+    transport, on the Test-1 grid at --shadow-res^3 points; 42 and 84 bins,
+    and ballistic transport.  Reports, by depth in cells into the slab's
+    shadow, the ionised fraction, and the penetration depth (the paper:
+    about 5 cells at 64^3; 8 (84 bins) and 15 (42 bins) at 128^3), over the
+    whole shadow out to 0.85 r_S and in a slice like the paper's figures
+    (within 1.5 cells of the source's plane, 12 cells behind the slab)."""
     from paper_0912_4273_gb300 import inputs as I
     from paper_0912_4273_gb300 import simplex as S
 
@@ -706,19 +715,24 @@ def run_shadow(args):
     p = I.cached(I.shadow_problem, n, seed=args.seed)
     t_grid = time.perf_counter() - t0
     out = {}
+    dt_myr = args.shadow_dt
+    steps = int(round(500.0 / dt_myr))
     for name, tp, nb in (("dct_84", S.SX_TRANSPORT_DCT, 84), ("dct_42", S.SX_TRANSPORT_DCT, 42),
                          ("ballistic", S.SX_TRANSPORT_BALLISTIC, 84)):
         s = S.Solver(I.fibonacci_bins(nb), precision=S.SX_FP32_TRANSPORT, seed=args.seed,
                      transport=tp).load(p)
         t0 = time.perf_counter()
-        s.step(0.5 * I.MYR_S, 1000)
+        s.step(dt_myr * I.MYR_S, steps)
         y = s.y
         el = time.perf_counter() - t0
         s.close()
         prof, pen = shadow_depth_profile(p, y)
-        out[name] = {"penetration_cells": pen, "ionised_fraction_by_depth": prof, "seconds": el}
+        sprof, spen = shadow_depth_profile(p, y, behind_cells=12, slice_cells=1.5)
+        out[name] = {"penetration_cells": pen, "ionised_fraction_by_depth": prof,
+                     "slice_penetration_cells": spen, "slice_ionised_fraction_by_depth": sprof,
+                     "seconds": el}
     print(json.dumps({"mode": "shadow", "resolution": args.shadow_res, "n_vertices": p.n,
-                      "grid_build_s": t_grid, **out}), flush=True)
+                      "dt_myr": dt_myr, "steps": steps, "grid_build_s": t_grid, **out}), flush=True)
 
 
 def run_clumpy(args):
@@ -842,6 +856,7 @@ def main(argv=None):
     ap.add_argument("--mode", choices=["step", "batched", "served", "clumpy", "transport", "shadow",
                                        "accuracy"], default="step")
     ap.add_argument("--shadow-res", type=int, default=128)
+    ap.add_argument("--shadow-dt", type=float, default=0.5, help="shadow: time step in Myr")
     ap.add_argument("--clumpy-n", type=int, default=1 << 22)
     ap.add_argument("--clumpy-steps", type=int, default=200)
     ap.add_argument("--update-every", type=int, default=50)

@@ -463,6 +463,36 @@ def equilibrium_profile(r_max: float, rate: float, nH: float, alpha_B: float, si
     return r, y, tau
 
 
+def ifront_position(y, pos, volume, mask, centre, r_max, nshell: int = 56) -> float:
+    """I-front position: the outermost radius at which the volume-weighted
+    average of the ionised fraction x = 1 - y over spherical shells about
+    ``centre`` (width r_max / nshell, vertices in ``mask``) falls through
+    0.5, linearly interpolated between shell midpoints; nan if it never
+    does."""
+    d = np.linalg.norm(np.asarray(pos)[mask] - np.asarray(centre), axis=1)
+    x = 1.0 - np.asarray(y)[mask]
+    v = np.asarray(volume)[mask]
+    edges = np.linspace(0.0, r_max, nshell + 1)
+    k = np.digitize(d, edges) - 1
+    ok = (k >= 0) & (k < nshell)
+    vol = np.bincount(k[ok], weights=v[ok], minlength=nshell)
+    xs = np.bincount(k[ok], weights=(x * v)[ok], minlength=nshell) / np.maximum(vol, 1e-300)
+    mid = 0.5 * (edges[1:] + edges[:-1])
+    for j in range(nshell - 1, 0, -1):
+        if xs[j - 1] >= 0.5 > xs[j]:
+            return float(mid[j - 1] + (xs[j - 1] - 0.5) / (xs[j - 1] - xs[j]) * (mid[j] - mid[j - 1]))
+    return float("nan")
+
+
+def equilibrium_front(rate: float, nH: float, alpha_B: float, sigma: float) -> float:
+    """Radius where the equilibrium profile (Eq. inner_stromgren_region) is
+    half ionised."""
+    rs = stromgren_radius(rate, nH, alpha_B)
+    r, y, _ = equilibrium_profile(2.0 * rs, rate, nH, alpha_B, sigma)
+    j = int(np.argmax(y > 0.5))
+    return float(r[j - 1] + (0.5 - y[j - 1]) / (y[j] - y[j - 1]) * (r[j] - r[j - 1]))
+
+
 def ionised_radius_octant(y, volume, interior_mask) -> float:
     """I-front radius of a corner source from the ionised volume of the octant."""
     vi = float(np.sum((1.0 - y[interior_mask]) * volume[interior_mask]))

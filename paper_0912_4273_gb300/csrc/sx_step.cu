@@ -317,6 +317,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   }
   if (lane < kGroup * MW) (&gocc[0][0])[lane] = 0u;
   if (lane <= kGroup) s_R[warp][lane] = a.row_ptr[vg + lane < a.n ? vg + lane : a.n];
+  // Ballistic transport alone: every vertex but the sinks (and ghosts) is
+  // thick in every step and writes every out-edge's packet, so an in-edge's
+  // packet is always the sender's of the last step (0 from a sink, which
+  // never writes), and no bin masks or sender modes are needed.
+  const bool pure_bal = BAL && a.transport == kTransportBallistic;
   if constexpr (BAL) {  // the group's modes: thick where y tau_max reaches tau_switch
     if (lane < kGroup) {
       bool thick = false;
@@ -372,10 +377,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       for (int w = 0; w < MW; ++w) my_m[w] = 0u;
       T edge_val = T(0);  // BAL: a packet that a thick sender routed along this edge
       if (e < R[kGroup]) {
-        my_src = a.col[e];
-        if (!SX_INDEX_OK((unsigned)my_src < (unsigned)a.n, a.diag)) my_src = 0;
+        if (!pure_bal) {
+          my_src = a.col[e];
+          if (!SX_INDEX_OK((unsigned)my_src < (unsigned)a.n, a.diag)) my_src = 0;
+        }
         if constexpr (BAL) {
-          if (a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
+          if (pure_bal || a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
           else load_mask<MW>(M_prev, (int64_t)e, my_m);
           if (s_thick[g0 + g]) {
             // a thick receiver keeps the edge's photons together: the
@@ -568,7 +575,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         // thin one (its masks are empty) and skips the per-edge sends
         bool dark;
         if constexpr (sizeof(T) == 8) dark = nin_acc == 0.0; else dark = nin_acc.hi == 0.f;
-        if (thick_v && dark) s_thick[vl] = 0;
+        if (thick_v && dark && !pure_bal) s_thick[vl] = 0;
       }
 #pragma unroll
       for (int w = 0; w < MW; ++w) {
@@ -682,7 +689,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     }
     const uint32_t sinks = __ballot_sync(0xffffffffu, vflags & 1);
     // consecutive vertices ga .. gb - 1 whose out-edges fit in the staging area
-    for (int ga = 0; ga < kGroup;) {
+    // (ballistic transport alone sends no bins: nothing to stage)
+    for (int ga = pure_bal ? kGroup : 0; ga < kGroup;) {
       int gb = ga + 1;
       while (gb < kGroup && s_R[warp][gb + 1] - s_R[warp][ga] <= kGroupCap) ++gb;
       const int32_t EA = s_R[warp][ga], EB = s_R[warp][gb];
@@ -842,7 +850,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         }
       }
       // every vertex's mode of this step, for its receivers in the next
-      if (lane < kGroup && vg + lane < a.n) a.mode[cur][vg + lane] = s_thick[g0 + lane];
+      if (!pure_bal && lane < kGroup && vg + lane < a.n) a.mode[cur][vg + lane] = s_thick[g0 + lane];
     }
   }
   if (warp == cw) {  // the chemistry lanes' subcycle counters
@@ -1174,14 +1182,14 @@ template <typename T, int MW>
 __global__ void k_inflight(int64_t n, int nbins, int nbp, const int32_t *__restrict__ rp,
                            const Edge *__restrict__ edges, const T *__restrict__ P,
                            const uint32_t *__restrict__ M, const uint8_t *__restrict__ mode,
-                           const T *__restrict__ B, double *__restrict__ out) {
+                           const T *__restrict__ B, double *__restrict__ out, bool all_ballistic) {
   const int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (v >= n) return;
   double s = 0.0;
   for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
     const Edge E = edges[e];
-    if (mode && mode[E.col]) {
+    if (all_ballistic || (mode && mode[E.col])) {
       if (lane == 0) s += (double)B[e];
       continue;
     }
@@ -1202,18 +1210,19 @@ cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st) {
   const int cur = (int)((step + 1) & 1);
   const unsigned blocks = (unsigned)((g.n * 32 + 255) / 256);
   const uint8_t *mode = g.mode[cur];  // null in direction-conserving transport
+  const bool allb = g.transport == kTransportBallistic;
   if (g.precision == 0) {
     const double *P = static_cast<const double *>(g.P[cur]);
     const double *B = static_cast<const double *>(g.B[cur]);
-    if (g.mw == 1) k_inflight<double, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
-    else if (g.mw == 2) k_inflight<double, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
-    else k_inflight<double, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    if (g.mw == 1) k_inflight<double, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
+    else if (g.mw == 2) k_inflight<double, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
+    else k_inflight<double, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
   } else {
     const float *P = static_cast<const float *>(g.P[cur]);
     const float *B = static_cast<const float *>(g.B[cur]);
-    if (g.mw == 1) k_inflight<float, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
-    else if (g.mw == 2) k_inflight<float, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
-    else k_inflight<float, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out);
+    if (g.mw == 1) k_inflight<float, 1><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
+    else if (g.mw == 2) k_inflight<float, 2><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
+    else k_inflight<float, 4><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, g.row_ptr, g.edges, P, g.M[cur], mode, B, g.s_out, allb);
   }
   return cudaGetLastError();
 }

@@ -83,8 +83,10 @@ def test_thousand_steps(grid, oracle_setup):
     r, yp, _ = O.equilibrium_profile(1.6 * O.stromgren_radius(NDOT, NH, ALPHA), NDOT, NH, ALPHA,
                                      I.SIGMA_H)
     r_eq = (3 * np.trapezoid((1 - yp) * r * r, r)) ** (1 / 3)
-    fronts = []
-    for stop in (300, 600, 800, 999):
+    fronts, positions = [], []
+    rs = O.stromgren_radius(NDOT, NH, ALPHA)
+    src = grid.pos[grid.src_vertex[0]]
+    for stop in (244, 300, 600, 800, 999):
         s.step(DT, stop - done)
         y_prev, n_in = s.y, s.photons()
         s.step(DT, 1)
@@ -102,6 +104,8 @@ def test_thousand_steps(grid, oracle_setup):
         t = done * DT
         fronts.append((t, O.ionised_radius_sphere(y_new, grid.volume, grid.interior)
                        / (r_eq * (1 - math.exp(-t / tr)) ** (1 / 3))))
+        positions.append((t, O.ifront_position(y_new, grid.pos, grid.volume, grid.interior, src,
+                                               1.4 * rs)))
     assert s.info["step"] == 1000
     assert s.info["capped"] == 0
     # the I-front (ionised-volume radius) against the equilibrium solution:
@@ -110,6 +114,16 @@ def test_thousand_steps(grid, oracle_setup):
         if t >= 2.4 * tr:
             assert abs(ratio - 1) < 0.02, (t / I.MYR_S, ratio)
     assert abs(fronts[-1][1] - 1) < 0.01, fronts
+    # the front position (half-ionised shell): within 1% of the analytic
+    # history (Eq. IFront_pos) at one recombination time, and at 500 Myr
+    # within 1% of the equilibrium profile's front (1.053 r_S, a soft edge)
+    # on the same history
+    t, r = positions[0]
+    assert abs(t / tr - 1) < 0.01
+    assert abs(r / O.ifront_radius(t, NDOT, NH, ALPHA) - 1) < 0.01, (t / tr, r / rs)
+    t, r = positions[-1]
+    r_half = O.equilibrium_front(NDOT, NH, ALPHA, I.SIGMA_H)
+    assert abs(r / (r_half * (1 - math.exp(-t / tr)) ** (1 / 3)) - 1) < 0.01, (t / tr, r / rs)
     # the FP32 run against the FP64 device path over all 1000 steps
     y32 = s.y
     s.close()

@@ -130,3 +130,25 @@ def test_subcycling_reading_does_not_move_the_front():
     (r0, st0), (r1, st1) = runs
     assert np.abs(r1 / r0 - 1).max() < 5e-3
     assert st1["subcycles"] > 3 * st0["subcycles"] and st0["capped"] == st1["capped"] == 0
+
+
+def test_front_position_follows_the_analytic_history_at_t_rec(paper):
+    """At one recombination time the front (the half-ionised shell) is
+    within 1% of the analytic sharp-front history r_S (1 - e^-1)^(1/3) (Eq.
+    IFront_pos) with the C1 time step of 0.5 Myr; the front of the
+    equilibrium profile itself lies at 1.053 r_S (its edge is soft), which
+    the late front approaches."""
+    nH, Nd, a = paper["n_H"], paper["Ndot"], paper["alpha_B"]
+    rs = O.stromgren_radius(Nd, nH, a)
+    tr = O.recombination_time(nH, a)
+    r_half = O.equilibrium_front(Nd, nH, a, I.SIGMA_H)
+    assert 1.04 < r_half / rs < 1.07
+    prob = I.stromgren_problem(8192, seed=0)
+    sim = O.OracleSim(prob, O.Params(nbins=42, seed=0), I.fibonacci_bins(42), threads=4)
+    dt = 0.5 * I.MYR_S
+    steps = int(round(tr / dt))
+    sim.step(dt, steps)
+    src = prob.pos[prob.src_vertex[0]]
+    r = O.ifront_position(sim.y, prob.pos, prob.volume, prob.interior, src, 1.4 * rs)
+    expect = O.ifront_radius(steps * dt, Nd, nH, a)
+    assert abs(r / expect - 1) < 0.01, r / expect
