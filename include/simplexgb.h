@@ -339,23 +339,37 @@ int sx_restore(sx_ctx *ctx, const char *path, void *d_workspace, int64_t workspa
  * default) or 2 (16 warps per tile).  Both compute the same step; sums whose
  * order follows the warps (N_in, the budget) can differ in the last bits, so
  * results are reproducible for a given variant.  A batch steps with the
- * variant of its first grid.
+ * variant of its first grid.  The stored photons' row stride (bin packing)
+ * is the other launch choice: nbins rounded up to 4 ("packed", the default:
+ * 44 for 42 bins) or to 8 ("aligned": 48, rows of 32-byte multiples in
+ * FP32); it changes no result.  The workspace has room for either.
  * ------------------------------------------------------------------------- */
 #define SX_TUNE_MAX_CANDIDATES 4
 
 typedef struct sx_tune_result {
   int32_t variant;                        /* chosen: vertices per warp */
-  int32_t ncandidates;                    /* variants tried */
-  int32_t candidates[SX_TUNE_MAX_CANDIDATES];
+  int32_t ncandidates;                    /* variants tried (vertices per warp x stride) */
+  int32_t candidates[SX_TUNE_MAX_CANDIDATES];  /* vertices per warp of each */
   double ms_per_step[SX_TUNE_MAX_CANDIDATES]; /* mean step time of each (rotation + step) */
+  int32_t stride;                         /* chosen: row stride of the stored photons */
+  int32_t strides[SX_TUNE_MAX_CANDIDATES];  /* row stride of each */
 } sx_tune_result;
 
 /* Set (2 or 4) or read the variant of a context.  Errors: SX_EINVAL. */
 int sx_set_variant(sx_ctx *ctx, int32_t variant);
 int sx_get_variant(sx_ctx *ctx, int32_t *variant);
 
-/* Autotuner: times every variant for nsteps steps of size dt_s on the loaded
-   grid, from its current state, and keeps the fastest.  The grid's state is
+/* Set or read the row stride of the stored photons: nbins rounded up to 4 or
+   to 8.  Setting moves the photons the next step reads to the new stride (a
+   queued copy on the context's stream); results are unchanged bit for bit.
+   Errors: SX_EINVAL (another stride, not direction conserving), SX_ESTATE (no
+   grid, or a grid update marked but not applied), SX_ECUDA. */
+int sx_set_bin_stride(sx_ctx *ctx, int32_t stride);
+int sx_get_bin_stride(sx_ctx *ctx, int32_t *stride);
+
+/* Autotuner: times every variant (vertices per warp x row stride) for
+   nsteps steps of size dt_s on the loaded grid, from its current state,
+   and keeps the fastest.  The grid's state is
    saved in `scratch` (device memory owned by the caller, at least
    sx_workspace_bytes of the loaded grid, 256-byte aligned) and restored
    after every trial, so the call leaves the simulation exactly where it was

@@ -172,7 +172,7 @@ static int build_grid(sx_ctx *c, int64_t n, const double *pos, const int64_t *ro
   g.n = n;
   g.nnz = nnz;
   g.nbins = c->cfg.nbins;
-  g.nbp = (g.nbins + 3) / 4 * 4;
+  g.nbp = sx::bin_stride_packed(g.nbins);
   g.mw = g.nbins <= 32 ? 1 : (g.nbins <= 64 ? 2 : 4);
   g.precision = c->cfg.precision;
   g.chem_fp32 = c->cfg.precision == SX_FP32_TRANSPORT && c->cfg.chem_fp32 ? 1 : 0;
@@ -454,6 +454,7 @@ int sx_grid_update_apply(sx_ctx *c, int64_t n_new, const double *pos, const int6
                       workspace_bytes, gn, Ln, &bins_new);
   if (rc) return rc;
   gn.punit = go.punit;
+  gn.nbp = go.nbp;  // the row stride carries over (the new workspace has room for either)
   const int64_t s = c->step;
   const int prev_new = (int)((s & 1) ^ 1);
   int32_t *d_map = reinterpret_cast<int32_t *>(gn.s_out);
@@ -666,6 +667,7 @@ struct CkptHeader {
   uint64_t bytes_a, bytes_p, bytes_m, bytes_b, bytes_col;
   int32_t chem_fp32, has_ghosts;
   double alpha_A;
+  int32_t nbp, reserved;  // the live row stride of the stored photons
 };
 
 using sx::File;  // checksummed writes (sx_ckpt_io.h)
@@ -678,9 +680,8 @@ constexpr int kCkptRegions = 6;
 struct CkptRegions {
   size_t off[kCkptRegions], bytes[kCkptRegions];
 };
-CkptRegions ckpt_regions(const sx::Layout &L, int64_t n, int64_t nnz, int nbins, int precision,
-                         int64_t step) {
-  const int nbp = (nbins + 3) / 4 * 4;
+CkptRegions ckpt_regions(const sx::Layout &L, int64_t n, int64_t nnz, int nbins, int nbp,
+                         int precision, int64_t step) {
   const int mw = nbins <= 32 ? 1 : (nbins <= 64 ? 2 : 4);
   const size_t tsz = precision == SX_FP64 ? sizeof(double) : sizeof(float);
   const int next = (int)((step & 1) ^ 1);  // the buffers the next step reads
@@ -730,7 +731,7 @@ int sx_save(sx_ctx *c, const char *path) {
   if (c->marked) return fail(c, SX_ESTATE, "a grid update is pending (mark without apply)");
   SX_CUDA(c, cudaSetDevice(c->cfg.device));
   const sx::DevGrid &g = c->g;
-  const CkptRegions r = ckpt_regions(c->L, g.n, g.nnz, g.nbins, c->cfg.precision, c->step);
+  const CkptRegions r = ckpt_regions(c->L, g.n, g.nnz, g.nbins, g.nbp, c->cfg.precision, c->step);
   CkptHeader h{};
   std::memcpy(h.magic, kCkptMagic, 8);
   h.n = g.n;
@@ -763,6 +764,7 @@ int sx_save(sx_ctx *c, const char *path) {
   h.chem_fp32 = c->cfg.chem_fp32;
   h.alpha_A = c->cfg.alpha_A;
   h.has_ghosts = c->has_ghosts ? 1 : 0;
+  h.nbp = g.nbp;
   // written to path.tmp, synced and renamed over path: a save that fails
   // part-way leaves the previous file at path as it was
   const std::string tmp = std::string(path) + ".tmp";
@@ -820,7 +822,8 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   if (h.n < 1 || h.n >= ((int64_t)1 << 31) || h.nnz < 0 || h.nnz >= ((int64_t)1 << 31) ||
       h.nsrc < 0 || h.nsrc > sx::kMaxSources || h.step < 0 || (h.group != 0 && h.group != 2 && h.group != 4) ||
       h.max_degree < 0 || h.max_degree > SX_MAX_DEGREE || !(h.punit > 0.0) || (h.chem_fp32 != 0 && h.chem_fp32 != 1) ||
-      !(h.alpha_A == 0.0 || (h.alpha_A >= h.alpha_B && std::isfinite(h.alpha_A))))
+      !(h.alpha_A == 0.0 || (h.alpha_A >= h.alpha_B && std::isfinite(h.alpha_A))) ||
+      (h.nbp != sx::bin_stride_packed(h.nbins) && h.nbp != sx::bin_stride_aligned(h.nbins)))
     return fail(c, SX_EINVAL, "corrupt checkpoint header");
   std::vector<double> bins(3 * (size_t)h.nbins);
   std::vector<int32_t> srcv(h.nsrc);
@@ -834,7 +837,7 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   const size_t need = L.total + sizeof(double) * 3 * sx::kMaxBins + 256;
   if (workspace_bytes < 0 || (size_t)workspace_bytes < need)
     return fail(c, SX_ENOMEM, "workspace too small for the checkpoint's grid");
-  const CkptRegions r = ckpt_regions(L, h.n, h.nnz, h.nbins, h.precision, h.step);
+  const CkptRegions r = ckpt_regions(L, h.n, h.nnz, h.nbins, h.nbp, h.precision, h.step);
   if (r.bytes[0] != h.bytes_a || r.bytes[1] != h.bytes_p || r.bytes[2] != h.bytes_m ||
       r.bytes[3] != h.bytes_b || r.bytes[4] != h.bytes_col)
     return fail(c, SX_EINVAL, "checkpoint written by an incompatible layout");
@@ -860,7 +863,7 @@ int sx_restore(sx_ctx *c, const char *path, void *d_workspace, int64_t workspace
   g.n = h.n;
   g.nnz = h.nnz;
   g.nbins = h.nbins;
-  g.nbp = (h.nbins + 3) / 4 * 4;
+  g.nbp = h.nbp;
   g.mw = h.nbins <= 32 ? 1 : (h.nbins <= 64 ? 2 : 4);
   g.precision = h.precision;
   g.chem_fp32 = h.precision == SX_FP32_TRANSPORT && h.chem_fp32 ? 1 : 0;
@@ -947,7 +950,7 @@ int sx_set_photon_unit(sx_ctx *c, double unit) {
 
 int sx_halo_bytes(const sx_ctx *c, int64_t n_edges, int64_t n_rows, int64_t *bytes) {
   if (!c || !bytes || n_edges < 0 || n_rows < 0) return fail(const_cast<sx_ctx *>(c), SX_EINVAL, "bad arguments");
-  const int nbp = (c->cfg.nbins + 3) / 4 * 4;
+  const int nbp = c->loaded ? c->g.nbp : sx::bin_stride_packed(c->cfg.nbins);  // the live row stride
   const int mw = c->cfg.nbins <= 32 ? 1 : (c->cfg.nbins <= 64 ? 2 : 4);
   const size_t tsz = c->cfg.precision == SX_FP64 ? sizeof(double) : sizeof(float);
   *bytes = (int64_t)(sx::halo_rows_offset(n_edges, mw) + (size_t)n_rows * nbp * tsz);
@@ -1058,6 +1061,39 @@ int sx_get_variant(sx_ctx *c, int32_t *variant) {
   return SX_OK;
 }
 
+// The stored photons' row stride: the buffer the next step reads is moved to
+// the new stride (the other holds nothing the next step reads).
+static int set_stride(sx_ctx *c, int stride) {
+  if (stride == c->g.nbp) return SX_OK;
+  const int live = (int)((c->step & 1) ^ 1);
+  SX_CUDA(c, sx::launch_restride(c->g, live, stride, c->stream));
+  c->g.nbp = stride;
+  if (c->graph) {  // a captured graph holds the old stride
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  return SX_OK;
+}
+
+int sx_set_bin_stride(sx_ctx *c, int32_t stride) {
+  NvtxRange nvtx_range_("sx_set_bin_stride");
+  if (!c) return SX_EINVAL;
+  if (int rc = dct_only(c, "a launch variant")) return rc;
+  if (!c->loaded) return fail(c, SX_ESTATE, "no grid loaded");
+  if (c->marked) return fail(c, SX_ESTATE, "a grid update is pending (mark without apply)");
+  const int nb = c->cfg.nbins;
+  if (stride != sx::bin_stride_packed(nb) && stride != sx::bin_stride_aligned(nb))
+    return fail(c, SX_EINVAL, "stride must be nbins rounded up to 4 or to 8");
+  SX_CUDA(c, cudaSetDevice(c->cfg.device));
+  return set_stride(c, stride);
+}
+
+int sx_get_bin_stride(sx_ctx *c, int32_t *stride) {
+  if (!c || !stride) return SX_EINVAL;
+  *stride = c->loaded ? c->g.nbp : sx::bin_stride_packed(c->cfg.nbins);
+  return SX_OK;
+}
+
 int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scratch_bytes,
                 sx_tune_result *out) {
   NvtxRange nvtx_range_("sx_autotune");
@@ -1075,17 +1111,35 @@ int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scra
   ensure_punit(c, dt);
   const cudaStream_t st = c->stream;
   const int32_t before = c->g.group == 2 ? 2 : 4;
+  const int32_t stride0 = c->g.nbp;
   // the state: every device buffer of the grid, and the host counters
   SX_CUDA(c, cudaMemcpyAsync(scratch, c->ws_base, c->ws_used, cudaMemcpyDeviceToDevice, st));
   std::memset(out, 0, sizeof(*out));
-  const int32_t cand[2] = {4, 2};
+  // candidates: vertices per warp (4, 2) x row stride (bins rounded up to 4
+  // and to 8; one stride when they coincide)
+  const int nb = c->cfg.nbins;
+  const int32_t strides[2] = {sx::bin_stride_packed(nb), sx::bin_stride_aligned(nb)};
+  const int nstrides = strides[0] == strides[1] ? 1 : 2;
+  int32_t cand[SX_TUNE_MAX_CANDIDATES], cstride[SX_TUNE_MAX_CANDIDATES];
+  int ncand = 0;
+  for (int si = 0; si < nstrides; ++si)
+    for (int32_t gq : {4, 2}) {
+      cand[ncand] = gq;
+      cstride[ncand++] = strides[si];
+    }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SX_CUDA(c, cudaEventCreate(&e0));
   cudaError_t ce = cudaEventCreate(&e1);
   double best = 0.0;
-  int32_t pick = before;
-  for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+  int32_t pick = before, pick_stride = stride0;
+  for (int i = 0; i < ncand && ce == cudaSuccess; ++i) {
     c->g.group = cand[i];
+    // the candidate's stride, from the saved layout (stride0)
+    if (cstride[i] != stride0) {
+      ce = sx::launch_restride(c->g, (int)((c->step & 1) ^ 1), cstride[i], st);
+      if (ce != cudaSuccess) break;
+    }
+    c->g.nbp = cstride[i];
     // one untimed step (first launch of the variant), then the timed ones
     for (int32_t k = 0; k <= nsteps && ce == cudaSuccess; ++k) {
       if (k == 1) ce = cudaEventRecord(e0, st);
@@ -1099,19 +1153,23 @@ int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scra
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
     if (ce == cudaSuccess) {
       out->candidates[i] = cand[i];
+      out->strides[i] = cstride[i];
       out->ms_per_step[i] = (double)ms / nsteps;
       out->ncandidates = i + 1;
       if (i == 0 || out->ms_per_step[i] < best) {
         best = out->ms_per_step[i];
         pick = cand[i];
+        pick_stride = cstride[i];
       }
       ce = cudaMemcpyAsync(c->ws_base, scratch, c->ws_used, cudaMemcpyDeviceToDevice, st);
     }
+    c->g.nbp = stride0;  // the restored layout
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   c->g.group = before;
+  c->g.nbp = stride0;
   if (ce != cudaSuccess) {
     // put the state back in any case, then report
     cudaMemcpyAsync(c->ws_base, scratch, c->ws_used, cudaMemcpyDeviceToDevice, st);
@@ -1119,7 +1177,9 @@ int sx_autotune(sx_ctx *c, double dt, int32_t nsteps, void *scratch, size_t scra
     return cuda_fail(c, ce, "sx_autotune");
   }
   out->variant = pick;
-  return sx_set_variant(c, pick);
+  out->stride = pick_stride;
+  if (int rc = sx_set_variant(c, pick)) return rc;
+  return set_stride(c, pick_stride);
 }
 
 int sx_get_info(sx_ctx *c, sx_info *info) {

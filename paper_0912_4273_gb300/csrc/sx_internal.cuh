@@ -272,6 +272,13 @@ struct DevGrid {
   uint8_t *binv;        // 3 nnz: the in-edges whose set holds each out-slot, ascending
 };
 
+// Row strides (elements) of the stored photons: the bins rounded up to 4
+// ("packed") or to 8 ("aligned": rows of 32 bytes in FP32, 64 in FP64).  A
+// grid's workspace has room for the aligned stride; the live one is
+// DevGrid::nbp, one of the two (a launch variant the autotuner picks).
+__host__ __device__ inline int bin_stride_packed(int nbins) { return (nbins + 3) / 4 * 4; }
+__host__ __device__ inline int bin_stride_aligned(int nbins) { return (nbins + 7) / 8 * 8; }
+
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_dif, off_P0, off_P1, off_M0,
       off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget,
@@ -339,6 +346,10 @@ cudaError_t launch_row_totals(int precision, int64_t n, int nbins, int nbp, cons
 cudaError_t launch_sum_rows(int precision, int64_t n, int nbins, int nbp, const void *I,
                             double *part, int nblk, cudaStream_t st);
 cudaError_t launch_inflight(DevGrid &g, int64_t step, cudaStream_t st);
+// Move the stored photons of buffer `buf` from the row stride g.nbp to
+// `stride`, through the other buffer (whose contents the next step does not
+// read); g.nbp is left for the caller to set.
+cudaError_t launch_restride(DevGrid &g, int buf, int stride, cudaStream_t st);
 // ballistic straight sets of every in-edge (after the edge tables)
 cudaError_t launch_ballistic_tables(DevGrid &g, cudaStream_t st);
 // kappa's per-block sums (numerator, denominator) into g.kappa_part, from the

@@ -12,7 +12,7 @@ static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transport) {
   Layout L{};
-  const int nbp = (nbins + 3) / 4 * 4;
+  const int nbp = bin_stride_aligned(nbins);  // room for either row stride (bin_stride_*)
   const int mw = nbins <= 32 ? 1 : (nbins <= 64 ? 2 : 4);
   const size_t tsz = precision == 0 ? sizeof(double) : sizeof(float);
   L.nblocks = (n + kTile - 1) / kTile;

@@ -16,6 +16,8 @@
 //   k_carry            neutral fraction and photons of the survivors into
 //                      the new grid's state
 //   k_sum_rows         deterministic FP64 sum of a photon field
+#include <algorithm>
+
 #include "sx_internal.cuh"
 
 namespace sx {
@@ -313,6 +315,40 @@ cudaError_t launch_sum_rows(int precision, int64_t n, int nbins, int nbp, const 
   else
     k_sum_rows<float><<<nblk, 256, 0, st>>>(n, nbins, nbp, static_cast<const float *>(I), part);
   return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Row stride change of the stored photons (a launch variant): buffer `buf`
+// at stride g.nbp is copied, bins 0..nbins-1 of every row, into the other
+// buffer at the new stride, then back in one contiguous copy.
+// ----------------------------------------------------------------------------
+template <typename T>
+__global__ void k_restride(int64_t n, int nbins, int from, const T *__restrict__ src, int to,
+                           T *__restrict__ dst) {
+  const int64_t total = n * nbins;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = k / nbins;
+    const int b = (int)(k - v * nbins);
+    dst[v * to + b] = src[v * from + b];
+  }
+}
+
+cudaError_t launch_restride(DevGrid &g, int buf, int stride, cudaStream_t st) {
+  if (stride == g.nbp || g.n <= 0) return cudaSuccess;
+  const int64_t total = g.n * g.nbins;
+  const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 4096);
+  const size_t tsz = g.precision == 0 ? sizeof(double) : sizeof(float);
+  void *live = g.P[buf], *tmp = g.P[buf ^ 1];
+  if (g.precision == 0)
+    k_restride<double><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, static_cast<const double *>(live),
+                                               stride, static_cast<double *>(tmp));
+  else
+    k_restride<float><<<blocks, 256, 0, st>>>(g.n, g.nbins, g.nbp, static_cast<const float *>(live),
+                                              stride, static_cast<float *>(tmp));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(live, tmp, tsz * (size_t)stride * (size_t)g.n, cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace sx

@@ -65,7 +65,8 @@ class sx_remesh_result(C.Structure):
 class sx_tune_result(C.Structure):
     _fields_ = [("variant", C.c_int32), ("ncandidates", C.c_int32),
                 ("candidates", C.c_int32 * SX_TUNE_MAX_CANDIDATES),
-                ("ms_per_step", C.c_double * SX_TUNE_MAX_CANDIDATES)]
+                ("ms_per_step", C.c_double * SX_TUNE_MAX_CANDIDATES),
+                ("stride", C.c_int32), ("strides", C.c_int32 * SX_TUNE_MAX_CANDIDATES)]
 
 
 class sx_info(C.Structure):
@@ -102,6 +103,8 @@ _SIGS = [
     ("sx_checkpoint_verify", C.c_int, [C.c_char_p]),
     ("sx_set_variant", C.c_int, [C.c_void_p, C.c_int32]),
     ("sx_get_variant", C.c_int, [C.c_void_p, _P(C.c_int32)]),
+    ("sx_set_bin_stride", C.c_int, [C.c_void_p, C.c_int32]),
+    ("sx_get_bin_stride", C.c_int, [C.c_void_p, _P(C.c_int32)]),
     ("sx_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_size_t,
                               _P(sx_tune_result)]),
     ("sx_grid_update_mark", C.c_int, [C.c_void_p, C.c_double, C.c_double, _P(C.c_int32),
@@ -343,6 +346,16 @@ def sx_set_variant(ctx, variant: int):
 def sx_get_variant(ctx) -> int:
     v = C.c_int32()
     _check(ctx, lib().sx_get_variant(ctx, C.byref(v)))
+    return v.value
+
+
+def sx_set_bin_stride(ctx, stride: int):
+    _check(ctx, lib().sx_set_bin_stride(ctx, stride))
+
+
+def sx_get_bin_stride(ctx) -> int:
+    v = C.c_int32()
+    _check(ctx, lib().sx_get_bin_stride(ctx, C.byref(v)))
     return v.value
 
 
@@ -673,8 +686,17 @@ class Solver:
         finally:
             del scratch
         k = r.ncandidates
-        return dict(variant=r.variant, candidates=list(r.candidates[:k]),
-                    ms_per_step=list(r.ms_per_step[:k]))
+        return dict(variant=r.variant, stride=r.stride, candidates=list(r.candidates[:k]),
+                    strides=list(r.strides[:k]), ms_per_step=list(r.ms_per_step[:k]))
+
+    @property
+    def bin_stride(self) -> int:
+        """Row stride of the stored photons (nbins rounded up to 4 or 8)."""
+        return sx_get_bin_stride(self.ctx)
+
+    @bin_stride.setter
+    def bin_stride(self, v: int):
+        sx_set_bin_stride(self.ctx, int(v))
 
     @property
     def info(self) -> dict:

@@ -114,13 +114,16 @@ def test_thousand_steps(grid, oracle_setup):
         if t >= 2.4 * tr:
             assert abs(ratio - 1) < 0.02, (t / I.MYR_S, ratio)
     assert abs(fronts[-1][1] - 1) < 0.01, fronts
-    # the front position (half-ionised shell): within 1% of the analytic
-    # history (Eq. IFront_pos) at one recombination time, and at 500 Myr
-    # within 1% of the equilibrium profile's front (1.053 r_S, a soft edge)
-    # on the same history
+    # the front position (half-ionised shell) against the analytic history
+    # (Eq. IFront_pos) at one recombination time: photons move one edge per
+    # step, about 0.13 kpc per 0.5 Myr step on this grid, so the front lags
+    # by their travel time across the sphere (measured 3.8%; the paper's
+    # 0.05 Myr step closes it: test_front_at_the_papers_time_step); at 500
+    # Myr within 1% of the equilibrium profile's front (1.053 r_S, a soft
+    # edge) on the same history
     t, r = positions[0]
     assert abs(t / tr - 1) < 0.01
-    assert abs(r / O.ifront_radius(t, NDOT, NH, ALPHA) - 1) < 0.01, (t / tr, r / rs)
+    assert 0.95 < r / O.ifront_radius(t, NDOT, NH, ALPHA) < 1.0, (t / tr, r / rs)
     t, r = positions[-1]
     r_half = O.equilibrium_front(NDOT, NH, ALPHA, I.SIGMA_H)
     assert abs(r / (r_half * (1 - math.exp(-t / tr)) ** (1 / 3)) - 1) < 0.01, (t / tr, r / rs)
@@ -132,6 +135,24 @@ def test_thousand_steps(grid, oracle_setup):
     assert np.abs(y32 - s64.y).max() <= 1e-4
     assert abs(budget_residual(s64.budget)) <= 1e-10
     s64.close()
+
+
+def test_front_at_the_papers_time_step(grid, oracle_setup):
+    """With the paper's Test-1 time step (0.05 Myr, Sect. 5.1.2) the front
+    of the full grid (FP32 transport) is within 1% of the analytic history
+    (Eq. IFront_pos) at one recombination time."""
+    bins, _, ref = oracle_setup
+    tr = O.recombination_time(NH, ALPHA)
+    dt = 0.05 * I.MYR_S
+    steps = int(round(tr / dt))
+    s = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa).load(grid)
+    s.step(dt, steps)
+    rs = O.stromgren_radius(NDOT, NH, ALPHA)
+    r = O.ifront_position(s.y, grid.pos, grid.volume, grid.interior, grid.pos[grid.src_vertex[0]],
+                          1.4 * rs)
+    assert abs(budget_residual(s.budget)) <= 1e-5
+    s.close()
+    assert abs(r / O.ifront_radius(steps * dt, NDOT, NH, ALPHA) - 1) < 0.01, r / rs
 
 
 def test_combined_transport_full_size(grid, oracle_setup):

@@ -368,16 +368,20 @@ def test_autotune_leaves_the_state_and_keeps_a_variant(c0):
     s.step(DT, 50)
     y, b, ph, st = s.y, s.budget, s.photons(), s.info["step"]
     r = s.autotune(DT, 4)
-    assert r["variant"] in (2, 4) and sorted(r["candidates"]) == [2, 4]
+    # vertices per warp x row stride (42 bins: 44 or 48)
+    assert sorted(zip(r["candidates"], r["strides"])) == [(2, 44), (2, 48), (4, 44), (4, 48)]
+    assert r["variant"] in (2, 4) and r["stride"] in (44, 48)
     assert all(ms > 0 for ms in r["ms_per_step"])
-    assert r["ms_per_step"][r["candidates"].index(r["variant"])] == min(r["ms_per_step"])
-    assert s.variant == r["variant"]
+    k = list(zip(r["candidates"], r["strides"])).index((r["variant"], r["stride"]))
+    assert r["ms_per_step"][k] == min(r["ms_per_step"])
+    assert s.variant == r["variant"] and s.bin_stride == r["stride"]
     assert np.array_equal(s.y, y) and s.budget == b and np.array_equal(s.photons(), ph)
     assert s.info["step"] == st
     s.step(DT, 50)
     u = S.Solver(bins, precision=S.SX_FP32_TRANSPORT, seed=0, kappa=ref.kappa).load(prob)
     u.step(DT, 50)
     u.variant = r["variant"]
+    u.bin_stride = r["stride"]
     u.step(DT, 50)
     assert np.array_equal(s.y, u.y) and s.budget == u.budget
     y_ref, b_ref, _ = snaps[1]
@@ -388,3 +392,35 @@ def test_autotune_leaves_the_state_and_keeps_a_variant(c0):
     assert e.value.code == S.SX_EINVAL
     s.close()
     u.close()
+
+
+@pytest.mark.parametrize("nbins,strides", [(42, (44, 48)), (84, (84, 88)), (21, (24, 24))])
+@pytest.mark.parametrize("precision", [S.SX_FP64, S.SX_FP32_TRANSPORT])
+def test_bin_stride_changes_no_result(nbins, strides, precision, tmp_path):
+    """The row stride of the stored photons (bin packing) is a layout
+    choice: switching it mid-run, even twice, and across a checkpoint,
+    leaves every result bit for bit as it was."""
+    prob = I.stromgren_problem(3000, seed=4)
+    bins = I.fibonacci_bins(nbins)
+    a = S.Solver(bins, precision=precision, seed=2).load(prob)
+    b = S.Solver(bins, precision=precision, seed=2).load(prob)
+    assert a.bin_stride == strides[0]
+    a.step(DT, 17)
+    b.step(DT, 17)
+    b.bin_stride = strides[1]
+    assert b.bin_stride == strides[1]
+    a.step(DT, 20)
+    b.step(DT, 20)  # graphs, captured anew for the stride
+    assert np.array_equal(a.y, b.y) and a.budget == b.budget and np.array_equal(a.photons(), b.photons())
+    b.save(str(tmp_path / "s.ckpt"))
+    c = S.Solver(bins, precision=precision, seed=2).restore(str(tmp_path / "s.ckpt"))
+    assert c.bin_stride == strides[1]
+    b.bin_stride = strides[0]
+    for s in (a, b, c):
+        s.step(DT, 9)
+    for s in (b, c):
+        assert np.array_equal(a.y, s.y) and a.budget == s.budget
+    with pytest.raises(S.SimplexError):
+        a.bin_stride = strides[1] + 4
+    for s in (a, b, c):
+        s.close()
