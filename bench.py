@@ -53,10 +53,11 @@ WORKLOADS = {
 }
 
 # DRAM traffic of one k_step launch measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, the launch of step 300), valid only for the kernel
-# source it was taken on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "2eef7a061f5b79cf43abb99d798f8549935d5ede867458a77947c88eec8b7e94",
-               "bytes_per_launch": 1059.800e6 + 380.462e6, "workload": "c1"}
+# dram__bytes_write.sum, the launch of step 305 of the headline run: state
+# step 300, 5 warm-up steps), valid only for the kernel source it was taken
+# on.
+NCU_TRAFFIC = {"sx_step.cu_sha256": "3ba634773b3600e4cc0ba55a2f61b60db54b7e07887e26397c09eb6eb04dac71",
+               "bytes_per_launch": 1075.852e6 + 394.153e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
