@@ -434,17 +434,31 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         const int32_t src = __shfl_sync(0xffffffffu, my_src, k);
         const int gk = __shfl_sync(0xffffffffu, g, k);
         int r = j - ek;  // rank of the packet among edge k's bins
-        int bo = 0;
+        // the word holding the r-th set bit and the rank within it, then the
+        // bit by halving (a fixed cost, whatever the rank)
+        uint32_t m = 0u;
+        int base = 0, rr = 0;
 #pragma unroll
         for (int w = 0; w < MW; ++w) {
-          uint32_t m = __shfl_sync(0xffffffffu, my_m[w], k);
-          const int c = __popc(m);
+          const uint32_t mk = __shfl_sync(0xffffffffu, my_m[w], k);
+          const int c = __popc(mk);
           if (r >= 0 && r < c) {
-            for (int t = 0; t < r; ++t) m &= m - 1u;
-            bo = 32 * w + __ffs(m) - 1;
+            m = mk;
+            base = 32 * w;
+            rr = r;
           }
           r -= c;
         }
+        int pos = 0, c = __popc(m & 0xFFFFu);
+        if (rr >= c) { rr -= c; m >>= 16; pos += 16; }
+        c = __popc(m & 0xFFu);
+        if (rr >= c) { rr -= c; m >>= 8; pos += 8; }
+        c = __popc(m & 0xFu);
+        if (rr >= c) { rr -= c; m >>= 4; pos += 4; }
+        c = __popc(m & 0x3u);
+        if (rr >= c) { rr -= c; m >>= 2; pos += 2; }
+        if (rr >= (int)(m & 1u)) pos += 1;
+        const int bo = base + pos;
         int key = 0;
         T val = T(0);
         if (on && SX_INDEX_OK(bo < nbins, a.diag)) {
