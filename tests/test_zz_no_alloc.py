@@ -10,6 +10,7 @@ every other test has run.
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_0912_4273_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -34,6 +35,8 @@ def test_kappa_noalloc_matches_load_grid_twice(nbins):
     for _ in range(2):
         k = S.sx_kappa_noalloc(prob.n, prob.pos, prob.row_ptr, prob.col, prob.flags, bins)
         assert k == pytest.approx(k_ref, rel=KAPPA_RTOL)
+    # and the oracle's kappa (FP64 sums of the FP32 per-vertex ratios: 1e-5)
+    assert k == pytest.approx(O.OracleSim(prob, O.Params(nbins=nbins), bins).kappa, rel=1e-5)
     # a different grid in between, then the first again: no state leaks across calls
     small = I.stromgren_problem(1000, seed=5)
     s = S.Solver(bins).load(small)
