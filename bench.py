@@ -56,8 +56,8 @@ WORKLOADS = {
 # dram__bytes_write.sum, the launch of step 305 of the headline run: state
 # step 300, 5 warm-up steps), valid only for the kernel source it was taken
 # on.
-NCU_TRAFFIC = {"sx_step.cu_sha256": "3ba634773b3600e4cc0ba55a2f61b60db54b7e07887e26397c09eb6eb04dac71",
-               "bytes_per_launch": 1075.852e6 + 394.153e6, "workload": "c1", "chem_fp32": False}
+NCU_TRAFFIC = {"step_source_sha256": "2de918bffef89e64a2ba408286f3b1123f6398544020f5b929f2bb188dd50702",
+               "bytes_per_launch": 1076.116e6 + 406.405e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
@@ -196,8 +196,11 @@ def measured_peaks():
 
 
 def kernel_source_sha() -> str:
-    p = os.path.join(ROOT, "paper_0912_4273_gb300", "csrc", "sx_step.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+    """sha256 of the step kernel's sources (sx_step.cu, then sx_step_common.cuh)."""
+    h = hashlib.sha256()
+    for f in ("sx_step.cu", "sx_step_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_0912_4273_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def make_problem(wl: dict, seed: int):
@@ -270,7 +273,7 @@ def run_ours(args, wl, rank, world, local_rank):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     traffic = None
-    if (NCU_TRAFFIC["sx_step.cu_sha256"] == kernel_source_sha() and NCU_TRAFFIC["workload"] == args.config
+    if (NCU_TRAFFIC["step_source_sha256"] == kernel_source_sha() and NCU_TRAFFIC["workload"] == args.config
             and NCU_TRAFFIC.get("chem_fp32", False) == bool(args.chem_fp32)):
         traffic = NCU_TRAFFIC["bytes_per_launch"]
     budget = solver.budget
@@ -446,10 +449,35 @@ def run_reference(args, wl, rank, world):
 # ---------------------------------------------------------------------------
 # batched (many independent grids) and served (request stream) measurements
 # ---------------------------------------------------------------------------
-def _grid_pool(sizes, seed0=1000):
+def _build_problem(recipe: str, n: int, seed: int):
     from paper_0912_4273_gb300 import inputs as I
 
-    return {int(n): I.cached(I.stromgren_problem, int(n), seed=seed0 + i) for i, n in enumerate(sizes)}
+    return I.cached(getattr(I, recipe), n, seed=seed)
+
+
+def _build_problems(jobs):
+    """(recipe name, n, seed) -> Problem for every job, the triangulations on
+    up to 8 worker processes (spawned: they inherit no CUDA state), largest
+    first."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    workers = min(len(jobs), os.cpu_count() or 1, 8)
+    if workers <= 1:
+        return [_build_problem(*j) for j in jobs]
+    order = sorted(range(len(jobs)), key=lambda i: -jobs[i][1])
+    out = [None] * len(jobs)
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        futs = {ex.submit(_build_problem, *jobs[i]): i for i in order}
+        for f in cf.as_completed(futs):
+            out[futs[f]] = f.result()
+    return out
+
+
+def _grid_pool(sizes, seed0=1000, recipe="stromgren_problem"):
+    sizes = [int(n) for n in sizes]
+    probs = _build_problems([(recipe, n, seed0 + i) for i, n in enumerate(sizes)])
+    return dict(zip(sizes, probs))
 
 
 def _sized_problem(base, nH, rate, box_over_rs=2.5):
@@ -552,8 +580,11 @@ def run_served(args):
     rng = np.random.default_rng(args.seed)
     pool_sizes = np.unique(np.round(np.geomspace(1e4, args.serve_nmax, args.serve_pool)).astype(int))
     t_pool = time.perf_counter()
-    uni = _grid_pool(pool_sizes, seed0=2000)
-    clumpy = {int(n): I.cached(I.clumpy_problem, int(n), seed=3000 + i) for i, n in enumerate(pool_sizes)}
+    sizes = [int(n) for n in pool_sizes]
+    built = _build_problems([("stromgren_problem", n, 2000 + i) for i, n in enumerate(sizes)]
+                            + [("clumpy_problem", n, 3000 + i) for i, n in enumerate(sizes)])
+    uni = dict(zip(sizes, built[:len(sizes)]))
+    clumpy = dict(zip(sizes, built[len(sizes):]))
     t_pool = time.perf_counter() - t_pool
     t = 0.0
     reqs = []

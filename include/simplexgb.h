@@ -401,7 +401,10 @@ int sx_batch_create(int32_t max_grids, int32_t device, void *stream, void *d_wor
 /* Advance n loaded contexts by nsteps steps, context i with time step
    dt_s[i].  All contexts must share nbins, precision and device.  Work is
    queued on the batch stream after the contexts' pending work; the contexts'
-   streams wait for it before their next call.  Errors: SX_EINVAL (n out of
+   streams wait for it before their next call.  Per step, grids of fewer
+   than 8192 tiles (262,144 vertices) share one persistent launch; each
+   larger grid steps in a launch of its own, as sx_step would (results are
+   the same either way).  Errors: SX_EINVAL (n out of
    1..max_grids, mixed nbins/precision/device, dt <= 0), SX_ESTATE (a context
    without grid), SX_ECUDA. */
 int sx_batch_step(sx_batch *batch, sx_ctx *const *ctxs, int32_t n, const double *dt_s,

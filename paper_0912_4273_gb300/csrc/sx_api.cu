@@ -133,6 +133,10 @@ struct sx_batch {
   }
 };
 
+// Grids of at least this many tiles (32 vertices each) in a batch step in
+// launches of their own.
+constexpr int64_t kBatchAloneTiles = 8192;
+
 static size_t batch_bytes(int32_t max_grids) {
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
   return up(sizeof(sx::RotArgs) * max_grids) + up(sizeof(sx::StepArgs) * max_grids) +
@@ -1280,28 +1284,49 @@ int sx_batch_step(sx_batch *b, sx_ctx *const *ctxs, int32_t n, const double *dt_
   b->h_args.resize(n);
   b->h_prefix.resize(n + 1);
   b->h_prefix[0] = 0;
+  // Grids of many waves of tiles step in launches of their own (their
+  // arguments in the launch's constant bank, no work queue); the others
+  // share the persistent launch.
+  std::vector<int32_t> alone;
+  int32_t ns = 0;  // grids in the shared launch: h_args[0 .. ns-1]
+  const sx_ctx *cs = nullptr;
   for (int32_t i = 0; i < n; ++i) {
     sx_ctx *c = ctxs[i];
     ensure_punit(c, dt_s[i]);
     b->h_rot[i] = sx::make_rot_args(c->g, c->bins_dev, c->cfg.seed, 0, dt_s[i]);
-    b->h_args[i] = sx::make_step_args(c->g, dt_s[i], c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub);
-    b->h_prefix[i + 1] = b->h_prefix[i] + c->g.nblocks;
+    if (c->g.nblocks >= kBatchAloneTiles) {
+      alone.push_back(i);
+    } else {
+      if (!cs) cs = c;
+      b->h_args[ns] = sx::make_step_args(c->g, dt_s[i], c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub);
+      b->h_prefix[ns + 1] = b->h_prefix[ns] + c->g.nblocks;
+      ++ns;
+    }
     // the batch stream runs after the context's queued work
     SX_BCUDA(b, cudaEventRecord(b->ev, c->stream));
     SX_BCUDA(b, cudaStreamWaitEvent(b->stream, b->ev, 0));
   }
   SX_BCUDA(b, cudaMemcpyAsync(b->d_rot, b->h_rot.data(), sizeof(sx::RotArgs) * n, cudaMemcpyHostToDevice, b->stream));
-  SX_BCUDA(b, cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(sx::StepArgs) * n, cudaMemcpyHostToDevice, b->stream));
-  SX_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+  if (ns > 0) {
+    SX_BCUDA(b, cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(sx::StepArgs) * ns, cudaMemcpyHostToDevice, b->stream));
+    SX_BCUDA(b, cudaMemcpyAsync(b->d_prefix, b->h_prefix.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, b->stream));
+  }
   SX_BCUDA(b, cudaEventRecord(b->ev_copy, b->stream));
   b->copy_pending = true;
   for (int32_t k = 0; k < nsteps;) {  // the tables of up to kRotAhead steps, then their steps
     const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
     SX_BCUDA(b, sx::launch_rotation_batch(b->d_rot, n, m, b->stream));
-    for (int j = 0; j < m; ++j, ++k)
-      SX_BCUDA(b, sx::launch_step_batch(c0->cfg.precision, c0->g.group, b->d_args, b->d_prefix, n,
-                                        b->h_prefix[n], b->d_queue, c0->cfg.nbins, j, b->device,
-                                        b->stream));
+    for (int j = 0; j < m; ++j, ++k) {
+      if (ns > 0)
+        SX_BCUDA(b, sx::launch_step_batch(cs->cfg.precision, cs->g.group, b->d_args, b->d_prefix, ns,
+                                          b->h_prefix[ns], b->d_queue, cs->cfg.nbins, j, b->device,
+                                          b->stream));
+      for (const int32_t i : alone) {
+        sx_ctx *c = ctxs[i];
+        SX_BCUDA(b, sx::launch_step(c->g, j, dt_s[i], c->cfg.chem_frac, c->cfg.chem_tol, c->cfg.chem_max_sub,
+                                    b->stream));
+      }
+    }
   }
   SX_BCUDA(b, cudaEventRecord(b->ev, b->stream));
   for (int32_t i = 0; i < n; ++i) {

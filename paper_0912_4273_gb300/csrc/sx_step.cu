@@ -541,11 +541,19 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         __syncwarp();
       }
     }
-    if constexpr (sizeof(T) == 4) {  // fold the compensation words into the bins
+    if constexpr (sizeof(T) == 4) {  // fold the compensation words into the occupied bins
       __syncwarp();
-      for (int i = lane; i < kGroup * nbs; i += 32) {
-        const float c = gcomp[i];
-        if (c != 0.f) grow[i] = __fadd_rn(grow[i], c);
+      if (lane < kGroup * MW) {  // lane: mask word lane % MW of group vertex lane / MW
+        const int g = lane / MW, w = lane % MW;
+        uint32_t m = gocc[g][w];
+        T *row = grow + (size_t)g * nbs + 32 * w;
+        const T *crow = gcomp + (size_t)g * nbs + 32 * w;
+        while (m) {
+          const int i = __ffs(m) - 1;
+          m &= m - 1u;
+          const float c = crow[i];
+          if (c != 0.f) row[i] = __fadd_rn(row[i], c);
+        }
       }
     }
   }
@@ -951,6 +959,7 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
     k_step_batch(const StepArgs *__restrict__ args, const int64_t *__restrict__ prefix, int ngrids,
                  unsigned long long *__restrict__ queue, int slot, int grab) {
   __shared__ long long s_item;
+  __shared__ StepArgs s_args;  // the current grid's arguments
   const int64_t total = prefix[ngrids];
   int cur_grid = -1;
   for (;;) {
@@ -968,7 +977,14 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks)
         const int mid = (lo + hi + 1) >> 1;
         if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
       }
-      step_tile<T, MW, G>(args[lo], args[lo].tab + slot, t - prefix[lo], lo != cur_grid, true);
+      static_assert(sizeof(StepArgs) % 4 == 0, "StepArgs is copied in 4-byte words");
+      if (lo != cur_grid) {  // every thread is past the last tile's use of s_args
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(args + lo);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&s_args);
+        for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / 4); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+      }
+      step_tile<T, MW, G>(s_args, s_args.tab + slot, t - prefix[lo], lo != cur_grid, true);
       cur_grid = lo;
     }
   }
