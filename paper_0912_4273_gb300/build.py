@@ -17,8 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")  # -DSX_DEBUG: the kernels check their indices
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBNAME = "libsimplexgb.so"
-SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_update.cu", "sx_halo.cu", "sx_noalloc.cu",
-           "sx_remesh.cpp"]
+SOURCES = ["sx_api.cu", "sx_setup.cu", "sx_step.cu", "sx_ballistic.cu", "sx_update.cu", "sx_halo.cu",
+           "sx_noalloc.cu", "sx_remesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I", INCLUDE]

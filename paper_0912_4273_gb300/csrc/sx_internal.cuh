@@ -318,6 +318,9 @@ StepArgs make_step_args(DevGrid &g, double dt, double chem_frac, double chem_tol
 // persistent launch per step over the tiles of all grids (work queue), with
 // the tables in slot `slot` of each grid.  All grids share nbins and precision.
 cudaError_t launch_rotation_batch(const RotArgs *d_rot, int ngrids, int count, cudaStream_t st);
+// One step of ballistic transport alone (sx_ballistic.cu): ntiles CTAs of
+// kTile vertices; precision 0 = FP64.
+cudaError_t launch_step_ballistic(const StepArgs &a, int64_t ntiles, int precision, cudaStream_t st);
 cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, const int64_t *d_prefix,
                               int ngrids, int64_t total_tiles, unsigned long long *d_queue,
                               int nbins, int slot, int device, cudaStream_t st);

@@ -609,76 +609,12 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           else nin_acc = ff_add(nin_acc, row[32 * w + i]);
         }
       }
-      if constexpr (sizeof(T) == 8) {
-        const double nin = nin_acc;
-        if (c.flags & kFlagGhost) {
-          // another shard's vertex: stepped and counted there
-        } else if (c.flags & kFlagSink) {
-          bud_sink = nin;  // a sink passes nothing on
-        } else {
-          double yv = s_y[vl];
-          double d_new = 0.0;  // diffuse radiation: photons made in this step
-          if (nin == 0.0 && yv == 1.0) {
-            f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
-          } else if (a.diffuse) {
-            double rec = 0.0;
-            f = chem_cell<true>(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
-                                a.fc, a.tol, a.max_sub, nsub, capped, &rec);
-            a.y[v] = yv;
-            if (c.invA != 0.0) d_new = __dmul_rn(a.ground, __ddiv_rn(rec, c.invA)) / a.punit;
-          } else {
-            f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
-                          a.fc, a.tol, a.max_sub, nsub, capped);
-            a.y[v] = yv;
-          }
-          if (a.diffuse && d_new != s_D[vl]) a.dif[v] = d_new;
-          bud_abs = __dmul_rn(nin, __dsub_rn(1.0, f));
-          bud_tr = __dmul_rn(nin, f);
-        }
-      } else {
-        const FF nin = nin_acc;
-        if (c.flags & kFlagGhost) {
-          // another shard's vertex: stepped and counted there
-        } else if (c.flags & kFlagSink) {
-          bud_sink_ff = nin;  // a sink passes nothing on
-        } else {
-          double yv = s_y[vl];
-          float absf = 0.f;
-          double rec = 0.0;  // diffuse radiation: recombinations per atom in this step
-          if (nin.hi == 0.f && yv == 1.0) {
-            f = 1.f;  // no photons and nothing to recombine: the state is a fixed point
-          } else {
-            const double Fa = __dmul_rn(__dmul_rn(ff_to_double(nin), a.punit),
-                                        __dmul_rn(c.invA, a.inv_dt));
-            if (c.invA == 0.0) {
-              f = 1.f;  // no atoms: transparent, nothing to ionise
-            } else if (a.chem_fp32 && Fa < 1e30 && c.tau_max < 1e30 && c.R0 < 1e30 && a.dt < 1e30) {
-              float recf = 0.f;
-              f = chem_cell_f(yv, (float)Fa, (float)a.dt, (float)c.tau_max, (float)c.R0,
-                              (float)a.fc, (float)a.tol, a.max_sub, nsub, capped, absf, recf);
-              rec = recf;
-            } else {  // the FP64 subcycles (by default, and where rates leave the FP32 range)
-              double fd;
-              if (a.diffuse)
-                fd = chem_cell<true>(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
-                                     c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub,
-                                     capped, &rec);
-              else
-                fd = chem_cell(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
-                               c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub, capped);
-              f = (float)fd;
-              absf = (float)(1.0 - fd);
-            }
-            a.y[v] = yv;
-          }
-          if (a.diffuse) {
-            const double d_new = c.invA != 0.0 ? __dmul_rn(a.ground, rec / c.invA) / a.punit : 0.0;
-            if (d_new != s_D[vl]) a.dif[v] = d_new;
-          }
-          bud_abs_ff = ff_mul(nin, absf);
-          bud_tr_ff = ff_mul(nin, f);
-        }
-      }
+      if constexpr (sizeof(T) == 8)
+        f = vertex_chem<T>(a, c, v, s_y[vl], nin_acc, a.diffuse ? s_D[vl] : 0.0, nsub, capped,
+                           bud_abs, bud_sink, bud_tr);
+      else
+        f = vertex_chem<T>(a, c, v, s_y[vl], nin_acc, a.diffuse ? s_D[vl] : 0.0, nsub, capped,
+                           bud_abs_ff, bud_sink_ff, bud_tr_ff);
     }
     s_f[vl] = f;
     diag_nsub = (unsigned)nsub;
@@ -1116,6 +1052,7 @@ cudaError_t launch_step(DevGrid &g, int slot, double dt, double chem_frac, doubl
   if (slot < 0 || slot >= kRotAhead) return cudaErrorInvalidValue;
   StepArgs a = make_step_args(g, dt, chem_frac, chem_tol, chem_max_sub);
   a.tab = g.tabs + slot;
+  if (g.transport == kTransportBallistic) return launch_step_ballistic(a, g.nblocks, g.precision, st);
   if (g.transport != kTransportDct) return dispatch_bal(g.precision, g.nbins, BalLaunch{a, g.nblocks, g.nbins, st});
   return dispatch_step(g.precision, g.nbins, g.group, StepLaunch{a, g.nblocks, g.nbins, st});
 }

@@ -227,6 +227,96 @@ struct Bud<float> {
   }
 };
 
+// ----------------------------------------------------------------------------
+// The step of one vertex's cell from its N_in (stored units; an FP64 sum, or
+// float-float in FP32 mode), Sect. 4.5.  A ghost is another shard's vertex,
+// stepped and counted there: nothing here.  A sink absorbs N_in.  Any other
+// cell runs the subcycles (FP64; FP32 rates with chem_fp32) from its
+// neutral fraction y0, writes y, and with diffuse radiation its
+// ground-level recombination photons of the step (dif[v], only where they
+// changed from d_prev, the last step's).  Returns the transmitted fraction
+// f (0 for ghosts and sinks) and the budget terms: absorbed N_in (1 - f),
+// passed to a sink, transmitted N_in f.
+// ----------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T vertex_chem(const StepArgs &a, const VConst &c, int64_t v, double y0,
+                                         typename Bud<T>::type nin_acc, double d_prev, int &nsub,
+                                         int &capped, typename Bud<T>::type &babs,
+                                         typename Bud<T>::type &bsink, typename Bud<T>::type &btr) {
+  T f = T(0);
+  if constexpr (sizeof(T) == 8) {
+    const double nin = nin_acc;
+    if (c.flags & kFlagGhost) {
+      // another shard's vertex: stepped and counted there
+    } else if (c.flags & kFlagSink) {
+      bsink = nin;  // a sink passes nothing on
+    } else {
+      double yv = y0;
+      double d_new = 0.0;  // diffuse radiation: photons made in this step
+      if (nin == 0.0 && yv == 1.0) {
+        f = 1.0;  // no photons and nothing to recombine: the state is a fixed point
+      } else if (a.diffuse) {
+        double rec = 0.0;
+        f = chem_cell<true>(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
+                            a.fc, a.tol, a.max_sub, nsub, capped, &rec);
+        a.y[v] = yv;
+        if (c.invA != 0.0) d_new = __dmul_rn(a.ground, __ddiv_rn(rec, c.invA)) / a.punit;
+      } else {
+        f = chem_cell(yv, __dmul_rn(nin, a.punit), a.dt, a.inv_dt, c.invA, c.tau_max, c.R0,
+                      a.fc, a.tol, a.max_sub, nsub, capped);
+        a.y[v] = yv;
+      }
+      if (a.diffuse && d_new != d_prev) a.dif[v] = d_new;
+      babs = __dmul_rn(nin, __dsub_rn(1.0, f));
+      btr = __dmul_rn(nin, f);
+    }
+  } else {
+    const FF nin = nin_acc;
+    if (c.flags & kFlagGhost) {
+      // another shard's vertex: stepped and counted there
+    } else if (c.flags & kFlagSink) {
+      bsink = nin;  // a sink passes nothing on
+    } else {
+      double yv = y0;
+      float absf = 0.f;
+      double rec = 0.0;  // diffuse radiation: recombinations per atom in this step
+      if (nin.hi == 0.f && yv == 1.0) {
+        f = 1.f;  // no photons and nothing to recombine: the state is a fixed point
+      } else {
+        const double Fa = __dmul_rn(__dmul_rn(ff_to_double(nin), a.punit),
+                                    __dmul_rn(c.invA, a.inv_dt));
+        if (c.invA == 0.0) {
+          f = 1.f;  // no atoms: transparent, nothing to ionise
+        } else if (a.chem_fp32 && Fa < 1e30 && c.tau_max < 1e30 && c.R0 < 1e30 && a.dt < 1e30) {
+          float recf = 0.f;
+          f = chem_cell_f(yv, (float)Fa, (float)a.dt, (float)c.tau_max, (float)c.R0,
+                          (float)a.fc, (float)a.tol, a.max_sub, nsub, capped, absf, recf);
+          rec = recf;
+        } else {  // the FP64 subcycles (by default, and where rates leave the FP32 range)
+          double fd;
+          if (a.diffuse)
+            fd = chem_cell<true>(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
+                                 c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub,
+                                 capped, &rec);
+          else
+            fd = chem_cell(yv, __dmul_rn(ff_to_double(nin), a.punit), a.dt, a.inv_dt,
+                           c.invA, c.tau_max, c.R0, a.fc, a.tol, a.max_sub, nsub, capped);
+          f = (float)fd;
+          absf = (float)(1.0 - fd);
+        }
+        a.y[v] = yv;
+      }
+      if (a.diffuse) {
+        const double d_new = c.invA != 0.0 ? __dmul_rn(a.ground, rec / c.invA) / a.punit : 0.0;
+        if (d_new != d_prev) a.dif[v] = d_new;
+      }
+      babs = ff_mul(nin, absf);
+      btr = ff_mul(nin, f);
+    }
+  }
+  return f;
+}
+
 #ifndef SX_STEP_MIN_BLOCKS
 #define SX_STEP_MIN_BLOCKS 6  // resident CTAs per SM the register allocation aims for
 #endif

@@ -1,7 +1,9 @@
 """Ballistic and combined transport on the GPU (Sect. 2.2.2, 2.2.4) against
 the FP64 oracle, element by element: neutral fractions, photons in flight per
 vertex and the photon budget, through the same launches as direction-
-conserving transport (the step kernel with thick vertices)."""
+conserving transport (the step kernel with thick vertices); ballistic
+transport alone has a kernel of its own, which must step exactly as the
+combined kernel does when every vertex is thick."""
 import math
 
 import numpy as np
@@ -52,6 +54,26 @@ def test_parity_with_oracle(grid, nbins, transport, tau_switch, precision, ytol,
     if transport == COMB:
         assert 0 < thick.sum() < grid.n  # both modes present
     s.close()
+
+
+@pytest.mark.parametrize("precision", [S.SX_FP64, S.SX_FP32_TRANSPORT])
+def test_ballistic_kernel_is_combined_with_every_vertex_thick(grid, precision):
+    """tau_switch = 0 makes every cell thick (y tau_max >= 0), so the combined
+    kernel's ballistic tiles run the same step as the ballistic kernel:
+    neutral fractions and photons in flight bit for bit; the budget to
+    rounding (a sink sums what reaches it in another order)."""
+    bins = I.fibonacci_bins(84)
+    out = []
+    for tp in (BAL, COMB):
+        s = S.Solver(bins, precision=precision, seed=4, transport=tp, tau_switch=0.0).load(grid)
+        for steps in (1, 16, 23):
+            s.step(DT, steps)
+            out.append((tp, s.y, s.photons(), s.budget))
+        s.close()
+    for (_, y0, p0, b0), (_, y1, p1, b1) in zip(out[:3], out[3:]):
+        assert np.array_equal(y0, y1)
+        assert np.array_equal(p0, p1)
+        assert _budget_err(b0, b1) <= 1e-12
 
 
 def test_combined_with_infinite_switch_is_the_direction_conserving_kernel(grid):
