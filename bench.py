@@ -775,8 +775,9 @@ def run_clumpy(args):
     (independent set), the cavities of the removed vertices re-triangulated
     on the host and the state carried over.  Reports the step kernel's throughput (per-launch CUDA
     events) and the cost of each update: marking on the device, local
-    re-triangulation on the host (scipy Qhull per cavity), loading the new
-    grid with the hand-over on the device."""
+    re-triangulation on the host (the library's native Bowyer-Watson per
+    cavity, sx_remesh_remove), loading the new grid with the hand-over on
+    the device."""
     import torch
 
     from paper_0912_4273_gb300 import inputs as I
