@@ -45,6 +45,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transpo
   L.off_kpart = take(sizeof(double) * 2 * L.nblocks_kappa);
   L.off_kappa = take(sizeof(double));
   L.off_budget = take(sizeof(double) * 8);
+  L.off_bsum = take(sizeof(double) * 4 * kBudgetBlocks);
   L.off_s_row_ptr = take(sizeof(int64_t) * (n + 1));
   L.off_s_col = take(sizeof(int32_t) * nnz);
   L.off_s_nH = take(sizeof(double) * n);
@@ -92,6 +93,7 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.nblocks_kappa = L.nblocks_kappa;
   g.kappa_dev = reinterpret_cast<double *>(b + L.off_kappa);
   g.budget_dev = reinterpret_cast<double *>(b + L.off_budget);
+  g.bsum = reinterpret_cast<double *>(b + L.off_bsum);
   g.s_row_ptr = reinterpret_cast<int64_t *>(b + L.off_s_row_ptr);
   g.s_col = reinterpret_cast<int32_t *>(b + L.off_s_col);
   g.s_nH = reinterpret_cast<double *>(b + L.off_s_nH);
