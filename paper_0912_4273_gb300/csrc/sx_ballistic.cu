@@ -64,6 +64,9 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
   __shared__ __align__(16) VConst s_vc[kTile];
   __shared__ __align__(16) double s_y[kTile];
   __shared__ double s_D[kTile];
+  // the tile's running budget terms (absorbed, escaped, -, diffuse emitted),
+  // fetched in the prologue so that the end of the tile does not wait on them
+  __shared__ __align__(16) double s_run[4];
   __shared__ int32_t s_R[kWarps][kGroup + 1];
   __shared__ BT s_bud[3][kTile];
   __shared__ BT s_esc[kWarps];
@@ -77,6 +80,8 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
     for (int i = lane; i < 2 * nv; i += 32)
       cp_async16(reinterpret_cast<char *>(s_vc) + 16 * i, reinterpret_cast<const char *>(a.vc + v0) + 16 * i);
     if (lane < nv) cp_async8(s_y + lane, a.y + v0 + lane);
+    if (lane == 0) cp_async16(s_run, a.partials + 4 * tile);
+    if (lane == 1) cp_async16(s_run + 2, a.partials + 4 * tile + 2);
     cp_async_commit();
   }
   const int g0 = warp * kGroup;
@@ -245,10 +250,10 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
       BT neg;
       if constexpr (sizeof(T) == 8) neg = -e3; else neg = FF{-e3.hi, -e3.lo};
       double *p = a.partials + 4 * tile;
-      p[0] += B::to_double(sum_abs);
-      p[1] += B::to_double(B::add(sum_esc, e3));
+      p[0] = s_run[0] + B::to_double(sum_abs);
+      p[1] = s_run[1] + B::to_double(B::add(sum_esc, e3));
       p[2] = B::to_double(B::add(sum_tr, neg));  // in flight after this step
-      if (a.diffuse) p[3] += B::to_double(sum_dif);  // diffuse photons emitted
+      if (a.diffuse) p[3] = s_run[3] + B::to_double(sum_dif);  // diffuse photons emitted
     }
   }
 }

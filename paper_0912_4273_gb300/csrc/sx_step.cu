@@ -249,6 +249,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // diffuse radiation: the photons each tile vertex emits in this step (made
   // in the last one), for the budget
   __shared__ double s_D[kTile];
+  // the tile's running budget terms (absorbed, escaped, -, diffuse emitted),
+  // fetched in the prologue so that the end of the tile does not wait on them
+  __shared__ __align__(16) double s_run[4];
   // each warp's sum of the photons its pairs let escape in phase 3, and the
   // chemistry lanes' absorbed, sink-bound and transmitted photons (kept here
   // through phase 3)
@@ -290,6 +293,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
     for (int i = lane; i < 2 * nv; i += 32)
       cp_async16(reinterpret_cast<char *>(s_vc) + 16 * i, reinterpret_cast<const char *>(a.vc + v0) + 16 * i);
     if (lane < nv) cp_async8(s_y + lane, a.y + v0 + lane);
+    if (lane == 0) cp_async16(s_run, a.partials + 4 * tile);
+    if (lane == 1) cp_async16(s_run + 2, a.partials + 4 * tile + 2);
     cp_async_commit();
   }
   const int g0 = warp * kGroup;          // first tile vertex of the warp's group
@@ -334,9 +339,6 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       s_S[g0 + lane] = T(0);
     }
   }
-  // the tile's running budget (escaped, absorbed), read now so that the load
-  // overlaps the tile, by the lanes that write it back
-
   if (reload) __syncthreads(); else __syncwarp();  // the rest of the prologue is the warp's own
 
   const int cur = (int)(s_step & 1);
@@ -861,10 +863,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       BT neg;
       if constexpr (sizeof(T) == 8) neg = -e3; else neg = FF{-e3.hi, -e3.lo};
       double *p = a.partials + 4 * tile;
-      p[0] += B::to_double(sum_abs);
-      p[1] += B::to_double(B::add(sum_esc, e3));
+      p[0] = s_run[0] + B::to_double(sum_abs);
+      p[1] = s_run[1] + B::to_double(B::add(sum_esc, e3));
       p[2] = B::to_double(B::add(sum_tr, neg));  // in flight after this step
-      if (a.diffuse) p[3] += B::to_double(sum_dif);  // diffuse photons emitted
+      if (a.diffuse) p[3] = s_run[3] + B::to_double(sum_dif);  // diffuse photons emitted
     }
   }
   if (more) __syncthreads();  // shared state is reused by the next tile of a persistent CTA
