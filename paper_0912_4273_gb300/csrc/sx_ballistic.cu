@@ -70,6 +70,7 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
   __shared__ int32_t s_R[kWarps][kGroup + 1];
   __shared__ BT s_bud[3][kTile];
   __shared__ BT s_esc[kWarps];
+  __shared__ BT s_sum[4];  // the tile's sums of s_bud and of s_D
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int cw = 0;  // the chemistry warp (lane per tile vertex)
@@ -227,20 +228,26 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
     if constexpr (sizeof(T) == 8) nz = e != 0.0; else nz = e.hi != 0.f;
     if (__any_sync(0xffffffffu, nz)) e = B::warp_sum(e); else e = BT{};
     if (lane == 0) s_esc[warp] = e;
-    BT sum_tr{}, sum_esc{}, sum_abs{}, sum_dif{};
-    if (warp == cw) {
-      sum_abs = B::warp_sum(s_bud[0][lane]);
-      sum_esc = B::warp_sum(s_bud[1][lane]);
-      sum_tr = B::warp_sum(s_bud[2][lane]);
-      if (a.diffuse) {
-        const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
-        if constexpr (sizeof(T) == 8) {
-          sum_dif = B::warp_sum(d);
-        } else {  // the photons emitted, as double: hi + lo in float-float
-          const float hi = (float)d;
-          sum_dif = B::warp_sum(FF{hi, (float)(d - (double)hi)});
-        }
+    // the chemistry lanes' three terms summed by warps 1..3 at once (warp 0
+    // when the tile has fewer warps), the diffuse photons by warp 4 (or 0)
+    auto term_warp = [](int k) { return kWarps > 3 ? k + 1 : 0; };
+    constexpr int wd = kWarps > 4 ? 4 : 0;
+    for (int k = 0; k < 3; ++k) {
+      if (warp == term_warp(k)) {
+        const BT t = B::warp_sum(s_bud[k][lane]);
+        if (lane == 0) s_sum[k] = t;
       }
+    }
+    if (warp == wd && a.diffuse) {
+      const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
+      BT t;
+      if constexpr (sizeof(T) == 8) {
+        t = B::warp_sum(d);
+      } else {  // the photons emitted, as double: hi + lo in float-float
+        const float hi = (float)d;
+        t = B::warp_sum(FF{hi, (float)(d - (double)hi)});
+      }
+      if (lane == 0) s_sum[3] = t;
     }
     __syncthreads();
     if (warp == cw && lane == 0) {
@@ -250,10 +257,10 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
       BT neg;
       if constexpr (sizeof(T) == 8) neg = -e3; else neg = FF{-e3.hi, -e3.lo};
       double *p = a.partials + 4 * tile;
-      p[0] = s_run[0] + B::to_double(sum_abs);
-      p[1] = s_run[1] + B::to_double(B::add(sum_esc, e3));
-      p[2] = B::to_double(B::add(sum_tr, neg));  // in flight after this step
-      if (a.diffuse) p[3] = s_run[3] + B::to_double(sum_dif);  // diffuse photons emitted
+      p[0] = s_run[0] + B::to_double(s_sum[0]);
+      p[1] = s_run[1] + B::to_double(B::add(s_sum[1], e3));
+      p[2] = B::to_double(B::add(s_sum[2], neg));  // in flight after this step
+      if (a.diffuse) p[3] = s_run[3] + B::to_double(s_sum[3]);  // diffuse photons emitted
     }
   }
 }

@@ -257,6 +257,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   // through phase 3)
   __shared__ typename Bud<T>::type s_esc[kWarps];
   __shared__ typename Bud<T>::type s_bud[3][kTile];
+  __shared__ typename Bud<T>::type s_sum[4];  // the tile's sums of s_bud and of s_D
   // BAL: thick vertices' photons per in-edge and their sources' photons of
   // the step, and every tile vertex's mode (one element each without BAL)
   __shared__ T s_E[BAL ? kTile : 1][BAL ? kMaxDeg : 1];
@@ -840,20 +841,23 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       if (__any_sync(0xffffffffu, nz)) e = B::warp_sum(e); else e = BT{};
       if (lane == 0) s_esc[warp] = e;
     }
-    BT sum_tr{}, sum_esc{}, sum_abs{}, sum_dif{};
-    if (warp == cw) {
-      sum_abs = B::warp_sum(s_bud[0][lane]);
-      sum_esc = B::warp_sum(s_bud[1][lane]);
-      sum_tr = B::warp_sum(s_bud[2][lane]);
+    // the chemistry lanes' three terms summed by warps 1..3 at once, the
+    // diffuse photons by warp 4 (warp 0 with 4 warps)
+    constexpr int wd = kWarps > 4 ? 4 : 0;
+    if (warp >= 1 && warp <= 3) {
+      const BT t = B::warp_sum(s_bud[warp - 1][lane]);
+      if (lane == 0) s_sum[warp - 1] = t;
+    }
+    if (warp == wd && a.diffuse) {
+      BT t;
       if constexpr (sizeof(T) == 8) {
-        if (a.diffuse) sum_dif = B::warp_sum(v0 + lane < a.n ? s_D[lane] : 0.0);
-      } else {
-        if (a.diffuse) {  // the photons emitted, as double: hi + lo in float-float
-          const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
-          const float hi = (float)d;
-          sum_dif = B::warp_sum(FF{hi, (float)(d - (double)hi)});
-        }
+        t = B::warp_sum(v0 + lane < a.n ? s_D[lane] : 0.0);
+      } else {  // the photons emitted, as double: hi + lo in float-float
+        const double d = v0 + lane < a.n ? s_D[lane] : 0.0;
+        const float hi = (float)d;
+        t = B::warp_sum(FF{hi, (float)(d - (double)hi)});
       }
+      if (lane == 0) s_sum[3] = t;
     }
     __syncthreads();
     if (warp == cw && lane == 0) {
@@ -863,10 +867,10 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
       BT neg;
       if constexpr (sizeof(T) == 8) neg = -e3; else neg = FF{-e3.hi, -e3.lo};
       double *p = a.partials + 4 * tile;
-      p[0] = s_run[0] + B::to_double(sum_abs);
-      p[1] = s_run[1] + B::to_double(B::add(sum_esc, e3));
-      p[2] = B::to_double(B::add(sum_tr, neg));  // in flight after this step
-      if (a.diffuse) p[3] = s_run[3] + B::to_double(sum_dif);  // diffuse photons emitted
+      p[0] = s_run[0] + B::to_double(s_sum[0]);
+      p[1] = s_run[1] + B::to_double(B::add(s_sum[1], e3));
+      p[2] = B::to_double(B::add(s_sum[2], neg));  // in flight after this step
+      if (a.diffuse) p[3] = s_run[3] + B::to_double(s_sum[3]);  // diffuse photons emitted
     }
   }
   if (more) __syncthreads();  // shared state is reused by the next tile of a persistent CTA
