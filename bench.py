@@ -56,8 +56,8 @@ WORKLOADS = {
 # dram__bytes_write.sum, the launch of step 305 of the headline run: state
 # step 300, 5 warm-up steps), valid only for the kernel source it was taken
 # on.
-NCU_TRAFFIC = {"step_source_sha256": "14c04fb304e76595f71a749c9efd090113a41da528b4b4506e3f9046477f8f10",
-               "bytes_per_launch": 1075.794e6 + 391.749e6, "workload": "c1", "chem_fp32": False}
+NCU_TRAFFIC = {"step_source_sha256": "a2a132113152e235f932d89d120ce1f1b4afd95813b5ec5522edf573da2e08ae",
+               "bytes_per_launch": 1075.452e6 + 391.867e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
