@@ -568,10 +568,10 @@ def run_served(args):
     geometries (a fresh triangulation per request would take minutes at
     4e6 points); each request draws its own size (nearest pooled one),
     source rates, bins, steps and rotation seed.  Continuous batching (the
-    server, default fill target, and with every resident grid in every
-    chunk) against one request at a time on the plain path (sx_step with
-    graphs); the results of every request are compared bit for bit across
-    the policies."""
+    server with every resident grid in every chunk, the headline, and with
+    the least-remaining-work fill target of --serve-fills) against one
+    request at a time on the plain path (sx_step with graphs); the results
+    of every request are compared bit for bit across the policies."""
     import torch
 
     from paper_0912_4273_gb300 import inputs as I
@@ -902,7 +902,7 @@ def main(argv=None):
     ap.add_argument("--serve-nmax", type=float, default=4e6)
     ap.add_argument("--serve-steps-max", type=int, default=1000)
     ap.add_argument("--chunk", type=int, default=8)
-    ap.add_argument("--serve-fills", default="131072,none",
+    ap.add_argument("--serve-fills", default="none,131072",
                     help="served: fill targets in vertices to run (the first is the headline; "
                          "none = every resident grid in every chunk)")
     ap.add_argument("--max-wait", type=float, default=None,
