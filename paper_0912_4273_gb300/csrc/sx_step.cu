@@ -387,26 +387,51 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         if constexpr (BAL) {
           if (pure_bal || a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
           else load_mask<MW>(M_prev, (int64_t)e, my_m);
-          if (s_thick[g0 + g]) {
-            // a thick receiver keeps the edge's photons together: the
-            // sender's bins ascending, then the edge packet
-            CSum<T> acc;
-#pragma unroll
-            for (int w = 0; w < MW; ++w) {
-              uint32_t m = my_m[w];
-              while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1u;
-                acc.add(Pp[(size_t)my_src * nbp + 32 * w + i]);
-              }
-              my_m[w] = 0u;
-            }
-            acc.add(edge_val);
-            if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc.value();
-            edge_val = T(0);
-          }
         } else {
           load_mask<MW>(M_prev, (int64_t)e, my_m);
+        }
+      }
+      if constexpr (BAL) {
+        // A thick receiver keeps the edge's photons together: the bins its
+        // thin sender routed along the edge, summed by the whole warp one
+        // edge at a time (lanes over the bins, a fixed tree), then the edge
+        // packet.
+        const bool thick_recv = e < R[kGroup] && s_thick[g0 + g];
+        uint32_t any_m = 0u;
+#pragma unroll
+        for (int w = 0; w < MW; ++w) any_m |= my_m[w];
+        uint32_t todo = __ballot_sync(0xffffffffu, thick_recv && any_m != 0u);
+        T binsum = T(0);
+        while (todo) {
+          const int l = __ffs(todo) - 1;
+          todo &= todo - 1u;
+          const int32_t sl = __shfl_sync(0xffffffffu, my_src, l);
+          typename Bud<T>::type part{};
+#pragma unroll
+          for (int w = 0; w < MW; ++w) {
+            const uint32_t ml = __shfl_sync(0xffffffffu, my_m[w], l);
+            if ((ml >> lane) & 1u) {
+              const T x = Pp[(size_t)sl * nbp + 32 * w + lane];
+              if constexpr (sizeof(T) == 8) part = __dadd_rn(part, x); else part = ff_add(part, x);
+            }
+          }
+          part = Bud<T>::warp_sum(part);  // lane 0
+          T tot;
+          if constexpr (sizeof(T) == 8) {
+            tot = __shfl_sync(0xffffffffu, part, 0);
+          } else {
+            tot = __fadd_rn(__shfl_sync(0xffffffffu, part.hi, 0), __shfl_sync(0xffffffffu, part.lo, 0));
+          }
+          if (lane == l) binsum = tot;
+        }
+        if (thick_recv) {
+          CSum<T> acc;
+          acc.add(binsum);
+          acc.add(edge_val);
+          if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc.value();
+          edge_val = T(0);
+#pragma unroll
+          for (int w = 0; w < MW; ++w) my_m[w] = 0u;
         }
       }
       int cnt = 0;
@@ -475,22 +500,28 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
         // to the direction they travelled (the edge to the sender reversed),
         // ties -> lowest bin
         const bool on = edge_val != T(0);
-        int key = 0;
-        if (on) {
-          const char4 q = a.edges[e].q;
-          const int nq = (int)(unsigned char)(-q.x) | ((int)(unsigned char)(-q.y) << 8) |
-                         ((int)(unsigned char)(-q.z) << 16);
-          int best = 0, bestd = __dp4a((int)s_qbq[0], nq, 0);
-          for (int b = 1; b < nbins; ++b) {
-            const int d = __dp4a((int)s_qbq[b], nq, 0);
-            if (d > bestd) {
-              best = b;
-              bestd = d;
-            }
+        uint32_t need = __ballot_sync(0xffffffffu, on);
+        if (need) {
+          int nq = 0;
+          if (on) {
+            const char4 q = a.edges[e].q;
+            nq = (int)(unsigned char)(-q.x) | ((int)(unsigned char)(-q.y) << 8) |
+                 ((int)(unsigned char)(-q.z) << 16);
           }
-          key = (g << 7) | best;
+          // one packet at a time, lanes over the bins: key dot * 128 +
+          // (127 - bin), largest for the largest dot and then the lowest bin
+          int best = 0;
+          while (need) {
+            const int l = __ffs(need) - 1;
+            need &= need - 1u;
+            const int nql = __shfl_sync(0xffffffffu, nq, l);
+            int bk = INT_MIN;
+            for (int b = lane; b < nbins; b += 32) bk = max(bk, __dp4a((int)s_qbq[b], nql, 0) * 128 + (127 - b));
+            bk = __reduce_max_sync(0xffffffffu, bk);
+            if (lane == l) best = 127 - (bk & 127);
+          }
+          add_round<T, MW>(grow, gcomp, nbs, gocc, on, on ? ((g << 7) | best) : 0, edge_val, lt_mask);
         }
-        add_round<T, MW>(grow, gcomp, nbs, gocc, on, key, edge_val, lt_mask);
       }
     }
     // a source puts its share in every bin (BAL: a thick source keeps its
