@@ -56,8 +56,8 @@ WORKLOADS = {
 # dram__bytes_write.sum, the launch of step 305 of the headline run: state
 # step 300, 5 warm-up steps), valid only for the kernel source it was taken
 # on.
-NCU_TRAFFIC = {"step_source_sha256": "a2a132113152e235f932d89d120ce1f1b4afd95813b5ec5522edf573da2e08ae",
-               "bytes_per_launch": 1075.452e6 + 391.867e6, "workload": "c1", "chem_fp32": False}
+NCU_TRAFFIC = {"step_source_sha256": "d35e3cb4c4d9ed35eb4cfe9681eeee57997a4fa962215c062037112638749e5d",
+               "bytes_per_launch": 1075.504e6 + 391.475e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
