@@ -29,6 +29,10 @@
 #include "sx_internal.cuh"
 #include "sx_step_common.cuh"  // chemistry, mask words, budget sums, packet rounds
 
+#ifndef SX_COMBINED_MIN_BLOCKS
+#define SX_COMBINED_MIN_BLOCKS 6  // resident CTAs per SM the combined kernel's registers aim for
+#endif
+
 namespace sx {
 
 // ----------------------------------------------------------------------------
@@ -260,7 +264,11 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   __shared__ typename Bud<T>::type s_sum[4];  // the tile's sums of s_bud and of s_D
   // BAL: thick vertices' photons per in-edge and their sources' photons of
   // the step, and every tile vertex's mode (one element each without BAL)
-  __shared__ T s_E[BAL ? kTile : 1][BAL ? kMaxDeg : 1];
+  // With 65 or more bins a thick vertex's packets per in-edge sit in its own
+  // bin row, which it does not use (it keeps no bins); with fewer bins the
+  // row is shorter than kMaxDeg and they get rows of their own.
+  constexpr bool kEAlias = BAL && MW >= 3;
+  __shared__ T s_E[(BAL && !kEAlias) ? kTile : 1][(BAL && !kEAlias) ? kMaxDeg : 1];
   __shared__ T s_S[BAL ? kTile : 1];
   __shared__ unsigned char s_thick[BAL ? kTile : 1];
   // Per-warp scratch: phase 1 (the packet list), then, after the barrier,
@@ -276,6 +284,9 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
   constexpr int cw = 0;
   static_assert(kTile == 32 && kWarps >= 4, "one chemistry warp of 32 lanes, among >= 4 warps");
   const int nbins = a.nbins, nbp = a.nbp, nbs = tile_stride(nbins);
+  auto erow = [&](int v) -> T * {  // a thick vertex's packets per in-edge
+    if constexpr (kEAlias) return s_I + (size_t)v * nbs; else return s_E[v];
+  };
   const uint32_t lt_mask = (1u << lane) - 1u;
   if (reload) {  // this step's tables (a CTA keeps them from tile to tile of one grid)
     for (int b = tid; b < kMaxBins; b += kThreads) {
@@ -428,7 +439,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           CSum<T> acc;
           acc.add(binsum);
           acc.add(edge_val);
-          if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = acc.value();
+          if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) erow(g0 + g)[e - R[g]] = acc.value();
           edge_val = T(0);
 #pragma unroll
           for (int w = 0; w < MW; ++w) my_m[w] = 0u;
@@ -620,7 +631,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           const int gw = vl / kGroup, gi = vl % kGroup;
           const int dg = s_R[gw][gi + 1] - s_R[gw][gi];
           for (int j = 0; j <= dg; ++j) {
-            const T x = j < dg ? s_E[vl][j] : s_S[vl];
+            const T x = j < dg ? erow(vl)[j] : s_S[vl];
             if constexpr (sizeof(T) == 8) nin_acc = __dadd_rn(nin_acc, x);
             else nin_acc = ff_add(nin_acc, x);
           }
@@ -804,7 +815,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
 #pragma unroll
         for (int q = 1; q < kGroup; ++q) g += (e >= s_R[warp][q]) ? 1 : 0;
         if (s_thick[g0 + g]) {
-          T &E = s_E[g0 + g][e - s_R[warp][g]];
+          T &E = erow(g0 + g)[e - s_R[warp][g]];
           const T o = E * s_f[g0 + g];
           const int cnt = (int)(a.stb[e] >> 24);
           if (cnt == 0) {
@@ -831,7 +842,7 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           const int dg = s_R[warp][g + 1] - r0;
           const unsigned ent = a.bpos[e];
           const uint8_t *lst = a.binv + 3 * (int64_t)r0 + (ent & 0xFFu);
-          const T *Eg = s_E[g0 + g];
+          const T *Eg = erow(g0 + g);
           CSum<T> acc;
           for (unsigned i = 0; i < (ent >> 8); ++i)
             if (SX_INDEX_OK(lst[i] < dg, a.diag)) acc.add(Eg[lst[i]]);
@@ -914,12 +925,13 @@ __global__ void __launch_bounds__(Shape<G>::kThreads, Shape<G>::kMinBlocks) k_st
   step_tile<T, MW, G>(a, a.tab, blockIdx.x, true, false);
 }
 
-// Ballistic and combined transport: the same tiles with thick vertices (4
-// vertices per warp), at 5 CTAs/SM (51 registers: a few bytes spill, and the
-// extra resident warps hide more of the dependent loads than 4 CTAs/SM at 64
-// registers do).
+// Combined transport: the same tiles with thick vertices (4 vertices per
+// warp), at 6 CTAs/SM and 40 registers (with 65 or more bins the thick
+// vertices' in-edge packets share the bin rows, so 6 tiles fit in shared
+// memory; the extra resident warps hide more of the dependent loads than
+// 5 CTAs/SM at 48 registers do).
 template <typename T, int MW>
-__global__ void __launch_bounds__(Shape<4>::kThreads, 5) k_step_bal(const StepArgs a) {
+__global__ void __launch_bounds__(Shape<4>::kThreads, SX_COMBINED_MIN_BLOCKS) k_step_bal(const StepArgs a) {
   step_tile<T, MW, 4, true>(a, a.tab, blockIdx.x, true, false);
 }
 
