@@ -107,8 +107,15 @@ __device__ __forceinline__ void ballistic_tile(const StepArgs &a, int64_t tile) 
     if ((thick >> g) & 1u) {
       const T x = Bp[e];
       if (SX_INDEX_OK(e - R[g] < kMaxDeg, a.diag)) s_E[g0 + g][e - R[g]] = x;
+      // phase C's tables of this edge, on their way to L1 while the
+      // chemistry runs
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.stb + e));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.bpos + e));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(a.edges + e));
     }
   }
+  if (lane < kGroup && ((thick >> lane) & 1u))
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.binv + 3 * (int64_t)s_R[warp][lane]));
   __syncthreads();
 
   // ---------------- phase B: N_in and chemistry, lane per vertex ----------------
