@@ -395,6 +395,8 @@ __device__ __forceinline__ void step_tile(const StepArgs &a, const StepTables *_
           my_src = a.col[e];
           if (!SX_INDEX_OK((unsigned)my_src < (unsigned)a.n, a.diag)) my_src = 0;
         }
+        // phase 3 stages this edge's record as an out-edge: on its way to L1
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.edges + e));
         if constexpr (BAL) {
           if (pure_bal || a.mode[cur ^ 1][my_src]) edge_val = static_cast<const T *>(a.B[cur ^ 1])[e];
           else load_mask<MW>(M_prev, (int64_t)e, my_m);
