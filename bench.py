@@ -56,8 +56,8 @@ WORKLOADS = {
 # dram__bytes_write.sum, the launch of step 305 of the headline run: state
 # step 300, 5 warm-up steps), valid only for the kernel source it was taken
 # on.
-NCU_TRAFFIC = {"step_source_sha256": "468da78a829e761229c11b962c0319e695c6e5584e3d6b844f95faf245b238f2",
-               "bytes_per_launch": 1075.826e6 + 391.624e6, "workload": "c1", "chem_fp32": False}
+NCU_TRAFFIC = {"step_source_sha256": "3fe48cd7104ed5380311f0296e1d895fb366e88c6453d4eda2bd88735c599834",
+               "bytes_per_launch": 1079.582e6 + 392.336e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
