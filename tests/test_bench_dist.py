@@ -71,3 +71,20 @@ def test_single_rank_helpers_are_identity():
 
     assert bench.reduce_max(3.5, 1) == 3.5
     assert bench.aggregate(10, 1, 1000.0) == 10.0
+
+
+def test_grid_pools_built_on_worker_processes_match_direct_builds():
+    """The served and batched benches build their grid pools on spawned
+    worker processes (largest first); every grid must come back under its
+    own key, equal to a build in this process."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    import bench
+    from paper_0912_4273_gb300 import inputs as I
+
+    jobs = [("stromgren_problem", 1500, 11), ("clumpy_problem", 3000, 12), ("stromgren_problem", 2500, 13)]
+    built = bench._build_problems(jobs)
+    for (recipe, n, seed), p in zip(jobs, built):
+        q = getattr(I, recipe)(n, seed=seed)
+        assert p.n == q.n and np.array_equal(p.col, q.col) and np.array_equal(p.pos, q.pos)
