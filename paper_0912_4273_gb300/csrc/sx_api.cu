@@ -544,6 +544,15 @@ int sx_add_source(sx_ctx *c, int32_t vertex, double rate) {
 // at a time; with `budgets`, after every step the budget is reduced and copied
 // to budgets[k] without waiting.
 static int step_direct(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets) {
+  int32_t k_read = 0;  // budgets[k_read ..] are staged on the device, not yet read back
+  auto read_back = [&](int32_t k_end) -> int {
+    if (k_end > k_read)
+      SX_CUDA(c, cudaMemcpyAsync(budgets + k_read, c->g.bhist, sizeof(sx_budget) * (size_t)(k_end - k_read),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    k_read = k_end;
+    return SX_OK;
+  };
+  static_assert(sizeof(sx_budget) == 4 * sizeof(double), "a staged budget is four doubles");
   for (int32_t k = 0; k < nsteps;) {
     const int m = std::min<int32_t>(nsteps - k, sx::kRotAhead);
     SX_CUDA(c, sx::launch_rotation(c->g, c->bins_dev, c->cfg.seed, m, 0, dt, c->stream));
@@ -563,12 +572,15 @@ static int step_direct(sx_ctx *c, double dt, int32_t nsteps, sx_budget *budgets)
       for (size_t s = 0; s < c->src_rate.size(); ++s) c->emitted += c->src_rate[s] * dt;
       c->step++;
       if (budgets) {
-        SX_CUDA(c, sx::launch_budget(c->g, budget_scale(c), c->stream));
-        SX_CUDA(c, cudaMemcpyAsync(budgets + k, c->g.budget_dev + 4, sizeof(sx_budget),
-                                   cudaMemcpyDeviceToHost, c->stream));
+        SX_CUDA(c, sx::launch_budget(c->g, budget_scale(c), c->stream, c->g.bhist + 4 * (k - k_read)));
+        if (k + 1 - k_read == sx::kBudgetHist) {
+          const int rc = read_back(k + 1);
+          if (rc) return rc;
+        }
       }
     }
   }
+  if (budgets) return read_back(nsteps);
   return SX_OK;
 }
 

@@ -13,6 +13,7 @@ constexpr int kMaxDeg = 64;        // largest non-sink degree the step kernel st
 // transports (the values of SX_TRANSPORT_*)
 enum Transport { kTransportDct = 0, kTransportBallistic = 1, kTransportCombined = 2 };
 constexpr int kBudgetBlocks = 256;  // most first-level CTAs of the budget sum
+constexpr int kBudgetHist = 256;    // per-step budgets staged on the device before one read-back
 constexpr int kTile = 32;          // vertices per CTA in the step kernel (one chemistry warp)
 constexpr int kMaxSources = 4096;
 // vertex flags: a sink absorbs everything into "escaped"; a ghost is a copy of
@@ -257,6 +258,7 @@ struct DevGrid {
   double *kappa_dev;    // 1
   double *budget_dev;   // 8: the sums, then the reported budget (k_budget)
   double *bsum;         // kBudgetBlocks*4: the first level of the budget sums
+  double *bhist;        // kBudgetHist*4: reported budgets of recent steps, read back in one copy
   // load-time scratch
   int64_t *s_row_ptr;
   int32_t *s_col;       // nnz neighbour ids as loaded; kept: the step kernel reads the senders here
@@ -283,7 +285,7 @@ __host__ __device__ inline int bin_stride_aligned(int nbins) { return (nbins + 7
 
 struct Layout {
   size_t off_pos, off_row_ptr, off_edges, off_vc, off_mean_len, off_y, off_dif, off_P0, off_P1, off_M0,
-      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget, off_bsum,
+      off_M1, off_partials, off_tabs, off_src, off_share, off_share_f, off_steps, off_incoming, off_diag, off_kpart, off_kappa, off_budget, off_bsum, off_bhist,
       off_s_row_ptr, off_s_col, off_s_nH, off_s_vol, off_s_y0, off_s_flags, off_s_ev, off_s_out,
       off_B0, off_B1, off_mode0, off_mode1, off_stb, off_bpos, off_binv, total;
   int64_t nblocks, nblocks_kappa;
@@ -334,7 +336,9 @@ struct BudgetScale {
   int fly_mode;
   int diffuse;  // 1: add the diffuse photons the cells emitted (the tiles' fourth partial)
 };
-cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st);
+// The budget of the grid's tiles into g.budget_dev (and the reported four
+// terms also into copy_to[0..3] when given).
+cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st, double *copy_to = nullptr);
 cudaError_t launch_kappa(DevGrid &g, const double *bins_dev, cudaStream_t st);
 // dynamic grid update (sx_update.cu)
 cudaError_t launch_mark(DevGrid &g, double y_thresh, double min_spacing, uint8_t *cand,

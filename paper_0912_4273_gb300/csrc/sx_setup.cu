@@ -46,6 +46,7 @@ Layout make_layout(int64_t n, int64_t nnz, int nbins, int precision, int transpo
   L.off_kappa = take(sizeof(double));
   L.off_budget = take(sizeof(double) * 8);
   L.off_bsum = take(sizeof(double) * 4 * kBudgetBlocks);
+  L.off_bhist = take(sizeof(double) * 4 * kBudgetHist);
   L.off_s_row_ptr = take(sizeof(int64_t) * (n + 1));
   L.off_s_col = take(sizeof(int32_t) * nnz);
   L.off_s_nH = take(sizeof(double) * n);
@@ -94,6 +95,7 @@ void bind_layout(DevGrid &g, void *base, const Layout &L) {
   g.kappa_dev = reinterpret_cast<double *>(b + L.off_kappa);
   g.budget_dev = reinterpret_cast<double *>(b + L.off_budget);
   g.bsum = reinterpret_cast<double *>(b + L.off_bsum);
+  g.bhist = reinterpret_cast<double *>(b + L.off_bhist);
   g.s_row_ptr = reinterpret_cast<int64_t *>(b + L.off_s_row_ptr);
   g.s_col = reinterpret_cast<int32_t *>(b + L.off_s_col);
   g.s_nH = reinterpret_cast<double *>(b + L.off_s_nH);

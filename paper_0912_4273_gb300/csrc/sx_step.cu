@@ -1155,68 +1155,85 @@ cudaError_t launch_step_batch(int precision, int group, const StepArgs *d_args, 
 // tiles, then one CTA sums their results; every sum is a fixed tree, so the
 // result does not depend on the schedule.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void budget_tree(double (*s)[256], double a0, double a1, double a2, double a3) {
-  s[0][threadIdx.x] = a0;
-  s[1][threadIdx.x] = a1;
-  s[2][threadIdx.x] = a2;
-  s[3][threadIdx.x] = a3;
+// The four sums of a 256-thread CTA in a fixed tree: within each warp by
+// shuffles, then the 8 warps' sums by warp 0; the result in thread 0.
+__device__ __forceinline__ void budget_tree(double (*s)[8], double a[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], d);
+  }
+  if (lane == 0)
+    for (int c = 0; c < 4; ++c) s[c][warp] = a[c];
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    if (threadIdx.x < h)
-      for (int c = 0; c < 4; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + h];
-    __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a[c] = lane < 8 ? s[c][lane] : 0.0;
+#pragma unroll
+      for (int d = 4; d > 0; d >>= 1) a[c] += __shfl_down_sync(0xffffffffu, a[c], d);
+    }
   }
 }
 
 // CTA b: the partials of tiles [b per, min(nb, (b + 1) per)) into bsum[4 b ..].
 __global__ void __launch_bounds__(256) k_budget_part(int64_t nb, int64_t per, const double *__restrict__ part,
                                                      double *__restrict__ bsum, int diffuse) {
-  __shared__ double s[4][256];
+  __shared__ double s[4][8];
   const int64_t lo = blockIdx.x * per, hi = lo + per < nb ? lo + per : nb;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-    a0 += part[4 * k];
-    a1 += part[4 * k + 1];
-    a2 += part[4 * k + 2];
-    if (diffuse) a3 += part[4 * k + 3];
+    a[0] += part[4 * k];
+    a[1] += part[4 * k + 1];
+    a[2] += part[4 * k + 2];
+    if (diffuse) a[3] += part[4 * k + 3];
   }
-  budget_tree(s, a0, a1, a2, a3);
-  if (threadIdx.x < 4) bsum[4 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+  budget_tree(s, a);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 4; ++c) bsum[4 * blockIdx.x + c] = a[c];
 }
 
 // out[0..2]: the sums of the tiles' partials (absorbed, escaped, in flight,
 // in stored units); out[4..7]: the budget as the C ABI reports it
-// (emitted, absorbed, escaped, in flight in photons, carries included).
+// (emitted, absorbed, escaped, in flight in photons, carries included), also
+// into copy_to[0..3] when given.
 __global__ void __launch_bounds__(256) k_budget(int nblk, const double *__restrict__ bsum,
-                                                double *__restrict__ out, BudgetScale sc) {
-  __shared__ double s[4][256];
+                                                double *__restrict__ out, double *__restrict__ copy_to,
+                                                BudgetScale sc) {
+  __shared__ double s[4][8];
   const int t = threadIdx.x;
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   if (t < nblk)
     for (int c = 0; c < 4; ++c) a[c] = bsum[4 * t + c];
-  budget_tree(s, a[0], a[1], a[2], a[3]);
+  budget_tree(s, a);
   if (t == 0) {
-    out[0] = s[0][0];
-    out[1] = s[1][0];
-    out[2] = s[2][0];
-    out[3] = s[3][0];
+    out[0] = a[0];
+    out[1] = a[1];
+    out[2] = a[2];
+    out[3] = a[3];
     // the sources' photons (host) and, with diffuse radiation, the photons
     // the recombining cells emitted
-    out[4] = sc.diffuse ? __dadd_rn(sc.emitted, __dmul_rn(s[3][0], sc.punit)) : sc.emitted;
-    out[5] = __dadd_rn(__dmul_rn(s[0][0], sc.punit), sc.carry_abs);
-    out[6] = __dadd_rn(__dmul_rn(s[1][0], sc.punit), sc.carry_esc);
-    out[7] = sc.fly_mode == 2 ? __dmul_rn(s[2][0], sc.punit) : (sc.fly_mode == 1 ? sc.carry_fly : 0.0);
+    double r[4];
+    r[0] = sc.diffuse ? __dadd_rn(sc.emitted, __dmul_rn(a[3], sc.punit)) : sc.emitted;
+    r[1] = __dadd_rn(__dmul_rn(a[0], sc.punit), sc.carry_abs);
+    r[2] = __dadd_rn(__dmul_rn(a[1], sc.punit), sc.carry_esc);
+    r[3] = sc.fly_mode == 2 ? __dmul_rn(a[2], sc.punit) : (sc.fly_mode == 1 ? sc.carry_fly : 0.0);
+    for (int c = 0; c < 4; ++c) {
+      out[4 + c] = r[c];
+      if (copy_to) copy_to[c] = r[c];
+    }
   }
 }
 
-cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st) {
+cudaError_t launch_budget(DevGrid &g, const BudgetScale &sc, cudaStream_t st, double *copy_to) {
   const int64_t nb = g.nblocks > 0 ? g.nblocks : 0;
   int64_t nblk = (nb + 255) / 256;  // about 256 tiles per first-level CTA
   if (nblk > kBudgetBlocks) nblk = kBudgetBlocks;
   if (nblk < 1) nblk = 1;
   const int64_t per = (nb + nblk - 1) / nblk;
   k_budget_part<<<(unsigned)nblk, 256, 0, st>>>(nb, per, g.partials, g.bsum, sc.diffuse);
-  k_budget<<<1, 256, 0, st>>>((int)nblk, g.bsum, g.budget_dev, sc);
+  k_budget<<<1, 256, 0, st>>>((int)nblk, g.bsum, g.budget_dev, copy_to, sc);
   return cudaGetLastError();
 }
 

@@ -110,20 +110,21 @@ def test_deterministic_and_chunk_invariant(c0):
         assert b == out[0][1]
 
 
-def test_step_budgets_match_synchronous_reads(c0):
-    """sx_step_budgets queues a budget read behind every step: the rows equal
-    the budgets read synchronously after single steps, and the state equals
-    sx_step's."""
+@pytest.mark.parametrize("steps", [20, 600])
+def test_step_budgets_match_synchronous_reads(c0, steps):
+    """sx_step_budgets queues a budget read behind every step (staged on the
+    device, read back 256 steps at a time): the rows equal the budgets read
+    synchronously after single steps, and the state equals sx_step's."""
     prob, bins, _, _ = c0
     a = S.Solver(bins, seed=0).load(prob)
     rows = []
-    for _ in range(20):
+    for _ in range(steps):
         a.step(DT, 1)
         b = a.budget
         rows.append([b["emitted"], b["absorbed"], b["escaped"], b["in_flight"]])
     c = S.Solver(bins, seed=0).load(prob)
-    out = torch.zeros((20, 4), dtype=torch.float64).pin_memory().numpy()
-    c.step_budgets(DT, 20, out)
+    out = torch.zeros((steps, 4), dtype=torch.float64).pin_memory().numpy()
+    c.step_budgets(DT, steps, out)
     c.sync()
     assert np.array_equal(np.array(rows), out)
     assert np.array_equal(a.y, c.y)
