@@ -56,8 +56,8 @@ WORKLOADS = {
 # dram__bytes_write.sum, the launch of step 305 of the headline run: state
 # step 300, 5 warm-up steps), valid only for the kernel source it was taken
 # on.
-NCU_TRAFFIC = {"step_source_sha256": "3fe48cd7104ed5380311f0296e1d895fb366e88c6453d4eda2bd88735c599834",
-               "bytes_per_launch": 1079.582e6 + 392.336e6, "workload": "c1", "chem_fp32": False}
+NCU_TRAFFIC = {"step_source_sha256": "b424a03402c3172cf34436d87d5c6bee069de5105d35d53741d0e9863789dfdf",
+               "bytes_per_launch": 1079.232e6 + 392.197e6, "workload": "c1", "chem_fp32": False}
 
 
 # ---------------------------------------------------------------------------
