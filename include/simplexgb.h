@@ -211,8 +211,9 @@ int sx_step(sx_ctx *ctx, double dt_s, int32_t nsteps);
 /* sx_step with the photon budget read after every step: budgets[k] receives
    the budget (as sx_read_photons reports it) after the k-th of the nsteps
    steps.  Nothing waits: the reads are queued on the context's stream behind
-   their steps (a reduction of the tiles' partial sums, then a 32-byte
-   device-to-host copy), and budgets holds them once sx_sync, or a call that
+   their steps (a reduction of the tiles' partial sums after every step into
+   a device staging area; one device-to-host copy per 256 steps and one at
+   the end of the call), and budgets holds them once sx_sync, or a call that
    returns results, has returned.  budgets must stay valid until then; in
    page-locked host memory the copies run asynchronously.  Steps are launched
    directly (not through the graph of sx_step).  Errors: as sx_step, and
